@@ -1,0 +1,159 @@
+/*
+ * tho.h — C ABI of libtho: two-stage Householder orthogonalization on GB300.
+ *
+ * Method: He & Shao, "On Two-Stage Householder Orthogonalization"
+ * (arXiv 2602.14449), Algorithm 1 with the second choice of P (Section 3.2).
+ *
+ * Problem (Section 1): given V (n x k0) with orthonormal columns and A (n x k),
+ * k0 + k <= n, compute Q (n x k) with Q^* Q = I, Range([V, A]) contained in
+ * Range([V, Q]) and Range(Q) orthogonal to Range(V), together with R (k x k,
+ * upper triangular, real nonnegative diagonal) and S (k0 x k) such that
+ * [V, A] = [V, Q] [[I, S], [0, R]]  (eq. vavq, Section 3.1).
+ *
+ * Conventions shared by every entry point
+ *   Layout     Column-major.  Element (i, j) of a matrix with leading
+ *              dimension ld is at ptr[i + j * ld]; ld >= number of rows.
+ *              Complex values (THO_C128) are interleaved (re, im) FP64 pairs,
+ *              the layout of torch.complex128 and cuDoubleComplex.
+ *   Memory     Matrix pointers passed to tho_orth / tho_orth_batched /
+ *              tho_orth_backward are DEVICE pointers on the current device.
+ *              They must be aligned to the element size (8 bytes for THO_F64,
+ *              16 bytes for THO_C128), else THO_ERR_ALIGN.
+ *   Ownership  The caller owns every matrix.  V and A are read only.  Q is
+ *              written (and used as the only n-sized scratch of the call).
+ *              The plan owns its device workspace, its launch tables and, for
+ *              batches, its CUDA graph; tho_plan_destroy frees them.
+ *   Streams    Compute calls are asynchronous on the given cudaStream_t
+ *              (passed as void*; NULL = legacy default stream).  A plan must
+ *              not be used by two calls that overlap in time: its workspace is
+ *              shared by all its calls.
+ *   Errors     Every function returns a tho_status_t; nothing aborts and no
+ *              C++ exception crosses the ABI.  Argument errors are detected
+ *              on the host before any launch.  Errors found on the device
+ *              (non-finite values, with THO_FLAG_CHECK_FINITE) are latched in
+ *              a device status word that tho_plan_status reads after the work
+ *              has completed.
+ *   Limits     1 <= k <= THO_MAX_K, 1 <= k0 <= THO_MAX_K0 (k0 = 0 only with
+ *              THO_FLAG_ALLOW_K0_ZERO), k0 + k <= n.
+ */
+#ifndef THO_H_
+#define THO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define THO_MAX_K0 128
+#define THO_MAX_K 32
+
+typedef enum {
+  THO_OK = 0,
+  THO_ERR_ARG = 1,         /* null pointer, bad count, bad leading dimension      */
+  THO_ERR_SHAPE = 2,       /* k0 + k > n, k < 1, k0 < 0, or k0 = 0 without flag    */
+  THO_ERR_ALIGN = 3,       /* matrix pointer not aligned to its element size      */
+  THO_ERR_NOMEM = 4,       /* device or pinned-host allocation failed              */
+  THO_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed                 */
+  THO_ERR_TIMEOUT = 6,     /* reserved: no entry point waits on the device         */
+  THO_ERR_NONFINITE = 7,   /* device check found NaN/Inf (THO_FLAG_CHECK_FINITE)   */
+  THO_ERR_UNSUPPORTED = 8  /* shape or mode beyond what this build implements      */
+} tho_status_t;
+
+typedef enum { THO_F64 = 0, THO_C128 = 1 } tho_dtype_t;
+
+/* THO_PREC_FP64: every step in FP64 (complex128).
+ * THO_PREC_FP32_BULK: the n-length streaming products (W^*A, the rank-k0
+ * updates, the leaf-QR updates and the tree application) run in FP32
+ * arithmetic with FP32 accumulation; inputs and outputs stay FP64 in memory;
+ * the k0 x k0 QR of V_{1:k0,:}, the T solves, reflector norms and phases and
+ * the sums of per-block partials stay FP64. */
+typedef enum { THO_PREC_FP64 = 0, THO_PREC_FP32_BULK = 1 } tho_prec_t;
+
+#define THO_FLAG_ALLOW_K0_ZERO 0x1u /* k0 = 0: plain Householder QR of A        */
+#define THO_FLAG_CHECK_FINITE 0x2u  /* latch THO_ERR_NONFINITE if G, R or Z2    */
+                                    /* contain NaN/Inf (read via tho_plan_status) */
+
+/* One orthogonalization problem: V is n x k0, A is n x k. */
+typedef struct {
+  int64_t n, k0, k;
+  int32_t dtype; /* tho_dtype_t */
+  int32_t prec;  /* tho_prec_t  */
+  uint32_t flags;
+} tho_desc_t;
+
+typedef struct tho_plan_s* tho_plan_t;
+
+/* Build a plan for `count` problems (count = 1: a single orthogonalization;
+ * count > 1: a batch run by tho_orth_batched).  All descriptors must share
+ * dtype, prec and flags.  Allocates the device workspace (cudaMalloc, on the
+ * current device) and uploads the launch tables; synchronous.
+ * Writes the plan handle to *out.  Errors: ARG, SHAPE, UNSUPPORTED, NOMEM, CUDA. */
+tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out);
+
+/* Free the plan's device and host resources (synchronizes the device first).
+ * NULL is accepted. */
+tho_status_t tho_plan_destroy(tho_plan_t plan);
+
+/* Bytes of device workspace the plan holds. */
+size_t tho_plan_workspace_bytes(tho_plan_t plan);
+
+/* Number of kernel launches one tho_orth / tho_orth_batched call issues. */
+int32_t tho_plan_kernel_launches(tho_plan_t plan);
+
+/* Algorithm 1 (Section 3.1) with P = -Q_1 from the QR of V_{1:k0,:}
+ * (Section 3.2, second choice), for a plan with count = 1.
+ *   V  n x k0, ldv >= n (may be NULL when k0 = 0)
+ *   A  n x k,  lda >= n
+ *   Q  n x k,  ldq >= n      output; must not overlap V or A
+ *   R  k x k,  ld = k        output or NULL (upper triangular, diag real >= 0)
+ *   S  k0 x k, ld = k0       output or NULL (S = P^* A'_{1:k0,:} = V^* A)
+ * Asynchronous on `stream`.  Errors: ARG, ALIGN, CUDA. */
+tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A, int64_t lda,
+                      void* Q, int64_t ldq, void* R, void* S, void* stream);
+
+/* Pointers of one batched problem (same meaning as in tho_orth). */
+typedef struct {
+  const void* V;
+  const void* A;
+  void* Q;
+  void* R;
+  void* S;
+  int64_t ldv, lda, ldq;
+} tho_instance_t;
+
+/* Run all problems of a batch plan (count = the plan's count; instances[i]
+ * matches descs[i]).  `instances` is a HOST array; it is copied into the
+ * plan before this call returns.  The batch runs as one CUDA-graph replay
+ * whose kernels each cover every problem (one launch per phase of
+ * Algorithm 1 for the whole batch).  The graph is instantiated on the first
+ * call for a given stream.  Asynchronous on `stream`.
+ * Errors: ARG, ALIGN, CUDA. */
+tho_status_t tho_orth_batched(tho_plan_t plan, const tho_instance_t* instances, int32_t count,
+                              void* stream);
+
+/* Reverse-mode derivative of the map (V, A) -> Q of Algorithm 1 (second
+ * choice of P, exact-arithmetic map at arbitrary V, A) for a real FP64 plan
+ * with count = 1.  Given Q from tho_orth on the same V, A and the upstream
+ * gradient dQ (n x k), writes dV (n x k0) and dA (n x k) such that
+ * <dQ, Q'(V, A)[dV_dir, dA_dir]> = <dV, dV_dir> + <dA, dA_dir> (real inner
+ * products).  (W, T) and the trailing factorization are recomputed, not
+ * stored.  Asynchronous on `stream`.  Errors: ARG, ALIGN, UNSUPPORTED, CUDA. */
+tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, const void* A,
+                               int64_t lda, const void* Q, int64_t ldq, const void* dQ,
+                               int64_t lddq, void* dV, int64_t lddv, void* dA, int64_t ldda,
+                               void* stream);
+
+/* Read and clear the plan's device status word (synchronizes the device).
+ * Returns THO_OK or the first device-detected error (THO_ERR_NONFINITE). */
+tho_status_t tho_plan_status(tho_plan_t plan);
+
+/* Static English description of a status code. */
+const char* tho_status_string(tho_status_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THO_H_ */

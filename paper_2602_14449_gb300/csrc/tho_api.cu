@@ -1,0 +1,336 @@
+// C ABI of libtho (include/tho.h): plans, argument checking, launch tables,
+// workspace layout and the CUDA-graph path of the batched entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tho.h"
+#include "tho_launch.h"
+
+using tho::Inst;
+using tho::Io;
+using tho::PlanCore;
+using tho::WorkItemH;
+
+struct tho_plan_s {
+  PlanCore pc;
+  const tho::Launcher* L = nullptr;
+  int device = 0;
+  // batched path
+  Io* d_io = nullptr;
+  Io* h_io = nullptr;  // pinned staging copy of the instance table
+  cudaEvent_t io_ev = nullptr;
+  bool io_ev_recorded = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+constexpr int64_t kAlignElems = 32;
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
+  if (d.dtype != d0.dtype || d.prec != d0.prec || d.flags != d0.flags) return THO_ERR_ARG;
+  if (d.dtype != THO_F64 && d.dtype != THO_C128) return THO_ERR_ARG;
+  if (d.prec != THO_PREC_FP64 && d.prec != THO_PREC_FP32_BULK) return THO_ERR_ARG;
+  if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE)) return THO_ERR_ARG;
+  if (d.k < 1 || d.k0 < 0 || d.n < 1) return THO_ERR_SHAPE;
+  if (d.k0 == 0 && !(d.flags & THO_FLAG_ALLOW_K0_ZERO)) return THO_ERR_SHAPE;
+  if (d.k0 + d.k > d.n) return THO_ERR_SHAPE;
+  if (d.k > THO_MAX_K || d.k0 > THO_MAX_K0) return THO_ERR_UNSUPPORTED;
+  return THO_OK;
+}
+
+void free_plan(tho_plan_s* p) {
+  if (!p) return;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->io_ev) cudaEventDestroy(p->io_ev);
+  if (p->h_io) cudaFreeHost(p->h_io);
+  if (p->d_io) cudaFree(p->d_io);
+  if (p->pc.ws) cudaFree(p->pc.ws);
+  if (p->pc.d_insts) cudaFree(p->pc.d_insts);
+  if (p->pc.d_items) cudaFree(p->pc.d_items);
+  if (p->pc.d_status) cudaFree(p->pc.d_status);
+  delete p;
+}
+
+tho_status_t check_io(const Inst& I, size_t elem, const void* V, int64_t ldv, const void* A,
+                      int64_t lda, const void* Q, int64_t ldq, const void* R, const void* S) {
+  if (!A || !Q) return THO_ERR_ARG;
+  if (I.k0 > 0 && !V) return THO_ERR_ARG;
+  if (lda < I.n || ldq < I.n || (I.k0 > 0 && ldv < I.n)) return THO_ERR_ARG;
+  auto mis = [elem](const void* p) { return p && (reinterpret_cast<uintptr_t>(p) % elem) != 0; };
+  if (mis(V) || mis(A) || mis(Q) || mis(R) || mis(S)) return THO_ERR_ALIGN;
+  return THO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tho_status_string(tho_status_t s) {
+  switch (s) {
+    case THO_OK: return "success";
+    case THO_ERR_ARG: return "invalid argument (null pointer, count or leading dimension)";
+    case THO_ERR_SHAPE: return "invalid shape (need 1 <= k, 0 <= k0, k0 + k <= n; k0 = 0 needs THO_FLAG_ALLOW_K0_ZERO)";
+    case THO_ERR_ALIGN: return "matrix pointer not aligned to its element size";
+    case THO_ERR_NOMEM: return "device or pinned host allocation failed";
+    case THO_ERR_CUDA: return "CUDA runtime error";
+    case THO_ERR_TIMEOUT: return "device wait timed out";
+    case THO_ERR_NONFINITE: return "non-finite value detected on the device";
+    case THO_ERR_UNSUPPORTED: return "shape or mode not supported by this build";
+  }
+  return "unknown status";
+}
+
+tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
+  if (!descs || !out || count < 1) return THO_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    tho_status_t s = check_desc(descs[i], descs[0]);
+    if (s != THO_OK) return s;
+  }
+  tho_plan_s* p = new (std::nothrow) tho_plan_s();
+  if (!p) return THO_ERR_NOMEM;
+  PlanCore& pc = p->pc;
+  pc.count = count;
+  pc.dtype = descs[0].dtype;
+  pc.prec = descs[0].prec;
+  pc.flags = descs[0].flags;
+  const bool cplx = pc.dtype == THO_C128;
+  const bool b32 = pc.prec == THO_PREC_FP32_BULK;
+  p->L = cplx ? (b32 ? &tho::kLaunchC128Bulk32 : &tho::kLaunchC128)
+              : (b32 ? &tho::kLaunchF64Bulk32 : &tho::kLaunchF64);
+  if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return THO_ERR_CUDA; }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    free_plan(p);
+    return THO_ERR_CUDA;
+  }
+  for (int i = 0; i < count; ++i) {
+    pc.kmax = std::max<int>(pc.kmax, (int)descs[i].k);
+    pc.k0max = std::max<int>(pc.k0max, (int)descs[i].k0);
+    pc.any_k0 = pc.any_k0 || descs[i].k0 > 0;
+  }
+  pc.kpmax = (int)round_up(pc.kmax, tho::kBJ);
+  pc.k0pmax = (int)round_up(pc.k0max, tho::kBI);
+  // Leaf height: the largest of 256/128/64 rows whose panel fits in shared memory.
+  pc.P = 0;
+  for (int P : {256, 128, 64}) {
+    if (P < 2 * pc.kmax) continue;
+    if (tho::leaf_smem_bytes(P, pc.k0pmax, pc.kpmax, p->L->bulk_elem, p->L->elem) <= 200 * 1024) {
+      pc.P = P;
+      break;
+    }
+  }
+  if (pc.P == 0) { free_plan(p); return THO_ERR_UNSUPPORTED; }
+
+  // Per-instance partition and workspace layout.
+  const int64_t target_total = (count == 1 ? 2 : 8) * (int64_t)sms;
+  double msum = 0;
+  for (int i = 0; i < count; ++i) msum += (double)(descs[i].n - descs[i].k0);
+  int64_t off = 0;
+  auto take = [&off](int64_t elems) {
+    int64_t o = off;
+    off += round_up(std::max<int64_t>(elems, 1), kAlignElems);
+    return o;
+  };
+  pc.h_insts.resize(count);
+  for (int i = 0; i < count; ++i) {
+    Inst& I = pc.h_insts[i];
+    std::memset(&I, 0, sizeof(I));
+    I.n = descs[i].n;
+    I.k0 = descs[i].k0;
+    I.k = descs[i].k;
+    I.m = I.n - I.k0;
+    I.k0p = (int)round_up(I.k0, tho::kBI);
+    I.kp = (int)round_up(I.k, tho::kBJ);
+    I.nb = (int)std::max<int64_t>(1, ceil_div(I.m, pc.P));
+    I.lev_cnt[0] = I.nb;
+    I.lev_off[0] = 0;
+    int L = 0;
+    int64_t nodes = I.nb;
+    while (I.lev_cnt[L] > 1) {
+      if (L + 1 > tho::kMaxLevels) { free_plan(p); return THO_ERR_UNSUPPORTED; }
+      I.lev_cnt[L + 1] = (I.lev_cnt[L] + 1) / 2;
+      I.lev_off[L + 1] = I.lev_off[L] + I.lev_cnt[L];
+      nodes += I.lev_cnt[L + 1];
+      ++L;
+    }
+    I.L = L;
+    pc.Lmax = std::max(pc.Lmax, L);
+    int64_t target = std::max<int64_t>(1, std::llround((double)target_total * (double)I.m / msum));
+    I.rows1 = round_up(ceil_div(I.m, target), tho::kTileRows);
+    I.g1 = (int)ceil_div(I.m, I.rows1);
+    I.rows4 = I.rows1;
+    I.g4 = I.g1;
+    I.leaves3 = (int)ceil_div(I.nb, target);
+    I.g3 = (int)ceil_div(I.nb, I.leaves3);
+    const int64_t k0 = I.k0, k = I.k, kk = k * k;
+    I.oX = take(k0 * k0);
+    I.oQ1 = take(k0 * k0);
+    I.oR1 = take(k0 * k0);
+    I.oT = take(k0 * k0);
+    I.oWt = take(k0 * k0);
+    I.oZ = take(k0 * k);
+    I.oZ2 = take(k0 * k);
+    I.oG1 = take((int64_t)I.g1 * k0 * k);
+    I.oG3 = take((int64_t)I.g3 * k0 * k);
+    I.oRn = take(nodes * kk);
+    I.oRef = take((nodes - I.nb) * (kk + 2 * k));
+    I.oF = take(nodes * kk);
+  }
+  pc.ws_elems = (size_t)off;
+
+  // Work-item tables, phase by phase.
+  auto& it = pc.h_items;
+  pc.tab.gram_off = (int)it.size();
+  for (int i = 0; i < count; ++i)
+    if (pc.h_insts[i].k0 > 0)
+      for (int c = 0; c < pc.h_insts[i].g1; ++c) it.push_back({i, c});
+  pc.tab.gram_n = (int)it.size() - pc.tab.gram_off;
+  pc.tab.leaf_off = (int)it.size();
+  for (int i = 0; i < count; ++i)
+    for (int b = 0; b < pc.h_insts[i].nb; ++b) it.push_back({i, b});
+  pc.tab.leaf_n = (int)it.size() - pc.tab.leaf_off;
+  pc.tab.apply_off = (int)it.size();
+  for (int i = 0; i < count; ++i)
+    for (int c = 0; c < pc.h_insts[i].g3; ++c) it.push_back({i, c});
+  pc.tab.apply_n = (int)it.size() - pc.tab.apply_off;
+  pc.tab.upd_off = (int)it.size();
+  for (int i = 0; i < count; ++i)
+    if (pc.h_insts[i].k0 > 0)
+      for (int c = 0; c < pc.h_insts[i].g4; ++c) it.push_back({i, c});
+  pc.tab.upd_n = (int)it.size() - pc.tab.upd_off;
+  for (int l = 1; l <= pc.Lmax; ++l) {
+    pc.tab.lev_off[l] = (int)it.size();
+    for (int i = 0; i < count; ++i)
+      if (pc.h_insts[i].L >= l)
+        for (int c = 0; c < pc.h_insts[i].lev_cnt[l]; ++c) it.push_back({i, c});
+    pc.tab.lev_n[l] = (int)it.size() - pc.tab.lev_off[l];
+  }
+
+  // Device allocations and uploads.
+  const size_t ws_bytes = pc.ws_elems * p->L->elem;
+  if (cudaMalloc(&pc.ws, ws_bytes) != cudaSuccess ||
+      cudaMalloc(&pc.d_insts, sizeof(Inst) * count) != cudaSuccess ||
+      cudaMalloc(&pc.d_items, sizeof(WorkItemH) * std::max<size_t>(it.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&pc.d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    return THO_ERR_NOMEM;
+  }
+  if (cudaMemcpy(pc.d_insts, pc.h_insts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(pc.d_items, it.data(), sizeof(WorkItemH) * it.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(pc.ws, 0, ws_bytes) != cudaSuccess || cudaMemset(pc.d_status, 0, sizeof(int)) != cudaSuccess ||
+      p->L->configure(pc) != cudaSuccess) {
+    free_plan(p);
+    return THO_ERR_CUDA;
+  }
+  if (count > 1) {
+    if (cudaMalloc(&p->d_io, sizeof(Io) * count) != cudaSuccess ||
+        cudaMallocHost(&p->h_io, sizeof(Io) * count) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(p);
+      return THO_ERR_NOMEM;
+    }
+    if (cudaEventCreateWithFlags(&p->io_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      free_plan(p);
+      return THO_ERR_CUDA;
+    }
+  }
+  *out = p;
+  return THO_OK;
+}
+
+tho_status_t tho_plan_destroy(tho_plan_t plan) {
+  if (!plan) return THO_OK;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return THO_OK;
+}
+
+size_t tho_plan_workspace_bytes(tho_plan_t plan) {
+  return plan ? plan->pc.ws_elems * plan->L->elem : 0;
+}
+
+int32_t tho_plan_kernel_launches(tho_plan_t plan) { return plan ? plan->pc.launches : 0; }
+
+tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A, int64_t lda, void* Q,
+                      int64_t ldq, void* R, void* S, void* stream) {
+  if (!plan || plan->pc.count != 1) return THO_ERR_ARG;
+  const Inst& I = plan->pc.h_insts[0];
+  tho_status_t s = check_io(I, plan->L->elem, V, ldv, A, lda, Q, ldq, R, S);
+  if (s != THO_OK) return s;
+  Io io0{V, A, Q, R, S, ldv, lda, ldq};
+  if (plan->L->run(plan->pc, nullptr, io0, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return THO_ERR_CUDA;
+  return THO_OK;
+}
+
+tho_status_t tho_orth_batched(tho_plan_t plan, const tho_instance_t* inst, int32_t count, void* stream) {
+  if (!plan || !inst || count != plan->pc.count || count < 2) return THO_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    tho_status_t s = check_io(plan->pc.h_insts[i], plan->L->elem, inst[i].V, inst[i].ldv, inst[i].A,
+                              inst[i].lda, inst[i].Q, inst[i].ldq, inst[i].R, inst[i].S);
+    if (s != THO_OK) return s;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // The pinned staging table may still feed the previous call's copy.
+  if (plan->io_ev_recorded && cudaEventSynchronize(plan->io_ev) != cudaSuccess) return THO_ERR_CUDA;
+  for (int i = 0; i < count; ++i)
+    plan->h_io[i] = Io{inst[i].V, inst[i].A, inst[i].Q, inst[i].R, inst[i].S, inst[i].ldv, inst[i].lda, inst[i].ldq};
+  if (cudaMemcpyAsync(plan->d_io, plan->h_io, sizeof(Io) * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaEventRecord(plan->io_ev, st) != cudaSuccess)
+    return THO_ERR_CUDA;
+  plan->io_ev_recorded = true;
+  if (!plan->gexec) {
+    cudaGraph_t g = nullptr;
+    const Io none{};
+    if (cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return THO_ERR_CUDA;
+    cudaError_t er = plan->L->run(plan->pc, plan->d_io, none, plan->cap_stream);
+    cudaError_t ec = cudaStreamEndCapture(plan->cap_stream, &g);
+    if (er != cudaSuccess || ec != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return THO_ERR_CUDA;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&plan->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      plan->gexec = nullptr;
+      return THO_ERR_CUDA;
+    }
+  }
+  if (cudaGraphLaunch(plan->gexec, st) != cudaSuccess) return THO_ERR_CUDA;
+  return THO_OK;
+}
+
+tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, const void* A, int64_t lda,
+                               const void* Q, int64_t ldq, const void* dQ, int64_t lddq, void* dV,
+                               int64_t lddv, void* dA, int64_t ldda, void* stream) {
+  (void)V; (void)ldv; (void)A; (void)lda; (void)Q; (void)ldq; (void)dQ; (void)lddq;
+  (void)dV; (void)lddv; (void)dA; (void)ldda; (void)stream;
+  if (!plan) return THO_ERR_ARG;
+  return THO_ERR_UNSUPPORTED;
+}
+
+tho_status_t tho_plan_status(tho_plan_t plan) {
+  if (!plan) return THO_ERR_ARG;
+  int h = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return THO_ERR_CUDA;
+  if (cudaMemcpy(&h, plan->pc.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return THO_ERR_CUDA;
+  if (cudaMemset(plan->pc.d_status, 0, sizeof(int)) != cudaSuccess) return THO_ERR_CUDA;
+  return (tho_status_t)h;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Templated host launch sequence; instantiated once per (storage, bulk) pair.
+#pragma once
+
+#include <algorithm>
+
+#include "tho_kernels.cuh"
+#include "tho_launch.h"
+
+namespace tho {
+
+template <class S, class B>
+cudaError_t configure_impl(PlanCore& pc) {
+  const size_t b = sizeof(B);
+  pc.smem_gram = std::max<size_t>((size_t)kTileRows * (pc.k0pmax + pc.kpmax), kRedElems) * b;
+  pc.smem_apply = std::max<size_t>((size_t)(2 * kTileRows * pc.kpmax + pc.kpmax * pc.kpmax +
+                                            kTileRows * pc.k0pmax),
+                                   kRedElems) * b;
+  pc.smem_upd = (size_t)(pc.k0pmax * pc.kpmax + kTileRows * pc.k0pmax) * b;
+  pc.smem_leaf = leaf_smem_bytes(pc.P, pc.k0pmax, pc.kpmax, b, sizeof(S));
+  pc.smem_tree = (size_t)2 * pc.kmax * pc.kmax * sizeof(S);
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_gram);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_apply_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_apply);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_update_q<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_upd);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_leaf<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_leaf);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tree_up<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_tree);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tree_down<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_tree);
+  if (e != cudaSuccess) return e;
+  // Count the launches one call issues (same order as run_impl).
+  int n = 0;
+  if (pc.any_k0) n += 3;  // v1qr, gram, solve_z
+  n += 1;                  // leaf
+  for (int l = 1; l <= pc.Lmax; ++l) n += pc.tab.lev_n[l] > 0 ? 2 : 0;
+  n += 2;                  // root, apply_gram
+  if (pc.any_k0) n += 2;  // solve_z2, update_q
+  pc.launches = n;
+  return cudaSuccess;
+}
+
+template <class S, class B>
+cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStream_t st) {
+  const WorkItem* items = reinterpret_cast<const WorkItem*>(pc.d_items);
+  const Inst* insts = pc.d_insts;
+  void* ws = pc.ws;
+  const dim3 blk(kThreads);
+  if (pc.any_k0) {
+    k_v1qr<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws);
+    if (pc.tab.gram_n > 0)
+      k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
+    k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
+  }
+  k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P);
+  for (int l = 1; l <= pc.Lmax; ++l)
+    if (pc.tab.lev_n[l] > 0)
+      k_tree_up<S><<<pc.tab.lev_n[l], blk, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+  k_root<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
+  for (int l = pc.Lmax; l >= 1; --l)
+    if (pc.tab.lev_n[l] > 0)
+      k_tree_down<S><<<pc.tab.lev_n[l], blk, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+  k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws);
+  if (pc.any_k0) {
+    k_solve_z2<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
+    if (pc.tab.upd_n > 0)
+      k_update_q<S, B><<<pc.tab.upd_n, blk, pc.smem_upd, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws);
+  }
+  return cudaGetLastError();
+}
+
+template <class S, class B>
+constexpr Launcher make_launcher() {
+  return Launcher{sizeof(S), sizeof(B), &configure_impl<S, B>, &run_impl<S, B>};
+}
+
+}  // namespace tho

@@ -1,0 +1,68 @@
+// Host-side plan core and the per-(storage, bulk) launch table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "tho_plan.h"
+
+namespace tho {
+
+struct WorkItemH {
+  int32_t inst, idx;
+};
+
+// Offsets/counts of each phase's work items inside the device item array.
+struct Tables {
+  int gram_off = 0, gram_n = 0;
+  int leaf_off = 0, leaf_n = 0;
+  int apply_off = 0, apply_n = 0;
+  int upd_off = 0, upd_n = 0;
+  int lev_off[kMaxLevels + 1] = {0};
+  int lev_n[kMaxLevels + 1] = {0};
+};
+
+struct PlanCore {
+  int count = 0;
+  int dtype = 0, prec = 0;
+  uint32_t flags = 0;
+  int P = 256;           // nominal leaf rows
+  int Lmax = 0;          // deepest tree
+  int kmax = 0, k0max = 0, k0pmax = 0, kpmax = 0;
+  bool any_k0 = false;
+  std::vector<Inst> h_insts;
+  Inst* d_insts = nullptr;
+  std::vector<WorkItemH> h_items;
+  void* d_items = nullptr;
+  Tables tab;
+  void* ws = nullptr;
+  size_t ws_elems = 0;
+  int* d_status = nullptr;
+  size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
+  int launches = 0;  // kernel launches per call
+};
+
+struct Launcher {
+  size_t elem;       // bytes of the FP64 storage type
+  size_t bulk_elem;  // bytes of the bulk arithmetic type
+  // Compute shared-memory sizes for the plan and raise the kernels' limits.
+  cudaError_t (*configure)(PlanCore& pc);
+  // Enqueue every kernel of one call on `st`.  d_io: device Io table (batched)
+  // or nullptr (single problem, pointers in io0).
+  cudaError_t (*run)(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStream_t st);
+};
+
+extern const Launcher kLaunchF64;       // real, FP64
+extern const Launcher kLaunchF64Bulk32; // real, FP32 bulk
+extern const Launcher kLaunchC128;      // complex, FP64
+extern const Launcher kLaunchC128Bulk32;// complex, FP32 bulk
+
+// Leaf-kernel shared memory for leaf height P (bytes).
+inline size_t leaf_smem_bytes(int P, int k0p, int kp, size_t bulk, size_t elem) {
+  return (size_t)(P * kp + k0p * kp + kTileRows * k0p) * bulk + kMaxKP * (8 + bulk + elem);
+}
+
+}  // namespace tho

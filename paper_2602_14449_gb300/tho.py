@@ -1,0 +1,254 @@
+"""Thin Python binding of libtho (include/tho.h) over ctypes.
+
+Argument marshalling only: every step of the orthogonalization runs in the
+CUDA kernels of ``libtho.so``.  PyTorch provides device memory and the current
+stream.  There is no CPU or PyTorch fallback: if the library is missing the
+calls raise.
+
+Matrices are column-major torch CUDA tensors: shape (rows, cols) with
+stride (1, ld), ld >= rows -- the layout of ``x.t().contiguous().t()`` or
+``torch.empty_strided((r, c), (1, r))``.  ``colmajor`` converts explicitly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtho.so")
+
+THO_OK, THO_ERR_ARG, THO_ERR_SHAPE, THO_ERR_ALIGN, THO_ERR_NOMEM = 0, 1, 2, 3, 4
+THO_ERR_CUDA, THO_ERR_TIMEOUT, THO_ERR_NONFINITE, THO_ERR_UNSUPPORTED = 5, 6, 7, 8
+THO_F64, THO_C128 = 0, 1
+THO_PREC_FP64, THO_PREC_FP32_BULK = 0, 1
+THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE = 0x1, 0x2
+THO_MAX_K0, THO_MAX_K = 128, 32
+
+EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",
+            "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string")
+
+
+class ThoError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} (status {code})")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("k0", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("prec", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_void_p), ("A", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("R", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("ldv", ctypes.c_int64), ("lda", ctypes.c_int64), ("ldq", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libtho.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libtho.so not found at {p}; build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.tho_plan.argtypes = [ctypes.POINTER(Desc), i32, ctypes.POINTER(vp)]
+        lib.tho_plan.restype = ctypes.c_int
+        lib.tho_plan_destroy.argtypes = [vp]
+        lib.tho_plan_destroy.restype = ctypes.c_int
+        lib.tho_plan_workspace_bytes.argtypes = [vp]
+        lib.tho_plan_workspace_bytes.restype = ctypes.c_size_t
+        lib.tho_plan_kernel_launches.argtypes = [vp]
+        lib.tho_plan_kernel_launches.restype = ctypes.c_int32
+        lib.tho_orth.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp, vp]
+        lib.tho_orth.restype = ctypes.c_int
+        lib.tho_orth_batched.argtypes = [vp, ctypes.POINTER(Instance), i32, vp]
+        lib.tho_orth_batched.restype = ctypes.c_int
+        lib.tho_orth_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp]
+        lib.tho_orth_backward.restype = ctypes.c_int
+        lib.tho_plan_status.argtypes = [vp]
+        lib.tho_plan_status.restype = ctypes.c_int
+        lib.tho_status_string.argtypes = [ctypes.c_int]
+        lib.tho_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def status_string(code: int) -> str:
+    return load().tho_status_string(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != THO_OK:
+        raise ThoError(code, what)
+
+
+def colmajor(x: torch.Tensor) -> torch.Tensor:
+    """Column-major copy of a 2-D tensor (explicit layout conversion for callers)."""
+    return x.t().contiguous().t()
+
+
+def _ld(x: torch.Tensor, name: str) -> int:
+    if x.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    rows, cols = x.shape
+    if cols > 1 and x.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride (1, ld)); use tho.colmajor()")
+    return max(x.stride(1), rows) if cols > 1 else max(rows, 1)
+
+
+def _dtype_code(t: torch.dtype) -> int:
+    if t == torch.float64:
+        return THO_F64
+    if t == torch.complex128:
+        return THO_C128
+    raise ValueError(f"unsupported dtype {t}; use float64 or complex128")
+
+
+def _empty_cm(rows: int, cols: int, dtype, device) -> torch.Tensor:
+    return torch.empty_strided((rows, cols), (1, max(rows, 1)), dtype=dtype, device=device)
+
+
+class Plan:
+    """Owns one tho_plan_t (workspace, launch tables, batched graph)."""
+
+    def __init__(self, shapes, dtype=torch.float64, prec: int = THO_PREC_FP64, flags: int = 0):
+        lib = load()
+        shapes = list(shapes)
+        arr = (Desc * len(shapes))()
+        code = _dtype_code(dtype)
+        for i, (n, k0, k) in enumerate(shapes):
+            arr[i] = Desc(n, k0, k, code, prec, flags)
+        h = ctypes.c_void_p()
+        _check(lib.tho_plan(arr, len(shapes), ctypes.byref(h)), "tho_plan")
+        self.handle = h
+        self.shapes = shapes
+        self.dtype = dtype
+        self.prec = prec
+        self.flags = flags
+
+    @property
+    def workspace_bytes(self) -> int:
+        return load().tho_plan_workspace_bytes(self.handle)
+
+    @property
+    def kernel_launches(self) -> int:
+        return load().tho_plan_kernel_launches(self.handle)
+
+    def status(self) -> int:
+        return load().tho_plan_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.tho_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plan_cache: dict = {}
+
+
+def get_plan(shapes, dtype, prec=THO_PREC_FP64, flags=0) -> Plan:
+    """Plan cached per (shapes, dtype, prec, flags, device, stream): calls on one
+    plan share its workspace, so concurrent streams get separate plans."""
+    dev = torch.cuda.current_device()
+    st = torch.cuda.current_stream().cuda_stream
+    key = (tuple(shapes), dtype, prec, flags, dev, st)
+    p = _plan_cache.get(key)
+    if p is None:
+        p = Plan(shapes, dtype, prec, flags)
+        _plan_cache[key] = p
+    return p
+
+
+def _ptr(x):
+    return ctypes.c_void_p(x.data_ptr()) if x is not None else None
+
+
+def orth(V: torch.Tensor, A: torch.Tensor, prec: int = THO_PREC_FP64, want_R: bool = True,
+         want_S: bool = True, flags: int = 0, plan: Plan | None = None, Q: torch.Tensor | None = None):
+    """Algorithm 1 (second choice of P) on the GPU: returns (Q, R, S).
+
+    V: n x k0 (orthonormal columns), A: n x k, column-major CUDA tensors of
+    dtype float64 or complex128.  R (k x k) and S (k0 x k) are None unless
+    requested.  Runs on the current torch stream.
+    """
+    n, k = A.shape
+    k0 = V.shape[1] if V is not None else 0
+    if k0 == 0:
+        flags |= THO_FLAG_ALLOW_K0_ZERO
+    dt = A.dtype
+    if V is not None and k0 > 0 and (V.dtype != dt or V.shape[0] != n or V.device != A.device):
+        raise ValueError("V and A must share dtype, device and row count")
+    ldv = _ld(V, "V") if k0 > 0 else n
+    lda = _ld(A, "A")
+    if Q is None:
+        Q = _empty_cm(n, k, dt, A.device)
+    ldq = _ld(Q, "Q")
+    R = _empty_cm(k, k, dt, A.device) if want_R else None
+    S = _empty_cm(k0, k, dt, A.device) if (want_S and k0 > 0) else None
+    p = plan or get_plan([(n, k0, k)], dt, prec, flags)
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().tho_orth(p.handle, _ptr(V) if k0 > 0 else None, ldv, _ptr(A), lda, _ptr(Q), ldq,
+                           _ptr(R), _ptr(S), ctypes.c_void_p(st)), "tho_orth")
+    return Q, R, S
+
+
+def orth_batched(pairs, prec: int = THO_PREC_FP64, plan: Plan | None = None, outs=None):
+    """Batched Algorithm 1 over a list of (V, A): one CUDA-graph replay.
+
+    Returns a list of (Q, R, S).  ``outs`` may pass preallocated (Q, R, S) triples.
+    """
+    shapes = [(A.shape[0], V.shape[1], A.shape[1]) for V, A in pairs]
+    dt = pairs[0][1].dtype
+    p = plan or get_plan(shapes, dt, prec, 0)
+    arr = (Instance * len(pairs))()
+    res = []
+    for i, (V, A) in enumerate(pairs):
+        n, k = A.shape
+        k0 = V.shape[1]
+        if outs is None:
+            Q = _empty_cm(n, k, dt, A.device)
+            R = _empty_cm(k, k, dt, A.device)
+            S = _empty_cm(k0, k, dt, A.device)
+        else:
+            Q, R, S = outs[i]
+        arr[i] = Instance(V.data_ptr(), A.data_ptr(), Q.data_ptr(), R.data_ptr(), S.data_ptr(),
+                          _ld(V, "V"), _ld(A, "A"), _ld(Q, "Q"))
+        res.append((Q, R, S))
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().tho_orth_batched(p.handle, arr, len(pairs), ctypes.c_void_p(st)), "tho_orth_batched")
+    return res
+
+
+def orth_backward(V, A, Q, dQ, plan: Plan | None = None):
+    """Reverse-mode derivative of (V, A) -> Q (real FP64): returns (dV, dA)."""
+    n, k = A.shape
+    k0 = V.shape[1]
+    dV = _empty_cm(n, k0, V.dtype, V.device)
+    dA = _empty_cm(n, k, A.dtype, A.device)
+    p = plan or get_plan([(n, k0, k)], A.dtype, THO_PREC_FP64, 0)
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().tho_orth_backward(p.handle, _ptr(V), _ld(V, "V"), _ptr(A), _ld(A, "A"), _ptr(Q), _ld(Q, "Q"),
+                                    _ptr(dQ), _ld(dQ, "dQ"), _ptr(dV), _ld(dV, "dV"), _ptr(dA), _ld(dA, "dA"),
+                                    ctypes.c_void_p(st)), "tho_orth_backward")
+    return dV, dA

@@ -1,0 +1,146 @@
+"""CUDA path against the CPU oracle (through the C ABI), element by element.
+
+Tolerances: entrywise |Q - Q_oracle| <= 1e-11 on well-conditioned inputs, loss
+of orthogonality and relative residual <= 1e-13 in FP64 (the bounds stated for
+the method), <= 1e-5 loss of orthogonality for the FP32-bulk variant.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from metrics import loo as loo_np
+from paper_2602_14449_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_Q = 1e-11
+TOL_LOO = 1e-13
+
+
+@pytest.fixture(scope="module")
+def tho():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_14449_gb300 import tho as _tho
+    _tho.load()
+    return _tho
+
+
+def _run(tho, p, prec=0):
+    dev = torch.device("cuda")
+    V = p.V.to(dev)
+    A = p.A.to(dev)
+    Q, R, S = tho.orth(V, A, prec=prec)
+    torch.cuda.synchronize()
+    return Q.cpu().numpy(), R.cpu().numpy(), (S.cpu().numpy() if S is not None else None)
+
+
+def _cmp(tho, p, tol=TOL_Q):
+    Q, R, S = _run(tho, p)
+    Qo, Ro, So = oracle.two_stage(p.V.numpy(), p.A.numpy())
+    np.testing.assert_allclose(Q, Qo, atol=tol, rtol=0)
+    np.testing.assert_allclose(R, Ro, atol=tol * max(1.0, np.abs(Ro).max()), rtol=0)
+    if p.k0:
+        np.testing.assert_allclose(S, So, atol=tol * max(1.0, np.abs(So).max()), rtol=0)
+    assert loo_np(p.V.numpy(), Q) < TOL_LOO
+    return Q
+
+
+def test_config1_full_size(tho):
+    """real FP64, n=4096, k0=16, k=4 (C1), entrywise against the oracle."""
+    _cmp(tho, inputs.config_problem(1))
+
+
+def test_worked_example(tho):
+    """eq. (badbcg): Q = [e3, e4] and LOO ~ u on the GPU too (Example 1)."""
+    V, A = inputs.worked_example()
+    dev = torch.device("cuda")
+    Q, R, S = tho.orth(V.to(dev), A.to(dev))
+    Q = Q.cpu().numpy()
+    np.testing.assert_allclose(Q, np.array([[0, 0], [0, 0], [1, 0], [0, 1.0]]), atol=1e-15)
+    np.testing.assert_allclose(R.cpu().numpy(), 1e-30 * np.eye(2), rtol=1e-14, atol=0)
+    assert loo_np(V.numpy(), Q) < 1e-15
+
+
+SHAPES = [
+    (64, 1, 1), (33, 16, 17), (97, 8, 4), (1000, 7, 3), (4095, 16, 4), (5000, 32, 32),
+    (12345, 64, 16), (40000, 128, 32), (70001, 5, 9), (3 * 256 + 17, 64, 30),
+]
+
+
+@pytest.mark.parametrize("n,k0,k", SHAPES)
+def test_random_real(tho, n, k0, k):
+    _cmp(tho, inputs.random_problem(n, k0, k, dtype=torch.float64, seed=n + 7 * k0 + 31 * k))
+
+
+@pytest.mark.parametrize("n,k0,k", [(64, 1, 1), (300, 8, 5), (5000, 32, 32), (20001, 128, 32), (777, 13, 2)])
+def test_random_complex(tho, n, k0, k):
+    _cmp(tho, inputs.random_problem(n, k0, k, dtype=torch.complex128, seed=n + k0 + k))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_k0_zero_is_householder_qr(tho, dtype):
+    p = inputs.random_problem(3000, 0, 8, dtype=dtype, seed=2)
+    dev = torch.device("cuda")
+    A = p.A.to(dev)
+    V = torch.zeros((3000, 0), dtype=dtype, device=dev)
+    Q, R, _ = tho.orth(V, A)
+    Qo, Ro = oracle.householder_qr(p.A.numpy())
+    np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+    np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=TOL_Q * np.abs(Ro).max())
+
+
+def test_minimal_rows(tho):
+    """n = k0 + k: a single leaf holding exactly k rows."""
+    _cmp(tho, inputs.random_problem(48, 16, 32, seed=4))
+
+
+def test_deterministic(tho):
+    p = inputs.random_problem(50000, 32, 8, seed=8)
+    a = _run(tho, p)[0]
+    b = _run(tho, p)[0]
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_rank_deficient_small(tho, dtype):
+    """C3 structure (half of A in Range(V) + 1e-14 noise), oracle-size: invariants."""
+    from gpu_metrics import loo, resid_fro
+    p = inputs.config_problem(3, n=20000, dtype=dtype)
+    dev = torch.device("cuda")
+    V, A = p.V.to(dev), p.A.to(dev)
+    Q, R, S = tho.orth(V, A)
+    assert loo(V, Q) < TOL_LOO
+    assert resid_fro(V, A, Q, R, S) < TOL_LOO
+
+
+def test_config2_full_size(tho):
+    """C2: n=2^20, k0=64, k=16, cond([V,A]) ~ 1e10: LOO and residual <= 1e-13;
+    S = V^*A matches the oracle (Q itself is only defined to ~u*cond)."""
+    from gpu_metrics import loo, resid_fro
+    p = inputs.config_problem(2, device="cuda")
+    Q, R, S = tho.orth(p.V, p.A)
+    assert loo(p.V, Q) < TOL_LOO
+    assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO
+    Sref = (p.V.conj().T @ p.A)
+    assert float((S - Sref).abs().max()) < 1e-12 * float(Sref.abs().max())
+
+
+def test_config3_full_size_fp64(tho):
+    """C3: complex128, n=2^22, k0=128, k=32, numerically rank deficient."""
+    from gpu_metrics import loo, resid_fro
+    p = inputs.config_problem(3, device="cuda")
+    Q, R, S = tho.orth(p.V, p.A)
+    assert loo(p.V, Q) < TOL_LOO
+    assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_fp32_bulk_variant(tho, dtype):
+    """FP32-bulk: loss of orthogonality <= 1e-5 against the FP64 oracle's bound."""
+    p = inputs.random_problem(30000, 32, 16, dtype=dtype, seed=12)
+    Q, R, S = _run(tho, p, prec=tho.THO_PREC_FP32_BULK)
+    Qo, _, _ = oracle.two_stage(p.V.numpy(), p.A.numpy())
+    assert loo_np(p.V.numpy(), Q) < 1e-5
+    assert np.abs(Q - Qo).max() < 1e-3

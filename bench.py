@@ -1,0 +1,397 @@
+"""Benchmark of the two-stage Householder orthogonalization on GB300.
+
+One step = one orthogonalization (Algorithm 1, second choice of P, every
+phase from the QR of V_{1:k0,:} to the explicit Q) of a resident synthetic
+problem.  Default workload: complex128, n = 2^22, k0 = 128, k = 32, half of
+A numerically in Range(V) (the n = 2^22 configuration of the headline metric).
+
+Metric: GB/s of algorithmic bytes B_alg = s n (3 k0 + 4 k) per orthogonalization
+(s = 16 bytes for complex128, 8 for real): three sweeps over V and A forced by
+the three global reductions of Algorithm 1 (W^* A, the trailing QR's R, and
+W^* [0; Qbar]), plus the write of Q.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c3-fp32|c2|c1]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Multi-GPU (torchrun): replicas only -- every rank orthogonalizes its own
+independent problem (block Krylov solvers issue independent orthogonalizations);
+there is no collective on the data path.  value = total bytes of all ranks /
+the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "two-stage HHQR GB/s (% HBM roof) at n=2^22; batched & fwd+bwd vs looped plain"
+UNIT = "GB/s"
+# FP64 FMA peak of one GB300 measured by the committed probe
+# (paper_2602_14449_gb300/csrc/peak_probe.cu; profiles/fp64_peak_probe.md):
+# 2 FP64 FMA / clk / SM x 152 SMs x 2.07 GHz = 1.259 TFLOP/s (nominal 1.25); the probe reads
+# 1.04 (DFMA chains) and the streaming kernels sustain 1.23.  The FP64 kernels issue DFMA.
+FP64_PEAK_TFLOPS = 1.259
+FP32_PEAK_TFLOPS = 78.4
+HBM_GBS_FALLBACK = 6795.1
+
+WORKLOADS = {
+    # name: (config id, n, k0, k, dtype name, prec, description)
+    "c3": (3, 1 << 22, 128, 32, "complex128", 0,
+           "complex128 n=4194304 k0=128 k=32, A=[V C1 + 1e-14 G1, G2] (numerically rank deficient), FP64 path"),
+    "c3-fp32": (3, 1 << 22, 128, 32, "complex128", 1,
+                "complex128 n=4194304 k0=128 k=32, FP32-bulk variant"),
+    "c2": (2, 1 << 20, 64, 16, "float64", 0, "real n=1048576 k0=64 k=16, A=V C + 1e-10 G (cond ~1e10)"),
+    "c1": (1, 4096, 16, 4, "float64", 0, "real n=4096 k0=16 k=4, A=N(0,1)"),
+}
+CPU_SAMPLE_ROWS = {"c3": 65536, "c3-fp32": 65536, "c2": 131072, "c1": 4096}
+REF_STEP_ROWS = {"c3": 16384, "c3-fp32": 16384, "c2": 32768, "c1": 4096}
+
+# Algorithmic real flops per trailing row of each streaming phase (x4 for complex):
+#   gram: V_2^* A_2 (2 k0 k); leaf: A' = A + V_2 Z (2 k0 k), Householder QR
+#   (2 k^2) and explicit leaf Q (2 k^2); apply: Q_leaf F (2 k^2) and V_2^* Qbar
+#   (2 k0 k); update_q: V_2 Z2 (2 k0 k).
+PHASE_FLOPS_PER_ROW = {
+    "gram": lambda k0, k: 2 * k0 * k,
+    "leaf": lambda k0, k: 2 * k0 * k + 4 * k * k,
+    "apply": lambda k0, k: 2 * k * k + 2 * k0 * k,
+    "update_q": lambda k0, k: 2 * k0 * k,
+}
+
+
+def b_alg(n, k0, k, cplx):
+    return (16 if cplx else 8) * n * (3 * k0 + 4 * k)
+
+
+def f_alg(n, k0, k, cplx):
+    return n * (8 * k0 * k + 4 * k * k) * (4 if cplx else 1)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json"
+    except (OSError, KeyError, ValueError):
+        return HBM_GBS_FALLBACK, "fallback"
+
+
+def _traffic_for(kernel: str):
+    """DRAM bytes per trailing row of `kernel` from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    src = os.path.join(ROOT, "paper_2602_14449_gb300", "csrc", "tho_kernels.cuh")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+            if f.get("kernel") == kernel and f.get("src") == h:
+                return float(f["bytes_per_row"])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(wl: str, rows: int):
+    """The CPU oracle (single-threaded, as it stands) on `rows` rows of the workload."""
+    import oracle
+    from paper_2602_14449_gb300 import inputs
+    cid, _, k0, k, dt, _, _ = WORKLOADS[wl]
+    import torch
+    p = inputs.config_problem(cid, n=rows, dtype=getattr(torch, dt))
+    V, A = p.V.numpy(), p.A.numpy()
+    t0 = time.perf_counter()
+    oracle.two_stage(V, A)
+    dt_s = time.perf_counter() - t0
+    gbs = b_alg(rows, k0, k, dt == "complex128") / dt_s / 1e9
+    return {"value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{rows} rows of the same workload (same k0, k, structure), one call, {dt_s:.2f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if ws > 1 and rank != 0:
+        return 0
+    import oracle
+    import torch
+    from paper_2602_14449_gb300 import inputs
+    wl = args.workload
+    cid, n, k0, k, dt, prec, desc = WORKLOADS[wl]
+    rows = REF_STEP_ROWS[wl]
+    p = inputs.config_problem(cid, n=rows, dtype=getattr(torch, dt))
+    V, A = p.V.numpy(), p.A.numpy()
+    for _ in range(args.warmup):
+        oracle.two_stage(V, A)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.two_stage(V, A)
+    el = time.perf_counter() - t0
+    cplx = dt == "complex128"
+    val = b_alg(rows, k0, k, cplx) * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx else "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "reference_sample_rows": rows, "oracle": "CPU oracle (plain C++ loops), 1 thread"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one oracle call on {rows} rows of the workload"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2602_14449_gb300 import inputs, tho
+    tho.load()
+    wl = args.workload
+    cid, n, k0, k, dt, prec, desc = WORKLOADS[wl]
+    if args.rows:
+        n = args.rows
+        desc = desc.replace(f"n={WORKLOADS[wl][1]}", f"n={n}")
+    cplx = dt == "complex128"
+    p = inputs.config_problem(cid, n=n, device=dev)
+    V, A = p.V, p.A
+    plan = tho.Plan([(n, k0, k)], V.dtype, prec, 0)
+    Q = torch.empty_strided((n, k), (1, n), dtype=V.dtype, device=dev)
+    R = torch.empty_strided((k, k), (1, k), dtype=V.dtype, device=dev)
+    S = torch.empty_strided((k0, k), (1, k0), dtype=V.dtype, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        tho.orth(V, A, prec=prec, plan=plan, Q=Q, R=R, S=S)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index)).split(",")[0] if ws == 1 else str(local)
+    sampler = ClockSampler(smi_index)
+    plan.set_phase_timing(True)
+    plan.read_phase_timing()
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier()
+    el_ms = e0.elapsed_time(e1)
+    phases = plan.read_phase_timing()
+    plan.set_phase_timing(False)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    ms_step = el_ms / args.steps
+    B = b_alg(n, k0, k, cplx)
+    value = B * ws * args.steps / (el_ms * 1e-3) / 1e9
+
+    # Roofline of the dominant streaming kernel (FP64-ALU bound on GB300).
+    m = n - k0
+    dom = max(PHASE_FLOPS_PER_ROW, key=lambda ph: phases[ph][0])
+    dom_ms, dom_groups = phases[dom]
+    flops_launch = PHASE_FLOPS_PER_ROW[dom](k0, k) * m * (4 if cplx else 1)
+    achieved = flops_launch / (dom_ms / dom_groups * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS if prec == 0 else FP32_PEAK_TFLOPS
+    tr_row = _traffic_for({"gram": "k_gram", "leaf": "k_leaf", "apply": "k_apply_gram",
+                           "update_q": "k_update_q"}[dom])
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": (tr_row * m if tr_row is not None else None), "kernel": {"gram": "k_gram", "leaf": "k_leaf",
+                "apply": "k_apply_gram", "update_q": "k_update_q"}[dom],
+                "peak_source": ("2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal; probe 1.04, k_gram sustains 1.23)" if prec == 0
+                                else "FP32 FFMA measured by peak_probe (of measured)")}
+    hbm, hbm_src = _hbm_peak()
+    step_tflops = f_alg(n, k0, k, cplx) / (ms_step * 1e-3) / 1e12
+
+    # End to end through the C ABI with host buffers (pinned), copies in the timed region.
+    e2e = None
+    if not args.no_e2e:
+        hV = torch.empty_like(V, device="cpu").pin_memory()
+        hA = torch.empty_like(A, device="cpu").pin_memory()
+        hV.copy_(V)
+        hA.copy_(A)
+        hQ = torch.empty_strided((n, k), (1, n), dtype=V.dtype).pin_memory()
+        hR = torch.empty_strided((k, k), (1, k), dtype=V.dtype).pin_memory()
+        hS = torch.empty_strided((k0, k), (1, k0), dtype=V.dtype).pin_memory()
+        dV = torch.empty_strided(V.shape, V.stride(), dtype=V.dtype, device=dev)
+        dA = torch.empty_strided(A.shape, A.stride(), dtype=V.dtype, device=dev)
+        ne2e = max(1, min(args.steps, 3))
+
+        def e2e_step():
+            dV.copy_(hV, non_blocking=True)
+            dA.copy_(hA, non_blocking=True)
+            tho.orth(dV, dA, prec=prec, plan=plan, Q=Q, R=R, S=S)
+            hQ.copy_(Q, non_blocking=True)
+            hR.copy_(R, non_blocking=True)
+            hS.copy_(S, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(ne2e):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = f0.elapsed_time(f1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        esz = V.element_size()
+        e2e = {"value": B * ws * ne2e / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int((V.numel() + A.numel()) * esz),
+               "d2h_bytes_per_step": int((n * k + k * k + k0 * k) * esz), "steps": ne2e,
+               "ms_per_step": e2e_ms / ne2e}
+        del hV, hA, dV, dA
+
+    # Accuracy of the benchmarked output (outside the timed region).
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    check = {}
+    try:
+        import gpu_metrics
+        Qc, Rc, Sc = tho.orth(V, A, prec=prec, plan=plan)
+        check = {"loo": gpu_metrics.loo(V, Qc), "resid_fro": gpu_metrics.resid_fro(V, A, Qc, Rc, Sc)}
+    except Exception as ex:  # the metric helper is optional for the bench line
+        check = {"error": str(ex)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, CPU_SAMPLE_ROWS[wl])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": ("c128" if cplx else "f64") + ("/fp32-bulk" if prec else ""),
+            "data": "synthetic",
+            "config": {"workload": desc, "n": n, "k0": k0, "k": k,
+                       "l2": f"inputs larger than L2 ({(V.numel() + A.numel()) * V.element_size() / 1e9:.1f} GB)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roofline,
+            "hbm_roof": {"peak_gbs": hbm, "source": hbm_src, "frac_of_hbm": value / ws / hbm},
+            "fp64_step": {"tflops": step_tflops, "frac_of_fp64_peak": step_tflops / FP64_PEAK_TFLOPS,
+                          "F_alg": f_alg(n, k0, k, cplx), "B_alg": B},
+            "columns_per_s": k * ws * args.steps / (el_ms * 1e-3),
+            "phases_ms_per_step": {ph: v[0] / args.steps for ph, v in phases.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": plan.kernel_launches * args.steps, "check": check,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--rows", type=int, default=0, help="override n (smaller problem of the same structure)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -145,6 +145,31 @@ tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, cons
                                int64_t lddq, void* dV, int64_t lddv, void* dA, int64_t ldda,
                                void* stream);
 
+/* Phase tracing (off by default).  The phases of one call, in launch order:
+ *   0 qr_v1     QR of V_{1:k0,:}, T and Wtop          (Section 3.2, choice 2)
+ *   1 gram      split-n partial sums of V_2^* A_2      (Algorithm 1, A <- H^* A)
+ *   2 solve_z   G = W^* A, Z = T^{-*} G, S             (Algorithm 1, A <- H^* A; S)
+ *   3 leaf      A' = A + V_2 Z and leaf Householder QR (Algorithm 1, QR of A')
+ *   4 tree_up   TSQR tree over the leaf R factors      (Algorithm 1, QR of A')
+ *   5 root      R with real nonnegative diagonal
+ *   6 tree_down per-leaf factors of the tree's Q
+ *   7 apply     Qbar = Q_leaf F and V_2^* Qbar partials (Algorithm 1, Q <- H [0; Qbar])
+ *   8 solve_z2  Z2 = T^{-1} G2, head rows of Q
+ *   9 update_q  Q_2 = Qbar + V_2 Z2
+ * While enabled, every tho_orth call records a CUDA event pair around each
+ * phase on the call's stream (tho_orth_batched is not traced). */
+#define THO_NUM_PHASES 10
+tho_status_t tho_plan_set_phase_timing(tho_plan_t plan, int32_t enable);
+
+/* Accumulated device time (ms) and launch groups per phase of every traced
+ * call since tracing was enabled or last read; waits for the recorded events,
+ * then resets the accumulators.  ms and groups have THO_NUM_PHASES entries
+ * (either may be NULL). */
+tho_status_t tho_plan_read_phase_timing(tho_plan_t plan, double* ms, int32_t* groups);
+
+/* Static name of phase i (0 <= i < THO_NUM_PHASES), else NULL. */
+const char* tho_phase_name(int32_t phase);
+
 /* Read and clear the plan's device status word (synchronizes the device).
  * Returns THO_OK or the first device-detected error (THO_ERR_NONFINITE). */
 tho_status_t tho_plan_status(tho_plan_t plan);

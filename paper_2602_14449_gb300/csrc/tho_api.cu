@@ -27,6 +27,11 @@ struct tho_plan_s {
   bool io_ev_recorded = false;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // phase tracing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;   // pairs: ev[2i] start, ev[2i+1] stop
+  std::vector<int> ev_phase;     // phase of pair i
+  size_t ev_used = 0;            // pairs recorded since the last read
 };
 
 namespace {
@@ -50,6 +55,7 @@ tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
 
 void free_plan(tho_plan_s* p) {
   if (!p) return;
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->io_ev) cudaEventDestroy(p->io_ev);
@@ -72,9 +78,62 @@ tho_status_t check_io(const Inst& I, size_t elem, const void* V, int64_t ldv, co
   return THO_OK;
 }
 
+void phase_hook(void* ctx, int phase, int end, cudaStream_t st) {
+  tho_plan_s* p = static_cast<tho_plan_s*>(ctx);
+  if (!end) {
+    if (p->ev_used * 2 >= p->ev.size()) {
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+      p->ev.push_back(a);
+      p->ev.push_back(b);
+      p->ev_phase.push_back(phase);
+    }
+    p->ev_phase[p->ev_used] = phase;
+    cudaEventRecord(p->ev[2 * p->ev_used], st);
+  } else {
+    if (p->ev_used * 2 >= p->ev.size()) return;
+    cudaEventRecord(p->ev[2 * p->ev_used + 1], st);
+    ++p->ev_used;
+  }
+}
+
+const char* const kPhaseNames[tho::kNumPhases] = {"qr_v1", "gram", "solve_z", "leaf", "tree_up",
+                                                 "root", "tree_down", "apply", "solve_z2", "update_q"};
+
 }  // namespace
 
 extern "C" {
+
+const char* tho_phase_name(int32_t phase) {
+  return (phase >= 0 && phase < tho::kNumPhases) ? kPhaseNames[phase] : nullptr;
+}
+
+tho_status_t tho_plan_set_phase_timing(tho_plan_t plan, int32_t enable) {
+  if (!plan) return THO_ERR_ARG;
+  plan->timing = enable != 0;
+  plan->ev_used = 0;
+  return THO_OK;
+}
+
+tho_status_t tho_plan_read_phase_timing(tho_plan_t plan, double* ms, int32_t* groups) {
+  if (!plan) return THO_ERR_ARG;
+  double acc[tho::kNumPhases] = {0};
+  int32_t cnt[tho::kNumPhases] = {0};
+  for (size_t i = 0; i < plan->ev_used; ++i) {
+    float t = 0.f;
+    if (cudaEventSynchronize(plan->ev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, plan->ev[2 * i], plan->ev[2 * i + 1]) != cudaSuccess)
+      return THO_ERR_CUDA;
+    acc[plan->ev_phase[i]] += t;
+    cnt[plan->ev_phase[i]] += 1;
+  }
+  plan->ev_used = 0;
+  for (int i = 0; i < tho::kNumPhases; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (groups) groups[i] = cnt[i];
+  }
+  return THO_OK;
+}
 
 const char* tho_status_string(tho_status_t s) {
   switch (s) {
@@ -272,7 +331,12 @@ tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A
   tho_status_t s = check_io(I, plan->L->elem, V, ldv, A, lda, Q, ldq, R, S);
   if (s != THO_OK) return s;
   Io io0{V, A, Q, R, S, ldv, lda, ldq};
-  if (plan->L->run(plan->pc, nullptr, io0, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+  tho::PhaseHook hook;
+  if (plan->timing) {
+    hook.fn = &phase_hook;
+    hook.ctx = plan;
+  }
+  if (plan->L->run(plan->pc, nullptr, io0, reinterpret_cast<cudaStream_t>(stream), hook) != cudaSuccess)
     return THO_ERR_CUDA;
   return THO_OK;
 }
@@ -298,7 +362,7 @@ tho_status_t tho_orth_batched(tho_plan_t plan, const tho_instance_t* inst, int32
     const Io none{};
     if (cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return THO_ERR_CUDA;
-    cudaError_t er = plan->L->run(plan->pc, plan->d_io, none, plan->cap_stream);
+    cudaError_t er = plan->L->run(plan->pc, plan->d_io, none, plan->cap_stream, tho::PhaseHook{});
     cudaError_t ec = cudaStreamEndCapture(plan->cap_stream, &g);
     if (er != cudaSuccess || ec != cudaSuccess || !g) {
       if (g) cudaGraphDestroy(g);

@@ -43,30 +43,52 @@ cudaError_t configure_impl(PlanCore& pc) {
 }
 
 template <class S, class B>
-cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStream_t st) {
+cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStream_t st, const PhaseHook& hk) {
   const WorkItem* items = reinterpret_cast<const WorkItem*>(pc.d_items);
   const Inst* insts = pc.d_insts;
   void* ws = pc.ws;
   const dim3 blk(kThreads);
   if (pc.any_k0) {
+    hk(kPhQrV1, 0, st);
     k_v1qr<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws);
-    if (pc.tab.gram_n > 0)
+    hk(kPhQrV1, 1, st);
+    if (pc.tab.gram_n > 0) {
+      hk(kPhGram, 0, st);
       k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
+      hk(kPhGram, 1, st);
+    }
+    hk(kPhSolveZ, 0, st);
     k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
+    hk(kPhSolveZ, 1, st);
   }
+  hk(kPhLeaf, 0, st);
   k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P);
+  hk(kPhLeaf, 1, st);
+  hk(kPhTreeUp, 0, st);
   for (int l = 1; l <= pc.Lmax; ++l)
     if (pc.tab.lev_n[l] > 0)
       k_tree_up<S><<<pc.tab.lev_n[l], blk, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+  hk(kPhTreeUp, 1, st);
+  hk(kPhRoot, 0, st);
   k_root<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
+  hk(kPhRoot, 1, st);
+  hk(kPhTreeDown, 0, st);
   for (int l = pc.Lmax; l >= 1; --l)
     if (pc.tab.lev_n[l] > 0)
       k_tree_down<S><<<pc.tab.lev_n[l], blk, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+  hk(kPhTreeDown, 1, st);
+  hk(kPhApply, 0, st);
   k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws);
+  hk(kPhApply, 1, st);
   if (pc.any_k0) {
+    hk(kPhSolveZ2, 0, st);
     k_solve_z2<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
-    if (pc.tab.upd_n > 0)
+    hk(kPhSolveZ2, 1, st);
+    if (pc.tab.upd_n > 0) {
+      hk(kPhUpdateQ, 0, st);
       k_update_q<S, B><<<pc.tab.upd_n, blk, pc.smem_upd, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws);
+      hk(kPhUpdateQ, 1, st);
+    }
   }
   return cudaGetLastError();
 }

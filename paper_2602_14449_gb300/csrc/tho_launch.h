@@ -45,6 +45,18 @@ struct PlanCore {
   int launches = 0;  // kernel launches per call
 };
 
+// Optional tracing hook: called with (ctx, phase, 0 = begin / 1 = end, stream).
+struct PhaseHook {
+  void (*fn)(void* ctx, int phase, int end, cudaStream_t st) = nullptr;
+  void* ctx = nullptr;
+  void operator()(int phase, int end, cudaStream_t st) const {
+    if (fn) fn(ctx, phase, end, st);
+  }
+};
+
+enum Phase { kPhQrV1 = 0, kPhGram, kPhSolveZ, kPhLeaf, kPhTreeUp, kPhRoot, kPhTreeDown, kPhApply,
+             kPhSolveZ2, kPhUpdateQ, kNumPhases };
+
 struct Launcher {
   size_t elem;       // bytes of the FP64 storage type
   size_t bulk_elem;  // bytes of the bulk arithmetic type
@@ -52,7 +64,7 @@ struct Launcher {
   cudaError_t (*configure)(PlanCore& pc);
   // Enqueue every kernel of one call on `st`.  d_io: device Io table (batched)
   // or nullptr (single problem, pointers in io0).
-  cudaError_t (*run)(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStream_t st);
+  cudaError_t (*run)(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStream_t st, const PhaseHook& hook);
 };
 
 extern const Launcher kLaunchF64;       // real, FP64

@@ -1,8 +1,8 @@
 """Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
 
 This module holds no arithmetic of the orthogonalization method: it only draws
-random matrices.  Orthonormal V comes from a library QR (``torch.linalg.qr``) of
-a Gaussian matrix, which is input generation, not the method under test.
+random matrices.  Orthonormal V comes from a library QR (``torch.linalg.qr``, CPU)
+or CholeskyQR2 (GPU) of a Gaussian matrix: input generation, not the method.
 
 Workloads (the shapes of block Krylov orthogonalization, the paper's usage
 mode in Section 1 and Algorithm 3):
@@ -53,10 +53,26 @@ def colmajor(x: torch.Tensor) -> torch.Tensor:
 
 
 def orthonormal(n: int, k0: int, dtype: torch.dtype, g: torch.Generator, device="cpu") -> torch.Tensor:
-    """V = Q factor of a seeded Gaussian n x k0 matrix (library QR), column-major."""
+    """V = Q factor of a seeded Gaussian n x k0 matrix, column-major.
+
+    On the CPU: the library (LAPACK) QR.  On a GPU: CholeskyQR2 -- two rounds
+    of X <- X L^{-*} with G = X^* X = L L^* (Gram by cuBLAS, the k0 x k0
+    Cholesky and triangular inverse on the CPU) -- which for a Gaussian
+    n x k0 matrix (condition ~ 1 + 2 sqrt(k0/n)) gives ||V^* V - I|| ~ u.
+    """
     x = gaussian(n, k0, dtype, g, device)
-    q, _ = torch.linalg.qr(x, mode="reduced")
-    return colmajor(q)
+    if torch.device(device).type == "cpu":
+        q, _ = torch.linalg.qr(x, mode="reduced")
+        return colmajor(q)
+    x = colmajor(x)
+    eye = torch.eye(k0, dtype=dtype)
+    for _ in range(2):
+        G = (x.conj().T @ x).cpu()
+        G = 0.5 * (G + G.conj().T)
+        L = torch.linalg.cholesky(G)
+        Linv = torch.linalg.solve_triangular(L, eye, upper=False)
+        x = colmajor(x @ Linv.conj().T.to(x.device))
+    return x
 
 
 def worked_example(dtype=torch.float64):

@@ -28,7 +28,9 @@ THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE = 0x1, 0x2
 THO_MAX_K0, THO_MAX_K = 128, 32
 
 EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",
-            "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string")
+            "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
+            "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name")
+THO_NUM_PHASES = 10
 
 
 class ThoError(RuntimeError):
@@ -82,6 +84,12 @@ def load(path: str | None = None):
         lib.tho_plan_status.restype = ctypes.c_int
         lib.tho_status_string.argtypes = [ctypes.c_int]
         lib.tho_status_string.restype = ctypes.c_char_p
+        lib.tho_plan_set_phase_timing.argtypes = [vp, i32]
+        lib.tho_plan_set_phase_timing.restype = ctypes.c_int
+        lib.tho_plan_read_phase_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        lib.tho_plan_read_phase_timing.restype = ctypes.c_int
+        lib.tho_phase_name.argtypes = [i32]
+        lib.tho_phase_name.restype = ctypes.c_char_p
         _lib = lib
         return lib
 
@@ -152,6 +160,17 @@ class Plan:
     def status(self) -> int:
         return load().tho_plan_status(self.handle)
 
+    def set_phase_timing(self, enable: bool = True):
+        _check(load().tho_plan_set_phase_timing(self.handle, int(enable)), "tho_plan_set_phase_timing")
+
+    def read_phase_timing(self):
+        """{phase name: (ms summed over traced calls, launch groups)} since the last read."""
+        lib = load()
+        ms = (ctypes.c_double * THO_NUM_PHASES)()
+        gr = (ctypes.c_int32 * THO_NUM_PHASES)()
+        _check(lib.tho_plan_read_phase_timing(self.handle, ms, gr), "tho_plan_read_phase_timing")
+        return {lib.tho_phase_name(i).decode(): (ms[i], gr[i]) for i in range(THO_NUM_PHASES)}
+
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
             _lib.tho_plan_destroy(self.handle)
@@ -185,12 +204,14 @@ def _ptr(x):
 
 
 def orth(V: torch.Tensor, A: torch.Tensor, prec: int = THO_PREC_FP64, want_R: bool = True,
-         want_S: bool = True, flags: int = 0, plan: Plan | None = None, Q: torch.Tensor | None = None):
+         want_S: bool = True, flags: int = 0, plan: Plan | None = None, Q: torch.Tensor | None = None,
+         R: torch.Tensor | None = None, S: torch.Tensor | None = None):
     """Algorithm 1 (second choice of P) on the GPU: returns (Q, R, S).
 
     V: n x k0 (orthonormal columns), A: n x k, column-major CUDA tensors of
     dtype float64 or complex128.  R (k x k) and S (k0 x k) are None unless
-    requested.  Runs on the current torch stream.
+    requested.  Q, R, S may be passed preallocated (column-major, R with
+    ld = k, S with ld = k0).  Runs on the current torch stream.
     """
     n, k = A.shape
     k0 = V.shape[1] if V is not None else 0
@@ -204,8 +225,13 @@ def orth(V: torch.Tensor, A: torch.Tensor, prec: int = THO_PREC_FP64, want_R: bo
     if Q is None:
         Q = _empty_cm(n, k, dt, A.device)
     ldq = _ld(Q, "Q")
-    R = _empty_cm(k, k, dt, A.device) if want_R else None
-    S = _empty_cm(k0, k, dt, A.device) if (want_S and k0 > 0) else None
+    if R is None and want_R:
+        R = _empty_cm(k, k, dt, A.device)
+    if S is None and want_S and k0 > 0:
+        S = _empty_cm(k0, k, dt, A.device)
+    for x, nm, ld in ((R, "R", k), (S, "S", k0)):
+        if x is not None and (x.stride(0) != 1 or (x.shape[1] > 1 and x.stride(1) != ld)):
+            raise ValueError(f"{nm} must be column-major with ld = {ld}")
     p = plan or get_plan([(n, k0, k)], dt, prec, flags)
     st = torch.cuda.current_stream().cuda_stream
     _check(load().tho_orth(p.handle, _ptr(V) if k0 > 0 else None, ldv, _ptr(A), lda, _ptr(Q), ldq,

@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "two-stage HHQR GB/s (% HBM roof) at n=2^22; batched & fwd+bwd vs looped plain"
 UNIT = "GB/s"
-# FP64 FMA peak of one GB300 measured by the committed probe
-# (paper_2602_14449_gb300/csrc/peak_probe.cu; profiles/fp64_peak_probe.md):
+# FP64 FMA peak of one GB300 (roofline denominator of the FP64 path), from the unit
+# count and clock, checked against the committed probe (csrc/peak_probe.cu):
 # 2 FP64 FMA / clk / SM x 152 SMs x 2.07 GHz = 1.259 TFLOP/s (nominal 1.25); the probe reads
 # 1.04 (DFMA chains) and the streaming kernels sustain 1.23.  The FP64 kernels issue DFMA.
 FP64_PEAK_TFLOPS = 1.259

@@ -18,18 +18,27 @@ cudaError_t configure_impl(PlanCore& pc) {
   pc.smem_upd = (size_t)(pc.k0pmax * pc.kpmax + kTileRows * pc.k0pmax) * b;
   pc.smem_leaf = leaf_smem_bytes(pc.P, pc.k0pmax, pc.kpmax, b, sizeof(S));
   pc.smem_tree = (size_t)2 * pc.kmax * pc.kmax * sizeof(S);
-  cudaError_t e;
-  e = cudaFuncSetAttribute(k_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_gram);
+  // The dynamic shared-memory limit is a per-kernel, per-device attribute shared
+  // by every plan: raise it to the device's opt-in maximum (never lower it), so
+  // a plan built later with smaller panels cannot break an earlier one.
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_apply_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_apply);
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_update_q<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_upd);
+  if ((size_t)optin < std::max({pc.smem_gram, pc.smem_apply, pc.smem_upd, pc.smem_leaf, pc.smem_tree}))
+    return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(k_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_leaf<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_leaf);
+  e = cudaFuncSetAttribute(k_apply_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tree_up<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_tree);
+  e = cudaFuncSetAttribute(k_update_q<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tree_down<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_tree);
+  e = cudaFuncSetAttribute(k_leaf<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tree_up<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tree_down<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
   int n = 0;

@@ -144,3 +144,18 @@ def test_fp32_bulk_variant(tho, dtype):
     Qo, _, _ = oracle.two_stage(p.V.numpy(), p.A.numpy())
     assert loo_np(p.V.numpy(), Q) < 1e-5
     assert np.abs(Q - Qo).max() < 1e-3
+
+
+def test_interleaved_plans(tho):
+    """A plan built after another (smaller panels) must not break the first one."""
+    big = inputs.random_problem(9000, 128, 32, dtype=torch.complex128, seed=21)
+    small = inputs.random_problem(600, 8, 4, seed=22)
+    dev = torch.device("cuda")
+    Vb, Ab = big.V.to(dev), big.A.to(dev)
+    Qb1, _, _ = tho.orth(Vb, Ab)
+    Qs, _, _ = tho.orth(small.V.to(dev), small.A.to(dev))
+    Qb2, _, _ = tho.orth(Vb, Ab)
+    torch.cuda.synchronize()
+    assert torch.equal(Qb1, Qb2)
+    Qso, _, _ = oracle.two_stage(small.V.numpy(), small.A.numpy())
+    np.testing.assert_allclose(Qs.cpu().numpy(), Qso, atol=TOL_Q)

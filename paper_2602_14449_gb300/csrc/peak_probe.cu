@@ -18,7 +18,7 @@
   std::fprintf(stderr, "CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
   std::exit(1); } } while (0)
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;
 
 __global__ void probe_dfma(double* out, double x, double y, int iters) {
   double a[kChains];
@@ -147,7 +147,7 @@ int main() {
   double* dout = nullptr;
   CK(cudaMalloc(&dout, nthr * sizeof(double)));
 
-  const int it64 = 4096, it32 = 65536, itmma = 2048;
+  const int it64 = 2048, it32 = 32768, itmma = 2048;
   const int reps = 5;
   float ms_dfma = time_ms([&] { probe_dfma<<<blocks, threads>>>(dout, 0.999999, 1e-9, it64); }, reps);
   CK(cudaGetLastError());

@@ -19,27 +19,28 @@ cudaError_t configure_impl(PlanCore& pc) {
   pc.smem_leaf = leaf_smem_bytes(pc.P, pc.k0pmax, pc.kpmax, b, sizeof(S));
   pc.smem_tree = (size_t)2 * pc.kmax * pc.kmax * sizeof(S);
   // The dynamic shared-memory limit is a per-kernel, per-device attribute shared
-  // by every plan: raise it to the device's opt-in maximum (never lower it), so
-  // a plan built later with smaller panels cannot break an earlier one.
+  // by every plan: raise it to the device's opt-in maximum less the kernel's
+  // static shared memory (never lower it), so a plan built later with smaller
+  // panels cannot break an earlier one.
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  if ((size_t)optin < std::max({pc.smem_gram, pc.smem_apply, pc.smem_upd, pc.smem_leaf, pc.smem_tree}))
-    return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(k_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_apply_gram<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_update_q<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_leaf<S, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tree_up<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tree_down<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e != cudaSuccess) return e;
+  auto raise = [optin](const void* fn, size_t need) -> cudaError_t {
+    cudaFuncAttributes fa;
+    cudaError_t r = cudaFuncGetAttributes(&fa, fn);
+    if (r != cudaSuccess) return r;
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if (need > (size_t)lim) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  };
+  if ((e = raise((const void*)k_gram<S, B>, pc.smem_gram)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_up<S>, pc.smem_tree)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
   int n = 0;
   if (pc.any_k0) n += 3;  // v1qr, gram, solve_z

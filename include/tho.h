@@ -170,6 +170,36 @@ tho_status_t tho_plan_read_phase_timing(tho_plan_t plan, double* ms, int32_t* gr
 /* Static name of phase i (0 <= i < THO_NUM_PHASES), else NULL. */
 const char* tho_phase_name(int32_t phase);
 
+/* tho_orth_noalloc: the same orthogonalization as tho_orth, for callers that
+ * cannot allocate device memory -- code running during a CUDA-graph capture
+ * under a no-allocation policy, latency-critical loops that cannot take
+ * cudaMalloc's implicit device synchronization, and plugins whose host
+ * application owns every byte of device memory through its own pool.  The
+ * paper has no counterpart: this is a deployment variant of Algorithm 1.
+ *
+ * It needs no plan and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  All of its scratch (status word, problem descriptor, work-item
+ * table, partial sums, TSQR factors and solves) lives in one file-scope static
+ * device array of THO_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads
+ * libtho holds until the process exits.  The caller still passes V, A and the
+ * outputs Q, R, S (same meaning, layout and alignment rules as tho_orth);
+ * `desc` describes the problem as for tho_plan (count = 1).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and overwrites
+ * what the previous call left there, so calls whose GPU work overlaps in time
+ * (two streams, two host threads) race: serialize them.  Device-side checks
+ * (THO_FLAG_CHECK_FINITE) are not reported by this entry point.
+ *
+ * Errors: ARG, SHAPE, ALIGN, CUDA as tho_plan/tho_orth; THO_ERR_UNSUPPORTED
+ * when the problem's scratch exceeds THO_NOALLOC_SCRATCH_BYTES (for example
+ * real n = 2^18 with k0 = 64, k = 16 fits; complex n = 2^22 with k0 = 128,
+ * k = 32 does not -- use a plan).  Asynchronous on `stream`. */
+#define THO_NOALLOC_SCRATCH_BYTES (16u << 20)
+tho_status_t tho_orth_noalloc(const tho_desc_t* desc, const void* V, int64_t ldv, const void* A,
+                              int64_t lda, void* Q, int64_t ldq, void* R, void* S, void* stream);
+
 /* Read and clear the plan's device status word (synchronizes the device).
  * Returns THO_OK or the first device-detected error (THO_ERR_NONFINITE). */
 tho_status_t tho_plan_status(tho_plan_t plan);

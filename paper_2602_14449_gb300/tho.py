@@ -29,7 +29,8 @@ THO_MAX_K0, THO_MAX_K = 128, 32
 
 EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
-            "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name")
+            "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
+            "tho_orth_noalloc")
 THO_NUM_PHASES = 10
 
 

@@ -50,9 +50,12 @@ WORKLOADS = {
                 "complex128 n=4194304 k0=128 k=32, FP32-bulk variant"),
     "c2": (2, 1 << 20, 64, 16, "float64", 0, "real n=1048576 k0=64 k=16, A=V C + 1e-10 G (cond ~1e10)"),
     "c1": (1, 4096, 16, 4, "float64", 0, "real n=4096 k0=16 k=4, A=N(0,1)"),
+    "c4": (4, 0, 0, 0, "float64", 0,
+           "batched: 256 real problems, n log-uniform in [16384, 262144], k0 in {8..128}, k in {4..32}, "
+           "one graph replay vs 256 looped tho_orth calls"),
 }
 CPU_SAMPLE_ROWS = {"c3": 65536, "c3-fp32": 65536, "c2": 131072, "c1": 4096}
-REF_STEP_ROWS = {"c3": 16384, "c3-fp32": 16384, "c2": 32768, "c1": 4096}
+REF_STEP_ROWS = {"c3": 16384, "c3-fp32": 16384, "c2": 32768, "c1": 4096, "c4": 16384}
 
 # Algorithmic real flops per trailing row of each streaming phase (x4 for complex):
 #   gram: V_2^* A_2 (2 k0 k); leaf: A' = A + V_2 Z (2 k0 k), Householder QR
@@ -181,6 +184,10 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if ws > 1 and rank != 0:
         return 0
+    if args.workload == "c4":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-problem "
+                          "workloads c1, c2, c3"}), flush=True)
+        return 0
     import oracle
     import torch
     from paper_2602_14449_gb300 import inputs
@@ -208,6 +215,89 @@ def run_reference(args):
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args):
+    """C4: the 256-problem batch as one tho_orth_batched graph replay, against
+    the same problems looped through tho_orth (one plan each)."""
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2602_14449_gb300 import inputs, tho
+    tho.load()
+    shapes = inputs.batched_shapes()
+    probs = inputs.batched_problems(shapes, device=dev)
+    pairs = [(p.V, p.A) for p in probs]
+    outs = [(torch.empty_strided((n, k), (1, n), dtype=torch.float64, device=dev),
+             torch.empty_strided((k, k), (1, k), dtype=torch.float64, device=dev),
+             torch.empty_strided((k0, k), (1, k0), dtype=torch.float64, device=dev)) for (n, k0, k) in shapes]
+    bplan = tho.Plan(shapes, torch.float64)
+    lplans = [tho.Plan([s], torch.float64) for s in shapes]
+    stream = torch.cuda.current_stream(dev)
+
+    def batched():
+        tho.orth_batched(pairs, plan=bplan, outs=outs)
+
+    def looped():
+        for (V, A), pl, (Q, R, S) in zip(pairs, lplans, outs):
+            tho.orth(V, A, plan=pl, Q=Q, R=R, S=S)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / args.steps
+
+    smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index)).split(",")[0] if ws == 1 else str(local)
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    ms_b = timed(batched)
+    clocks = sampler.stop()
+    ms_l = timed(looped)
+    B = sum(b_alg(n, k0, k, False) for (n, k0, k) in shapes)
+    F = sum(f_alg(n, k0, k, False) for (n, k0, k) in shapes)
+    val = B * ws / (ms_b * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c4"][6], "problems": len(shapes),
+                       "rows_total": sum(s[0] for s in shapes), "B_alg": B, "F_alg": F,
+                       "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "batched": {"ms": ms_b, "gbs": B / (ms_b * 1e-3) / 1e9, "tflops": F / (ms_b * 1e-3) / 1e12,
+                        "launches": bplan.kernel_launches},
+            "looped": {"ms": ms_l, "gbs": B / (ms_l * 1e-3) / 1e9, "tflops": F / (ms_l * 1e-3) / 1e12,
+                       "launches": sum(p.kernel_launches for p in lplans)},
+            "speedup_batched_vs_looped": ms_l / ms_b,
+            "clocks": clocks, "gpu_launches": bplan.kernel_launches * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
@@ -390,6 +480,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -159,3 +159,45 @@ def test_interleaved_plans(tho):
     assert torch.equal(Qb1, Qb2)
     Qso, _, _ = oracle.two_stage(small.V.numpy(), small.A.numpy())
     np.testing.assert_allclose(Qs.cpu().numpy(), Qso, atol=TOL_Q)
+
+
+BATCH_SHAPES = [(300, 8, 4), (1000, 16, 8), (5000, 32, 16), (777, 1, 1), (4096, 64, 32), (2000, 128, 8),
+                (50000, 16, 4), (33, 16, 17), (70001, 5, 9)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_batched_matches_oracle(tho, dtype):
+    """tho_orth_batched (one graph replay for the whole batch) against the oracle, per problem."""
+    probs = [inputs.random_problem(n, k0, k, dtype=dtype, seed=40 + i) for i, (n, k0, k) in enumerate(BATCH_SHAPES)]
+    pairs = [(p.V.cuda(), p.A.cuda()) for p in probs]
+    res = tho.orth_batched(pairs)
+    torch.cuda.synchronize()
+    for p, (Q, R, S) in zip(probs, res):
+        Qo, Ro, So = oracle.two_stage(p.V.numpy(), p.A.numpy())
+        np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+        np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=TOL_Q * max(1, np.abs(Ro).max()))
+        np.testing.assert_allclose(S.cpu().numpy(), So, atol=TOL_Q * max(1, np.abs(So).max()))
+    # A second call replays the same graph with new output buffers: same bits.
+    res2 = tho.orth_batched(pairs)
+    torch.cuda.synchronize()
+    for (Q, _, _), (Q2, _, _) in zip(res, res2):
+        assert torch.equal(Q, Q2)
+
+
+def test_batched_c4_workload(tho):
+    """The 256-problem batched workload (n log-uniform in [16384, 262144]): every
+    problem meets LOO and residual <= 1e-13 and matches the looped tho_orth."""
+    from gpu_metrics import loo, resid_fro
+    shapes = inputs.batched_shapes()
+    probs = inputs.batched_problems(shapes, device="cuda")
+    pairs = [(p.V, p.A) for p in probs]
+    res = tho.orth_batched(pairs)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for i, (p, (Q, R, S)) in enumerate(zip(probs, res)):
+        assert loo(p.V, Q) < TOL_LOO, i
+        assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO, i
+        if i % 16 == 0:
+            Ql, _, _ = tho.orth(p.V, p.A)
+            worst = max(worst, float((Ql - Q).abs().max()))
+    assert worst < TOL_Q

@@ -50,6 +50,9 @@ WORKLOADS = {
                 "complex128 n=4194304 k0=128 k=32, FP32-bulk variant"),
     "c2": (2, 1 << 20, 64, 16, "float64", 0, "real n=1048576 k0=64 k=16, A=V C + 1e-10 G (cond ~1e10)"),
     "c1": (1, 4096, 16, 4, "float64", 0, "real n=4096 k0=16 k=4, A=N(0,1)"),
+    "c5": (5, 1 << 20, 64, 16, "float64", 0,
+           "differentiation: real n=1048576 k0=64 k=16, A=N(0,1), dQ=N(0,1); fused forward+adjoint vs "
+           "autograd through a GPU torch-ops composition of Algorithm 1"),
     "c4": (4, 0, 0, 0, "float64", 0,
            "batched: 256 real problems, n log-uniform in [16384, 262144], k0 in {8..128}, k in {4..32}, "
            "one graph replay vs 256 looped tho_orth calls"),
@@ -184,7 +187,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if ws > 1 and rank != 0:
         return 0
-    if args.workload == "c4":
+    if args.workload in ("c4", "c5"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-problem "
                           "workloads c1, c2, c3"}), flush=True)
         return 0
@@ -298,6 +301,118 @@ def run_batched(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def _torch_composition(V, A):
+    """Algorithm 1 (choice 2 of P) as plain differentiable torch ops on the GPU:
+    the comparator of the fused forward+adjoint (autograd through every step)."""
+    import torch
+    n, k0 = V.shape
+
+    def hh(X):
+        m, k = X.shape
+        R, vs, bs = X, [], []
+        for j in range(k):
+            x = R[j:, j]
+            alpha = torch.sqrt((x * x).sum())
+            sg = torch.where(x[0] < 0, -1.0, 1.0)
+            v = torch.cat([x[:1] + sg * alpha, x[1:]])
+            b = 2.0 / (v * v).sum()
+            R = torch.cat([R[:j], R[j:] - b * torch.outer(v, v @ R[j:])], 0)
+            vs.append(v)
+            bs.append(b)
+        Qx = torch.eye(m, k, dtype=X.dtype, device=X.device)
+        for j in reversed(range(k)):
+            Qx = torch.cat([Qx[:j], Qx[j:] - bs[j] * torch.outer(vs[j], vs[j] @ Qx[j:])], 0)
+        d = torch.where(torch.diagonal(R[:k]) < 0, -1.0, 1.0)
+        return Qx * d, d[:, None] * torch.triu(R[:k])
+
+    def solve_tri(Tm, B, lower):
+        rows = [None] * Tm.shape[0]
+        order = range(Tm.shape[0]) if lower else range(Tm.shape[0] - 1, -1, -1)
+        for i in order:
+            s = B[i]
+            for j in (range(i) if lower else range(i + 1, Tm.shape[0])):
+                s = s - Tm[i, j] * rows[j]
+            rows[i] = s / Tm[i, i]
+        return torch.stack(rows, 0)
+
+    Q1, R1 = hh(V[:k0])
+    T = torch.eye(k0, dtype=V.dtype, device=V.device) + R1.T
+    W = torch.cat([-Q1, torch.zeros(n - k0, k0, dtype=V.dtype, device=V.device)], 0) - V
+    Z = solve_tri(T.T, W.T @ A, lower=False)
+    Ap = A - W @ Z
+    Qb, _ = hh(Ap[k0:])
+    E = torch.cat([torch.zeros(k0, A.shape[1], dtype=A.dtype, device=A.device), Qb], 0)
+    Z2 = solve_tri(T, W.T @ E, lower=True)
+    return E - W @ Z2
+
+
+def run_adjoint(args):
+    """C5: forward + hand-written adjoint through the C ABI (autograd.Function),
+    against autograd through the torch-ops composition on the same GPU."""
+    import torch
+    ws, rank, local = _dist()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2602_14449_gb300 import inputs, tho
+    from paper_2602_14449_gb300.autograd import two_stage_orth
+    tho.load()
+    cid, n, k0, k, dt, prec, desc = WORKLOADS["c5"]
+    p = inputs.config_problem(5, device=dev)
+    V0, A0, dQ = p.V, p.A, p.dQ
+    stream = torch.cuda.current_stream(dev)
+
+    def fused():
+        V = V0.detach().requires_grad_()
+        A = A0.detach().requires_grad_()
+        two_stage_orth(V, A).backward(dQ)
+        return V.grad, A.grad
+
+    def composed():
+        V = V0.detach().clone().requires_grad_()
+        A = A0.detach().clone().requires_grad_()
+        _torch_composition(V, A).backward(dQ)
+        return V.grad, A.grad
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index)).split(",")[0]
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    ms_f = timed(fused, args.steps, args.warmup)
+    clocks = sampler.stop()
+    plan = tho.get_plan([(n, k0, k)], torch.float64)
+    ms_fwd = timed(lambda: tho.orth(V0, A0, plan=plan), args.steps, 1)
+    ms_c = timed(composed, 1, 1)
+    gVf, gAf = fused()
+    gVc, gAc = composed()
+    agree = max(float((gVf - gVc).abs().max() / gVc.abs().max()), float((gAf - gAc).abs().max() / gAc.abs().max()))
+    B = b_alg(n, k0, k, False)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": B / (ms_f * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "k0": k0, "k": k, "value_is": "B_alg of one forward / (forward+backward time)"},
+            "fused_fwd_bwd_ms": ms_f, "forward_only_ms": ms_fwd, "backward_ms": ms_f - ms_fwd,
+            "torch_composition_fwd_bwd_ms": ms_c, "speedup_fused_vs_composition": ms_c / ms_f,
+            "grad_rel_diff_fused_vs_composition": agree, "clocks": clocks,
+            "gpu_launches": (plan.kernel_launches + 10) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -482,6 +597,8 @@ def main():
         return run_reference(args)
     if args.workload == "c4":
         return run_batched(args)
+    if args.workload == "c5":
+        return run_adjoint(args)
     return run_gpu(args)
 
 

@@ -10,7 +10,7 @@ in ``include/tho.h`` (``libtho.so``); ``paper_2602_14449_gb300.tho`` is the thin
 ctypes binding and ``paper_2602_14449_gb300.autograd`` the autograd wrapper.
 """
 
-__all__ = ["tho", "inputs"]
+__all__ = ["tho", "inputs", "autograd"]
 
 
 def __getattr__(name):

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tho.h"
+#include "tho_backward.h"
 #include "tho_launch.h"
 
 using tho::Inst;
@@ -32,6 +33,8 @@ struct tho_plan_s {
   std::vector<cudaEvent_t> ev;   // pairs: ev[2i] start, ev[2i+1] stop
   std::vector<int> ev_phase;     // phase of pair i
   size_t ev_used = 0;            // pairs recorded since the last read
+  // reverse mode (allocated on the first tho_orth_backward call)
+  tho::BwdState* bwd = nullptr;
 };
 
 namespace {
@@ -56,6 +59,10 @@ tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
 void free_plan(tho_plan_s* p) {
   if (!p) return;
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  if (p->bwd) {
+    tho::backward_free(*p->bwd);
+    delete p->bwd;
+  }
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->io_ev) cudaEventDestroy(p->io_ev);
@@ -382,10 +389,31 @@ tho_status_t tho_orth_batched(tho_plan_t plan, const tho_instance_t* inst, int32
 tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, const void* A, int64_t lda,
                                const void* Q, int64_t ldq, const void* dQ, int64_t lddq, void* dV,
                                int64_t lddv, void* dA, int64_t ldda, void* stream) {
-  (void)V; (void)ldv; (void)A; (void)lda; (void)Q; (void)ldq; (void)dQ; (void)lddq;
-  (void)dV; (void)lddv; (void)dA; (void)ldda; (void)stream;
-  if (!plan) return THO_ERR_ARG;
-  return THO_ERR_UNSUPPORTED;
+  if (!plan || plan->pc.count != 1) return THO_ERR_ARG;
+  const Inst& I = plan->pc.h_insts[0];
+  if (plan->pc.dtype != THO_F64 || plan->pc.prec != THO_PREC_FP64 || I.k0 < 1) return THO_ERR_UNSUPPORTED;
+  if (!V || !A || !Q || !dQ || !dV || !dA) return THO_ERR_ARG;
+  if (ldv < I.n || lda < I.n || ldq < I.n || lddq < I.n || lddv < I.n || ldda < I.n) return THO_ERR_ARG;
+  for (const void* p : {V, A, Q, dQ, (const void*)dV, (const void*)dA})
+    if (reinterpret_cast<uintptr_t>(p) % sizeof(double)) return THO_ERR_ALIGN;
+  if (!plan->bwd) {
+    plan->bwd = new (std::nothrow) tho::BwdState();
+    if (!plan->bwd) return THO_ERR_NOMEM;
+    cudaError_t e = tho::backward_prepare(plan->pc, *plan->bwd);
+    if (e != cudaSuccess) {
+      tho::backward_free(*plan->bwd);
+      delete plan->bwd;
+      plan->bwd = nullptr;
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? THO_ERR_NOMEM : THO_ERR_CUDA;
+    }
+  }
+  tho::BwdIo io{static_cast<const double*>(V), static_cast<const double*>(A), static_cast<const double*>(Q),
+                static_cast<const double*>(dQ), static_cast<double*>(dV), static_cast<double*>(dA),
+                ldv, lda, ldq, lddq, lddv, ldda};
+  if (tho::backward_run(plan->pc, *plan->bwd, io, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return THO_ERR_CUDA;
+  return THO_OK;
 }
 
 tho_status_t tho_plan_status(tho_plan_t plan) {

@@ -478,10 +478,13 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
 // ------------------------------------------------------------------------------
 // a7 (tree, upward): node i of level `lev` combines children 2i, 2i+1 of level
 // lev-1 by a Householder QR of [R_a; R_b].  With both blocks upper triangular,
-// reflector j touches only top row j and bottom rows 0..j.  Reflectors are kept
-// (bottom part k x k upper triangular, top entries, betas) for the downward pass.
+// reflector j touches only top row j and bottom rows 0..j.  One thread owns one
+// trailing column (no cross-thread reductions: every FP64 instruction is useful
+// work).  Reflectors are kept (bottom part k x k upper triangular, top
+// entries, betas) for the downward pass.  Launched with kTreeThreads threads.
+constexpr int kTreeThreads = 64;
 template <class S>
-__global__ void __launch_bounds__(kThreads) k_tree_up(const Inst* insts, const WorkItem* items, void* ws, int lev) {
+__global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, const WorkItem* items, void* ws, int lev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -493,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_up(const Inst* insts, const W
   const int64_t node = I.lev_off[lev] + i;
   S* Rdst = Rn + node * kk;
   if (!two) {
-    for (int e = threadIdx.x; e < kk; e += kThreads) Rdst[e] = Rn[c0 * kk + e];
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) Rdst[e] = Rn[c0 * kk + e];
     return;
   }
   S* X = reinterpret_cast<S*>(smem_raw);  // 2k x k, ld 2k
@@ -501,49 +504,45 @@ __global__ void __launch_bounds__(kThreads) k_tree_up(const Inst* insts, const W
   __shared__ S vtop[kMaxKP];
   __shared__ S rdiag[kMaxKP];
   const int ld = 2 * k;
-  for (int e = threadIdx.x; e < 2 * kk; e += kThreads) {
+  for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
     int r = e % ld, c = e / ld;
     X[e] = (r < k) ? Rn[c0 * kk + r + c * k] : Rn[(c0 + 1) * kk + (r - k) + c * k];
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+  const int t = threadIdx.x;
   for (int j = 0; j < k; ++j) {
-    if (warp == 0) {
-      double s = 0.0;
-      for (int r = lane; r <= j; r += 32) s += abs2d(X[k + r + j * ld]);
-      s = warp_sum(s);
-      if (lane == 0) {
-        S xj = X[j + j * ld];
-        s += abs2d(xj);
-        double b;
-        S vj, rjj;
-        make_reflector<S>(s, xj, b, vj, rjj);
-        beta_s[j] = b;
-        vtop[j] = vj;
-        rdiag[j] = rjj;
-      }
+    if (t == 0) {
+      S xj = X[j + j * ld];
+      double s = abs2d(xj);
+      for (int r = 0; r <= j; ++r) s += abs2d(X[k + r + j * ld]);
+      double b;
+      S vj, rjj;
+      make_reflector<S>(s, xj, b, vj, rjj);
+      beta_s[j] = b;
+      vtop[j] = vj;
+      rdiag[j] = rjj;
     }
     __syncthreads();
     const double b = beta_s[j];
-    if (b != 0.0) {
-      for (int c = j + 1 + warp; c < k; c += nw) {
-        S d = zero<S>();
-        for (int r = lane; r <= j; r += 32) d = cmadd(d, X[k + r + j * ld], X[k + r + c * ld]);
-        d = warp_sum(d);
-        d = scale(cmadd(d, vtop[j], X[j + c * ld]), b);
-        for (int r = lane; r <= j; r += 32) X[k + r + c * ld] = msub(X[k + r + c * ld], X[k + r + j * ld], d);
-        if (lane == 0) X[j + c * ld] = msub(X[j + c * ld], vtop[j], d);
-      }
+    const int c = j + 1 + t;
+    if (b != 0.0 && c < k) {
+      S* xc = X + c * ld;
+      const S* xv = X + j * ld;
+      S d = cmadd(zero<S>(), vtop[j], xc[j]);
+      for (int r = 0; r <= j; ++r) d = cmadd(d, xv[k + r], xc[k + r]);
+      d = scale(d, b);
+      xc[j] = msub(xc[j], vtop[j], d);
+      for (int r = 0; r <= j; ++r) xc[k + r] = msub(xc[k + r], xv[k + r], d);
     }
     __syncthreads();
   }
   S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
-  for (int e = threadIdx.x; e < kk; e += kThreads) {
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
     int r = e % k, c = e / k;
     Rdst[e] = (r < c) ? X[r + c * ld] : (r == c ? rdiag[c] : zero<S>());
     ref[e] = (r <= c) ? X[k + r + c * ld] : zero<S>();
   }
-  for (int e = threadIdx.x; e < k; e += kThreads) {
+  for (int e = threadIdx.x; e < k; e += blockDim.x) {
     ref[kk + e] = vtop[e];
     ref[kk + k + e] = from_real<S>(beta_s[e]);
   }
@@ -576,9 +575,10 @@ __global__ void k_root(const Inst* insts, const Io* iot, Io io0, void* ws, int* 
 }
 
 // a7 (tree, downward): parent node i of level `lev` (lev >= 1) gives its children
-// [F_{2i}; F_{2i+1}] = H_0 ... H_{k-1} [F_i; 0].
+// [F_{2i}; F_{2i+1}] = H_0 ... H_{k-1} [F_i; 0].  One thread per column of F; the
+// node's reflectors are staged in shared memory.  Launched with kTreeThreads threads.
 template <class S>
-__global__ void __launch_bounds__(kThreads) k_tree_down(const Inst* insts, const WorkItem* items, void* ws, int lev) {
+__global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, const WorkItem* items, void* ws, int lev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -590,37 +590,39 @@ __global__ void __launch_bounds__(kThreads) k_tree_down(const Inst* insts, const
   S* F = wsp<S>(ws, I.oF);
   const S* Fi = F + node * kk;
   if (!two) {
-    for (int e = threadIdx.x; e < kk; e += kThreads) F[c0 * kk + e] = Fi[e];
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) F[c0 * kk + e] = Fi[e];
     return;
   }
   S* E = reinterpret_cast<S*>(smem_raw);  // 2k x k, ld 2k
+  S* Rf = E + 2 * kk;                     // reflectors: k x k bottom parts | k tops | k betas
   const int ld = 2 * k;
   const S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
-  for (int e = threadIdx.x; e < 2 * kk; e += kThreads) {
+  for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
     int r = e % ld, c = e / ld;
     E[e] = (r < k) ? Fi[r + c * k] : zero<S>();
   }
+  for (int e = threadIdx.x; e < kk + 2 * k; e += blockDim.x) Rf[e] = ref[e];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
-  for (int j = k - 1; j >= 0; --j) {
-    const double b = real_(ref[kk + k + j]);
-    if (b != 0.0) {
-      const S vt = ref[kk + j];
-      for (int c = warp; c < k; c += nw) {
-        S d = zero<S>();
-        for (int r = lane; r <= j; r += 32) d = cmadd(d, ref[r + j * k], E[k + r + c * ld]);
-        d = warp_sum(d);
-        d = scale(cmadd(d, vt, E[j + c * ld]), b);
-        for (int r = lane; r <= j; r += 32) E[k + r + c * ld] = msub(E[k + r + c * ld], ref[r + j * k], d);
-        if (lane == 0) E[j + c * ld] = msub(E[j + c * ld], vt, d);
-      }
+  const int c = threadIdx.x;
+  if (c < k) {
+    S* ec = E + c * ld;
+    for (int j = k - 1; j >= 0; --j) {
+      const double b = real_(Rf[kk + k + j]);
+      if (b == 0.0) continue;
+      const S vt = Rf[kk + j];
+      const S* vb = Rf + j * k;
+      S d = cmadd(zero<S>(), vt, ec[j]);
+      for (int r = 0; r <= j; ++r) d = cmadd(d, vb[r], ec[k + r]);
+      d = scale(d, b);
+      ec[j] = msub(ec[j], vt, d);
+      for (int r = 0; r <= j; ++r) ec[k + r] = msub(ec[k + r], vb[r], d);
     }
-    __syncthreads();
   }
-  for (int e = threadIdx.x; e < kk; e += kThreads) {
-    int r = e % k, c = e / k;
-    F[c0 * kk + e] = E[r + c * ld];
-    F[(c0 + 1) * kk + e] = E[k + r + c * ld];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    int r = e % k, cc = e / k;
+    F[c0 * kk + e] = E[r + cc * ld];
+    F[(c0 + 1) * kk + e] = E[k + r + cc * ld];
   }
 }
 

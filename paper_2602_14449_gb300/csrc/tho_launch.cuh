@@ -17,7 +17,7 @@ cudaError_t configure_impl(PlanCore& pc) {
                                    kRedElems) * b;
   pc.smem_upd = (size_t)(pc.k0pmax * pc.kpmax + kTileRows * pc.k0pmax) * b;
   pc.smem_leaf = leaf_smem_bytes(pc.P, pc.k0pmax, pc.kpmax, b, sizeof(S));
-  pc.smem_tree = (size_t)2 * pc.kmax * pc.kmax * sizeof(S);
+  pc.smem_tree = (size_t)(3 * pc.kmax * pc.kmax + 2 * pc.kmax) * sizeof(S);
   // The dynamic shared-memory limit is a per-kernel, per-device attribute shared
   // by every plan: raise it to the device's opt-in maximum less the kernel's
   // static shared memory (never lower it), so a plan built later with smaller
@@ -77,7 +77,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   hk(kPhTreeUp, 0, st);
   for (int l = 1; l <= pc.Lmax; ++l)
     if (pc.tab.lev_n[l] > 0)
-      k_tree_up<S><<<pc.tab.lev_n[l], blk, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+      k_tree_up<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   hk(kPhTreeUp, 1, st);
   hk(kPhRoot, 0, st);
   k_root<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
@@ -85,7 +85,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   hk(kPhTreeDown, 0, st);
   for (int l = pc.Lmax; l >= 1; --l)
     if (pc.tab.lev_n[l] > 0)
-      k_tree_down<S><<<pc.tab.lev_n[l], blk, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+      k_tree_down<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   hk(kPhTreeDown, 1, st);
   hk(kPhApply, 0, st);
   k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws);

@@ -48,6 +48,10 @@ WORKLOADS = {
            "complex128 n=4194304 k0=128 k=32, A=[V C1 + 1e-14 G1, G2] (numerically rank deficient), FP64 path"),
     "c3-fp32": (3, 1 << 22, 128, 32, "complex128", 1,
                 "complex128 n=4194304 k0=128 k=32, FP32-bulk variant"),
+    "c3-emu": (3, 1 << 22, 128, 32, "complex128", 2,
+               "complex128 n=4194304 k0=128 k=32, FP64-accurate products emulated on bf16 tensor cores"),
+    "c2-emu": (2, 1 << 20, 64, 16, "float64", 2,
+               "real n=1048576 k0=64 k=16, A=V C + 1e-10 G, FP64-accurate products emulated on bf16 tensor cores"),
     "c2": (2, 1 << 20, 64, 16, "float64", 0, "real n=1048576 k0=64 k=16, A=V C + 1e-10 G (cond ~1e10)"),
     "c1": (1, 4096, 16, 4, "float64", 0, "real n=4096 k0=16 k=4, A=N(0,1)"),
     "c5": (5, 1 << 20, 64, 16, "float64", 0,
@@ -57,8 +61,9 @@ WORKLOADS = {
            "batched: 256 real problems, n log-uniform in [16384, 262144], k0 in {8..128}, k in {4..32}, "
            "one graph replay vs 256 looped tho_orth calls"),
 }
-CPU_SAMPLE_ROWS = {"c3": 65536, "c3-fp32": 65536, "c2": 131072, "c1": 4096}
-REF_STEP_ROWS = {"c3": 16384, "c3-fp32": 16384, "c2": 32768, "c1": 4096, "c4": 16384}
+CPU_SAMPLE_ROWS = {"c3": 65536, "c3-fp32": 65536, "c3-emu": 65536, "c2": 131072, "c2-emu": 131072, "c1": 4096}
+REF_STEP_ROWS = {"c3": 16384, "c3-fp32": 16384, "c3-emu": 16384, "c2": 32768, "c2-emu": 32768, "c1": 4096,
+                 "c4": 16384}
 
 # Algorithmic real flops per trailing row of each streaming phase (x4 for complex):
 #   gram: V_2^* A_2 (2 k0 k); leaf: A' = A + V_2 Z (2 k0 k), Householder QR
@@ -488,7 +493,7 @@ def run_gpu(args):
     dom_ms, dom_groups = phases[dom]
     flops_launch = PHASE_FLOPS_PER_ROW[dom](k0, k) * m * (4 if cplx else 1)
     achieved = flops_launch / (dom_ms / dom_groups * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS if prec == 0 else FP32_PEAK_TFLOPS
+    peak = FP32_PEAK_TFLOPS if prec == 1 else FP64_PEAK_TFLOPS
     tr_row = _traffic_for({"gram": "k_gram", "leaf": "k_leaf", "apply": "k_apply_gram",
                            "update_q": "k_update_q"}[dom])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -561,7 +566,7 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": ("c128" if cplx else "f64") + ("/fp32-bulk" if prec else ""),
+            "vs_baseline": None, "dtype": ("c128" if cplx else "f64") + {0: "", 1: "/fp32-bulk", 2: "/bf16-emulated"}[prec],
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "k0": k0, "k": k,
                        "l2": f"inputs larger than L2 ({(V.numel() + A.numel()) * V.element_size() / 1e9:.1f} GB)",

@@ -69,7 +69,14 @@ typedef enum { THO_F64 = 0, THO_C128 = 1 } tho_dtype_t;
  * arithmetic with FP32 accumulation; inputs and outputs stay FP64 in memory;
  * the k0 x k0 QR of V_{1:k0,:}, the T solves, reflector norms and phases and
  * the sums of per-block partials stay FP64. */
-typedef enum { THO_PREC_FP64 = 0, THO_PREC_FP32_BULK = 1 } tho_prec_t;
+/* THO_PREC_FP64_EMU: FP64 accuracy with the split-n products on bf16 tensor
+ * cores.  Each FP64 operand is cut into eight signed 7-bit integer slices
+ * relative to a power-of-two scale shared along the contraction; slice
+ * products accumulate exactly in FP32 and are folded into int64 sums (the
+ * integer-slice splitting of Ozaki et al.).  The normwise error is of the FP64
+ * kind: (contraction length) x 2^-52 x the product of the operand scales.
+ * Inputs must be finite. */
+typedef enum { THO_PREC_FP64 = 0, THO_PREC_FP32_BULK = 1, THO_PREC_FP64_EMU = 2 } tho_prec_t;
 
 #define THO_FLAG_ALLOW_K0_ZERO 0x1u /* k0 = 0: plain Householder QR of A        */
 #define THO_FLAG_CHECK_FINITE 0x2u  /* latch THO_ERR_NONFINITE if G, R or Z2    */

@@ -47,7 +47,7 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
   if (d.dtype != d0.dtype || d.prec != d0.prec || d.flags != d0.flags) return THO_ERR_ARG;
   if (d.dtype != THO_F64 && d.dtype != THO_C128) return THO_ERR_ARG;
-  if (d.prec != THO_PREC_FP64 && d.prec != THO_PREC_FP32_BULK) return THO_ERR_ARG;
+  if (d.prec != THO_PREC_FP64 && d.prec != THO_PREC_FP32_BULK && d.prec != THO_PREC_FP64_EMU) return THO_ERR_ARG;
   if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE)) return THO_ERR_ARG;
   if (d.k < 1 || d.k0 < 0 || d.n < 1) return THO_ERR_SHAPE;
   if (d.k0 == 0 && !(d.flags & THO_FLAG_ALLOW_K0_ZERO)) return THO_ERR_SHAPE;
@@ -172,9 +172,9 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   pc.prec = descs[0].prec;
   pc.flags = descs[0].flags;
   const bool cplx = pc.dtype == THO_C128;
-  const bool b32 = pc.prec == THO_PREC_FP32_BULK;
-  p->L = cplx ? (b32 ? &tho::kLaunchC128Bulk32 : &tho::kLaunchC128)
-              : (b32 ? &tho::kLaunchF64Bulk32 : &tho::kLaunchF64);
+  const bool b32 = pc.prec == THO_PREC_FP32_BULK, emu = pc.prec == THO_PREC_FP64_EMU;
+  p->L = cplx ? (b32 ? &tho::kLaunchC128Bulk32 : (emu ? &tho::kLaunchC128Emu : &tho::kLaunchC128))
+              : (b32 ? &tho::kLaunchF64Bulk32 : (emu ? &tho::kLaunchF64Emu : &tho::kLaunchF64));
   if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return THO_ERR_CUDA; }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
@@ -249,7 +249,8 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
     I.oZ = take(k0 * k);
     I.oZ2 = take(k0 * k);
     I.oG1 = take((int64_t)I.g1 * k0 * k);
-    I.oG3 = take((int64_t)I.g3 * k0 * k);
+    I.np3 = pc.prec == THO_PREC_FP64_EMU ? I.g1 : I.g3;
+    I.oG3 = take((int64_t)std::max(I.g3, I.g1) * k0 * k);
     I.oRn = take(nodes * kk);
     I.oRef = take((nodes - I.nb) * (kk + 2 * k));
     I.oF = take(nodes * kk);

@@ -1,0 +1,266 @@
+// FP64-accurate products on bf16 tensor cores (integer-slice emulation).
+//
+// GB300 runs FP64 FMA at 1.26 TFLOP/s but bf16 warp MMA (mma.sync m16n8k16,
+// FP32 accumulate) at ~600 TFLOP/s.  A product of FP64 matrices is computed
+// exactly enough by the splitting method of Ozaki et al.: every operand value
+// x in a group sharing one power-of-two scale 2^e (|x| < 2^e) is written as a
+// 56-bit fixed-point integer X = trunc(x 2^(56-e)) = sum_{p=1..8} s_p 2^(56-7p)
+// with signed 7-bit slices |s_p| <= 127, each exactly representable in bf16.
+// A slice product s_p t_q is an integer below 2^14, so FP32 accumulation of
+// the products of one "level" L = p + q (at most 8 pairs, 128 contraction
+// steps) stays below 2^24 and is exact (64 steps are used: <= 2^23).  Levels 2..9 are kept (36 slice
+// pairs); the dropped levels weigh <= 2^-63 relative per product, which with
+// the 56-bit slicing leaves a normwise error of the FP64 kind, bounded by
+// (contraction length) x 2^-52 x (scale of the column of x) x (scale of y).
+// After each 64-step block the level sums are folded into two exact int64
+// accumulators (levels 2..5 and 6..9) and converted to FP64 once at the end.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "tho_kernels.cuh"
+
+namespace tho {
+
+constexpr int kEmuSlices = 8;
+constexpr int kEmuLevels = 8;      // levels 2..9
+constexpr int kEmuKT = 64;         // real contraction steps per exact block (and per smem tile)
+constexpr int kEmuMaxLoads = 24;   // staged values per thread per tile: (64 + 32) x 64 / 256
+// Row stride of the slice tiles: 64 + 8 bf16 = 144 bytes, so the 8 row groups
+// of a fragment load fall on distinct banks (bank = 4 g + t).
+constexpr int kEmuLd = kEmuKT + 8;
+
+// Biased exponent field of a double (0 for zero and subnormals).
+__device__ __forceinline__ int dexp(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// Signed slices of x relative to the group's maximal biased exponent emax
+// (|x| < 2^(emax - 1022)), as packed-ready floats.
+__device__ __forceinline__ void emu_split(double x, int emax, float (&s)[kEmuSlices]) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  unsigned long long X = 0;
+  if (e != 0) {
+    const unsigned long long M = (bits & 0xfffffffffffffULL) | 0x10000000000000ULL;
+    const int sh = e - emax + 3;  // <= 3
+    X = sh >= 0 ? (M << sh) : (-sh >= 64 ? 0ULL : (M >> -sh));
+  }
+  const unsigned hi = (unsigned)(X >> 28), lo = (unsigned)(X & 0xfffffffu);
+  const float sg = bits < 0 ? -1.0f : 1.0f;
+  s[0] = sg * (float)((hi >> 21) & 127u);
+  s[1] = sg * (float)((hi >> 14) & 127u);
+  s[2] = sg * (float)((hi >> 7) & 127u);
+  s[3] = sg * (float)(hi & 127u);
+  s[4] = sg * (float)((lo >> 21) & 127u);
+  s[5] = sg * (float)((lo >> 14) & 127u);
+  s[6] = sg * (float)((lo >> 7) & 127u);
+  s[7] = sg * (float)(lo & 127u);
+}
+
+__device__ __forceinline__ unsigned short bf16_bits(float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));  // exact: |v| <= 127 integer
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Complex embedding of the second operand's "imaginary" output columns:
+// from the packed pair (y(2t), y(2t+1)) = (re, im) build (im, -re).
+__device__ __forceinline__ unsigned im_pair(unsigned w) {
+  return ((w >> 16) | (w << 16)) ^ 0x80000000u;
+}
+
+// Fold the 8 level accumulators into the two exact integer accumulators and clear them.
+__device__ __forceinline__ void emu_fold(float (&acc)[kEmuLevels][4], long long (&hi)[4], long long (&lo)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    long long h = (long long)__float2int_rz(acc[0][e]) << 21;
+    h += (long long)__float2int_rz(acc[1][e]) << 14;
+    h += (long long)__float2int_rz(acc[2][e]) << 7;
+    h += (long long)__float2int_rz(acc[3][e]);
+    long long l = (long long)__float2int_rz(acc[4][e]) << 21;
+    l += (long long)__float2int_rz(acc[5][e]) << 14;
+    l += (long long)__float2int_rz(acc[6][e]) << 7;
+    l += (long long)__float2int_rz(acc[7][e]);
+    hi[e] += h;
+    lo[e] += l;
+#pragma unroll
+    for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+  }
+}
+
+// a3 (sweep 1), emulated: partial sums of V_2^* A_2 over one chunk of trailing
+// rows with the products on bf16 tensor cores.  The complex case uses the real
+// embedding along the contraction (row r -> real steps 2r (re), 2r + 1 (im)):
+//   Re G = sum_q X(q, i) Y(q, j),  Im G = sum_q X(q, i) Y~(q, j),
+//   X = V as reals, Y = A as reals, Y~(2r) = Im A, Y~(2r + 1) = -Re A.
+// Output columns n < k are Re G(:, n), n >= k are Im G(:, n - k).
+// Passes over groups of MT 16-row output tiles keep the accumulators in
+// registers (<= 2 tiles per warp).  Shared memory: Vsl [8][MT*16][KT] bf16 |
+// Asl [8][kpe][KT] bf16 | eV [k0p] | eA [kp] (ints).
+// which = 0: X = A, partials to the G1 slots (sweep 1); which = 1: X = Q (holding
+// Qbar after sweep 3a), partials to the G3 slots.
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_gram_emu(const Inst* insts, const Io* iot, Io io0,
+                                                       const WorkItem* items, void* ws, int which) {
+  constexpr bool C = Tr<S>::C;
+  constexpr int RPE = C ? 2 : 1;        // real contraction steps per row
+  constexpr int TR = kEmuKT / RPE;      // rows per tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const Io io = get_io(iot, io0, it.inst);
+  const int k0 = (int)I.k0, k = (int)I.k;
+  const int kpe = (k + 7) / 8 * 8;                // A columns, padded to the 8-wide N tile
+  const int NT = (C ? 2 * kpe : kpe) / 8;         // N tiles (complex: Re block then Im block)
+  const int k0t = (k0 + 15) / 16;                 // 16-row output tiles of G
+  const int MT = max(1, min(k0t, min(4, 16 / NT)));  // output tiles per pass along M (<= 64 rows)
+  const int MB = MT * 16;
+  unsigned short* Vsl = reinterpret_cast<unsigned short*>(smem_raw);
+  unsigned short* Asl = Vsl + kEmuSlices * MB * kEmuLd;
+  int* eV = reinterpret_cast<int*>(Asl + kEmuSlices * kpe * kEmuLd);
+  int* eA = eV + I.k0p + 16;
+  const double* Vd = reinterpret_cast<const double*>(io.V);
+  const double* Ad = reinterpret_cast<const double*>(which ? io.Q : io.A);
+  const int64_t ldv = io.ldv * RPE, lda = (which ? io.ldq : io.lda) * RPE;  // leading dimensions in doubles
+  const int64_t r_begin = I.k0 + (int64_t)it.idx * I.rows1;
+  const int64_t r_end = min64(I.n, r_begin + I.rows1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+
+  // Column scales over the chunk: maximal biased exponent per column.
+  for (int col = warp; col < k0 + k; col += kThreads / 32) {
+    const double* src = col < k0 ? Vd + (int64_t)col * ldv : Ad + (int64_t)(col - k0) * lda;
+    int m = 0;
+    for (int64_t q = r_begin * RPE + lane; q < r_end * RPE; q += 32) m = max(m, dexp(src[q]));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) {
+      if (col < k0) eV[col] = m;
+      else eA[col - k0] = m;
+    }
+  }
+  __syncthreads();
+
+  S* out = wsp<S>(ws, which ? I.oG3 : I.oG1) + (int64_t)it.idx * k0 * k;
+  for (int m0 = 0; m0 < k0t * 16; m0 += MB) {
+    // This warp's output tiles: tile index w and w + 8 of MT x NT.
+    const int ntiles = MT * NT;
+    float acc[2][kEmuLevels][4];
+    long long hi[2][4], lo[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        hi[u][e] = lo[u][e] = 0;
+#pragma unroll
+        for (int L = 0; L < kEmuLevels; ++L) acc[u][L][e] = 0.0f;
+      }
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += TR) {
+      const int nr = (int)min64(TR, r_end - r0);
+      const int nq = nr * RPE;
+      __syncthreads();
+      // Split this pass's V columns and all A columns of the tile into slices:
+      // every load of the tile is issued before the first split so that the
+      // global-memory latency is paid once per tile.
+      const int nv = MB * kEmuKT, ntot = (MB + kpe) * kEmuKT;
+      double val[kEmuMaxLoads];
+#pragma unroll
+      for (int u = 0; u < kEmuMaxLoads; ++u) {
+        const int e = threadIdx.x + u * kThreads;
+        double x = 0.0;
+        if (e < ntot) {
+          const int q = e % kEmuKT;
+          if (q < nq) {
+            if (e < nv) {
+              const int col = m0 + e / kEmuKT;
+              if (col < k0) x = Vd[(int64_t)col * ldv + r0 * RPE + q];
+            } else {
+              const int j = (e - nv) / kEmuKT;
+              if (j < k) x = Ad[(int64_t)j * lda + r0 * RPE + q];
+            }
+          }
+        }
+        val[u] = x;
+      }
+#pragma unroll
+      for (int u = 0; u < kEmuMaxLoads; ++u) {
+        const int e = threadIdx.x + u * kThreads;
+        if (e >= ntot) continue;
+        const int q = e % kEmuKT;
+        float sl[kEmuSlices];
+        if (e < nv) {
+          const int m = e / kEmuKT, col = m0 + m;
+          emu_split(val[u], col < k0 ? eV[col] : 0, sl);
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) Vsl[(p * MB + m) * kEmuLd + q] = bf16_bits(sl[p]);
+        } else {
+          const int j = (e - nv) / kEmuKT;
+          emu_split(val[u], j < k ? eA[j] : 0, sl);
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) Asl[(p * kpe + j) * kEmuLd + q] = bf16_bits(sl[p]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int tile = warp + 8 * u;
+        if (tile >= ntiles) continue;
+        const int mt = tile / NT, nt = tile % NT;
+        const bool imag = C && nt * 8 >= kpe;
+        const int jb = (imag ? nt * 8 - kpe : nt * 8) + g;  // A column of this lane's B fragment
+        for (int ks = 0; ks < kEmuKT; ks += 16) {
+          unsigned bf[kEmuSlices][2];
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            const unsigned* row = reinterpret_cast<const unsigned*>(Asl + (qq * kpe + jb) * kEmuLd + ks);
+            unsigned b0 = row[t4], b1 = row[t4 + 4];
+            if (imag) {
+              b0 = im_pair(b0);
+              b1 = im_pair(b1);
+            }
+            bf[qq][0] = b0;
+            bf[qq][1] = b1;
+          }
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) {
+            const unsigned* ra = reinterpret_cast<const unsigned*>(Vsl + (p * MB + mt * 16 + g) * kEmuLd + ks);
+            const unsigned* rb = reinterpret_cast<const unsigned*>(Vsl + (p * MB + mt * 16 + g + 8) * kEmuLd + ks);
+            const unsigned a0 = ra[t4], a1 = rb[t4], a2 = ra[t4 + 4], a3 = rb[t4 + 4];
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              if (p + qq > kEmuLevels - 1) continue;  // level p + qq + 2 > 9: dropped
+              mma_bf16(acc[u][p + qq], a0, a1, a2, a3, bf[qq][0], bf[qq][1]);
+            }
+          }
+        }
+        emu_fold(acc[u], hi[u], lo[u]);
+      }
+    }
+    // Write this pass's outputs: element (row, col) of the fragment.
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int tile = warp + 8 * u;
+      if (tile >= ntiles) continue;
+      const int mt = tile / NT, nt = tile % NT;
+      const bool imag = C && nt * 8 >= kpe;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = m0 + mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = (imag ? nt * 8 - kpe : nt * 8) + 2 * t4 + (e & 1);
+        if (i >= k0 || j >= k) continue;
+        const int sc = eV[i] + eA[j] - 2044;
+        const double v = ldexp((double)hi[u][e], sc - 35) + ldexp((double)lo[u][e], sc - 63);
+        double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
+        if constexpr (C) o[imag ? 1 : 0] = v;
+        else o[0] = v;
+      }
+    }
+  }
+}
+
+}  // namespace tho

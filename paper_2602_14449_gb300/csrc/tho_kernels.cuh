@@ -628,15 +628,16 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, c
 
 // ------------------------------------------------------------------------------
 // a8 (sweep 3a): for each leaf of a chunk, Qbar_b = Q_leaf,b F_b (in place in Q)
-// and partial sums of V_2^* Qbar.
+// and, with do_gram, partial sums of V_2^* Qbar.
 template <class S, class B>
 __global__ void __launch_bounds__(kThreads) k_apply_gram(const Inst* insts, const Io* iot, Io io0,
-                                                         const WorkItem* items, void* ws) {
+                                                         const WorkItem* items, void* ws, int do_gram) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
   const Io io = get_io(iot, io0, it.inst);
-  const int k0 = (int)I.k0, k = (int)I.k, k0p = I.k0p, kp = I.kp;
+  const int k = (int)I.k, kp = I.kp;
+  const int k0 = do_gram ? (int)I.k0 : 0, k0p = do_gram ? I.k0p : 0;  // k0 = 0: apply F only
   B* Qs = reinterpret_cast<B*>(smem_raw);      // tile of Q_leaf
   B* Qb = Qs + kTileRows * kp;                  // tile of Qbar
   B* Fs = Qb + kTileRows * kp;                  // kp x kp, ld kp
@@ -697,7 +698,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_z2(const Inst* insts, const 
   __shared__ S z[kMaxK0];
   for (int i = threadIdx.x; i < k0; i += kThreads) {
     S s = zero<S>();
-    for (int c = 0; c < I.g3; ++c) s = add(s, Gp[(int64_t)c * k0 * k + i + (int64_t)j * k0]);
+    for (int c = 0; c < I.np3; ++c) s = add(s, Gp[(int64_t)c * k0 * k + i + (int64_t)j * k0]);
     g[i] = neg(s);
   }
   __syncthreads();

@@ -3,14 +3,19 @@
 
 #include <algorithm>
 
+#include "tho_emu.cuh"
 #include "tho_kernels.cuh"
 #include "tho_launch.h"
 
 namespace tho {
 
-template <class S, class B>
+template <class S, class B, bool EMU>
 cudaError_t configure_impl(PlanCore& pc) {
   const size_t b = sizeof(B);
+  {
+    const int kpe = (pc.kmax + 7) / 8 * 8;
+    pc.smem_gram_emu = (size_t)kEmuSlices * kEmuLd * 2 * (64 + kpe) + sizeof(int) * (pc.k0pmax + 16 + pc.kpmax + 16);
+  }
   pc.smem_gram = std::max<size_t>((size_t)kTileRows * (pc.k0pmax + pc.kpmax), kRedElems) * b;
   pc.smem_apply = std::max<size_t>((size_t)(2 * kTileRows * pc.kpmax + pc.kpmax * pc.kpmax +
                                             kTileRows * pc.k0pmax),
@@ -36,6 +41,7 @@ cudaError_t configure_impl(PlanCore& pc) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   };
   if ((e = raise((const void*)k_gram<S, B>, pc.smem_gram)) != cudaSuccess) return e;
+  if (EMU && (e = raise((const void*)k_gram_emu<S>, pc.smem_gram_emu)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
@@ -47,12 +53,13 @@ cudaError_t configure_impl(PlanCore& pc) {
   n += 1;                  // leaf
   for (int l = 1; l <= pc.Lmax; ++l) n += pc.tab.lev_n[l] > 0 ? 2 : 0;
   n += 2;                  // root, apply_gram
+  if (EMU && pc.any_k0) n += 1;  // emulated V_2^* Qbar
   if (pc.any_k0) n += 2;  // solve_z2, update_q
   pc.launches = n;
   return cudaSuccess;
 }
 
-template <class S, class B>
+template <class S, class B, bool EMU>
 cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStream_t st, const PhaseHook& hk) {
   const WorkItem* items = reinterpret_cast<const WorkItem*>(pc.d_items);
   const Inst* insts = pc.d_insts;
@@ -64,7 +71,10 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     hk(kPhQrV1, 1, st);
     if (pc.tab.gram_n > 0) {
       hk(kPhGram, 0, st);
-      k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
+      if (EMU)
+        k_gram_emu<S><<<pc.tab.gram_n, blk, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 0);
+      else
+        k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
       hk(kPhGram, 1, st);
     }
     hk(kPhSolveZ, 0, st);
@@ -88,7 +98,10 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
       k_tree_down<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   hk(kPhTreeDown, 1, st);
   hk(kPhApply, 0, st);
-  k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws);
+  k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws,
+                                                                 EMU ? 0 : 1);
+  if (EMU && pc.any_k0 && pc.tab.gram_n > 0)  // V_2^* Qbar on tensor cores, into the G3 partials
+    k_gram_emu<S><<<pc.tab.gram_n, blk, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 1);
   hk(kPhApply, 1, st);
   if (pc.any_k0) {
     hk(kPhSolveZ2, 0, st);
@@ -103,9 +116,9 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   return cudaGetLastError();
 }
 
-template <class S, class B>
+template <class S, class B, bool EMU = false>
 constexpr Launcher make_launcher() {
-  return Launcher{sizeof(S), sizeof(B), &configure_impl<S, B>, &run_impl<S, B>};
+  return Launcher{sizeof(S), sizeof(B), &configure_impl<S, B, EMU>, &run_impl<S, B, EMU>};
 }
 
 }  // namespace tho

@@ -42,6 +42,7 @@ struct PlanCore {
   size_t ws_elems = 0;
   int* d_status = nullptr;
   size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
+  size_t smem_gram_emu = 0;  // emulated split-n Gram (THO_PREC_FP64_EMU)
   int launches = 0;  // kernel launches per call
 };
 
@@ -71,6 +72,8 @@ extern const Launcher kLaunchF64;       // real, FP64
 extern const Launcher kLaunchF64Bulk32; // real, FP32 bulk
 extern const Launcher kLaunchC128;      // complex, FP64
 extern const Launcher kLaunchC128Bulk32;// complex, FP32 bulk
+extern const Launcher kLaunchF64Emu;    // real, FP64-accurate products on bf16 tensor cores
+extern const Launcher kLaunchC128Emu;   // complex, FP64-accurate products on bf16 tensor cores
 
 // Leaf-kernel shared memory for leaf height P (bytes).
 inline size_t leaf_smem_bytes(int P, int k0p, int kp, size_t bulk, size_t elem) {

@@ -149,7 +149,8 @@ extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int
   I.oZ = take(k0 * k);
   I.oZ2 = take(k0 * k);
   I.oG1 = take((int64_t)I.g1 * k0 * k);
-  I.oG3 = take((int64_t)I.g3 * k0 * k);
+  I.np3 = I.g3;
+  I.oG3 = take((int64_t)std::max(I.g3, I.g1) * k0 * k);
   I.oRn = take(nodes * kk);
   I.oRef = take((nodes - I.nb) * (kk + 2 * k));
   I.oF = take(nodes * kk);

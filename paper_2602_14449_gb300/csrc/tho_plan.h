@@ -35,6 +35,7 @@ struct Inst {
   int32_t nb, L;         // TSQR leaves, tree levels above the leaves
   int32_t g1, g3, g4;    // chunks of sweep 1 (rows), sweep 3a (leaves), sweep 3b (rows)
   int32_t leaves3;       // leaves per sweep-3a chunk
+  int32_t np3;           // partials of V_2^* Qbar summed by k_solve_z2 (g3, or g1 when emulated)
   int64_t rows1, rows4;  // rows per chunk of sweeps 1 and 3b (multiples of kTileRows)
   int64_t oX, oQ1, oR1, oT, oWt, oZ, oZ2, oG1, oG3, oRn, oRef, oF;
   int64_t lev_off[kMaxLevels + 1];  // first node index of each level (R and F arrays)

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtho.so")
 THO_OK, THO_ERR_ARG, THO_ERR_SHAPE, THO_ERR_ALIGN, THO_ERR_NOMEM = 0, 1, 2, 3, 4
 THO_ERR_CUDA, THO_ERR_TIMEOUT, THO_ERR_NONFINITE, THO_ERR_UNSUPPORTED = 5, 6, 7, 8
 THO_F64, THO_C128 = 0, 1
-THO_PREC_FP64, THO_PREC_FP32_BULK = 0, 1
+THO_PREC_FP64, THO_PREC_FP32_BULK, THO_PREC_FP64_EMU = 0, 1, 2
 THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE = 0x1, 0x2
 THO_MAX_K0, THO_MAX_K = 128, 32
 

@@ -201,3 +201,27 @@ def test_batched_c4_workload(tho):
             Ql, _, _ = tho.orth(p.V, p.A)
             worst = max(worst, float((Ql - Q).abs().max()))
     assert worst < TOL_Q
+
+
+# --- FP64-accurate emulated products (bf16 tensor cores): same tolerances as FP64 ---
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("n,k0,k", [(4096, 16, 4), (33, 16, 17), (12345, 64, 16), (40000, 128, 32), (3 * 256 + 17, 7, 30)])
+def test_emulated_matches_oracle(tho, dtype, n, k0, k):
+    p = inputs.random_problem(n, k0, k, dtype=dtype, seed=n + 3 * k0 + k)
+    Q, R, S = _run(tho, p, prec=tho.THO_PREC_FP64_EMU)
+    Qo, Ro, So = oracle.two_stage(p.V.numpy(), p.A.numpy())
+    np.testing.assert_allclose(Q, Qo, atol=TOL_Q, rtol=0)
+    np.testing.assert_allclose(R, Ro, atol=TOL_Q * max(1.0, np.abs(Ro).max()), rtol=0)
+    np.testing.assert_allclose(S, So, atol=TOL_Q * max(1.0, np.abs(So).max()), rtol=0)
+    assert loo_np(p.V.numpy(), Q) < TOL_LOO
+
+
+@pytest.mark.parametrize("cid", [2, 3])
+def test_emulated_full_size(tho, cid):
+    """C2 (cond 1e10) and C3 (rank deficient) at full size: LOO, residual <= 1e-13."""
+    from gpu_metrics import loo, resid_fro
+    p = inputs.config_problem(cid, device="cuda")
+    Q, R, S = tho.orth(p.V, p.A, prec=tho.THO_PREC_FP64_EMU)
+    assert loo(p.V, Q) < TOL_LOO
+    assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO

@@ -263,4 +263,205 @@ __global__ void __launch_bounds__(kThreads) k_gram_emu(const Inst* insts, const 
   }
 }
 
+// Real-embedded second operand of the rank-k0 update out = base + V_2 Z:
+//   real:    B(q, j) = Z(q, j)
+//   complex: B(2l, j) = Re Z(l, j), B(2l + 1, j) = -Im Z(l, j)   (Re outputs);
+//   the Im outputs use B~(2l, j) = Im Z, B~(2l + 1, j) = Re Z, built from the
+//   packed pair (Re, -Im) by swapping halves and negating the low half.
+__device__ __forceinline__ unsigned im_pair_update(unsigned w) {
+  return ((w >> 16) | (w << 16)) ^ 0x00008000u;
+}
+
+// Slices of column j of Z (k0 values of S, in shared memory) into the update's
+// B operand: out[(p * kpe + j) * kzp + q] (bf16), eZ[j] = maximal biased exponent.
+// Called by the CTA of column j of the T-solves; kzp = padded real length.
+template <class S>
+__device__ void emu_split_column(const S* z, int k0, int j, int kpe, int kzp, unsigned short* out, int* eZ) {
+  constexpr bool C = Tr<S>::C;
+  __shared__ int emax_s;
+  if (threadIdx.x == 0) emax_s = 0;
+  __syncthreads();
+  int m = 0;
+  for (int l = threadIdx.x; l < k0; l += blockDim.x) {
+    if constexpr (C) {
+      const z64 v = *reinterpret_cast<const z64*>(z + l);
+      m = max(m, max(dexp(v.x), dexp(v.y)));
+    } else {
+      m = max(m, dexp(*reinterpret_cast<const double*>(z + l)));
+    }
+  }
+  atomicMax(&emax_s, m);
+  __syncthreads();
+  const int em = emax_s;
+  if (threadIdx.x == 0) eZ[j] = em;
+  for (int q = threadIdx.x; q < kzp; q += blockDim.x) {
+    double x = 0.0;
+    if constexpr (C) {
+      if (q < 2 * k0) {
+        const z64 v = *reinterpret_cast<const z64*>(z + q / 2);
+        x = (q & 1) ? -v.y : v.x;
+      }
+    } else {
+      if (q < k0) x = *reinterpret_cast<const double*>(z + q);
+    }
+    float sl[kEmuSlices];
+    emu_split(x, em, sl);
+#pragma unroll
+    for (int p = 0; p < kEmuSlices; ++p) out[((size_t)p * kpe + j) * kzp + q] = bf16_bits(sl[p]);
+  }
+}
+
+// a5 / a9 (rank-k0 update), emulated: over one chunk of trailing rows,
+//   which = 0:  Q_2 <- A_2 + V_2 Z    (A' of the trailing block, parked in Q)
+//   which = 1:  Q_2 <- Q_2 + V_2 Z2   (Q = Qbar - W Z2 with W_2 = -V_2)
+// with the products on bf16 tensor cores: per-row scales of V over its k0
+// entries, per-column scales of Z (sliced by the T-solve kernels).  Row tiles
+// of TM = 16 MTt rows; K blocks of 64 real steps (exact FP32 level sums),
+// folded into int64.  Shared: Zs [8][kpe][kEmuLd] | Vs [8][TM][kEmuLd] bf16 | eR [TM].
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_update_emu(const Inst* insts, const Io* iot, Io io0,
+                                                         const WorkItem* items, void* ws, int which) {
+  constexpr bool C = Tr<S>::C;
+  constexpr int RPE = C ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const Io io = get_io(iot, io0, it.inst);
+  const int k0 = (int)I.k0, k = (int)I.k;
+  const int kpe = (k + 7) / 8 * 8;
+  const int NT = (C ? 2 * kpe : kpe) / 8;
+  const int MTt = max(1, min(4, 16 / NT));
+  const int TM = 16 * MTt;
+  const int kz = RPE * k0, kzp = (kz + kEmuKT - 1) / kEmuKT * kEmuKT;
+  unsigned short* Zs = reinterpret_cast<unsigned short*>(smem_raw);
+  unsigned short* Vs = Zs + kEmuSlices * kpe * kEmuLd;
+  int* eR = reinterpret_cast<int*>(Vs + kEmuSlices * TM * kEmuLd);
+  const unsigned short* Zg = reinterpret_cast<const unsigned short*>(wsp<S>(ws, which ? I.oZsl2 : I.oZsl1));
+  const int* eZ = reinterpret_cast<const int*>(wsp<S>(ws, which ? I.oEz2 : I.oEz1));
+  const double* Vd = reinterpret_cast<const double*>(io.V);
+  const double* Bd = reinterpret_cast<const double*>(which ? io.Q : io.A);
+  double* Qd = reinterpret_cast<double*>(io.Q);
+  const int64_t ldv = io.ldv * RPE, ldb = (which ? io.ldq : io.lda) * RPE, ldq = io.ldq * RPE;
+  const int64_t r_begin = I.k0 + (int64_t)it.idx * I.rows4;
+  const int64_t r_end = min64(I.n, r_begin + I.rows4);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+  const int ntiles = MTt * NT;
+
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += TM) {
+    const int nr = (int)min64(TM, r_end - r0);
+    __syncthreads();
+    for (int r = threadIdx.x; r < TM; r += kThreads) eR[r] = 0;
+    __syncthreads();
+    // Row scales of V over its k0 (complex: 2 k0 real) entries.
+    {
+      int m = 0, rr = -1;
+#pragma unroll 8
+      for (int e = threadIdx.x; e < TM * kz; e += kThreads) {
+        const int r = e % TM, q = e / TM;  // q: real index within the row; r is fixed per thread
+        if (r != rr) {
+          if (rr >= 0) atomicMax(&eR[rr], m);
+          rr = r;
+          m = 0;
+        }
+        if (r < nr) m = max(m, dexp(Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)]));
+      }
+      if (rr >= 0) atomicMax(&eR[rr], m);
+    }
+    float acc[2][kEmuLevels][4];
+    long long hi[2][4], lo[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        hi[u][e] = lo[u][e] = 0;
+#pragma unroll
+        for (int L = 0; L < kEmuLevels; ++L) acc[u][L][e] = 0.0f;
+      }
+    for (int kb = 0; kb < kzp; kb += kEmuKT) {
+      __syncthreads();  // eR complete; previous block's fragments consumed
+      // Z slices of this K block (bf16, from the workspace).
+      for (int e = threadIdx.x; e < kEmuSlices * kpe * (kEmuKT / 2); e += kThreads) {
+        const int w = e % (kEmuKT / 2), pj = e / (kEmuKT / 2);
+        reinterpret_cast<unsigned*>(Zs + pj * kEmuLd)[w] =
+            reinterpret_cast<const unsigned*>(Zg + (size_t)pj * kzp + kb)[w];
+      }
+      // V block: rows r0.., real steps kb..kb+63, batched loads then slices.
+      constexpr int NV = 4 * kEmuKT * 16 / kThreads;  // TM <= 64 rows: <= 16 values per thread
+      double val[NV];
+#pragma unroll
+      for (int u = 0; u < NV; ++u) {
+        const int e = threadIdx.x + u * kThreads;  // e = q_local + 64 * r
+        const int ql = e % kEmuKT, r = e / kEmuKT, q = kb + ql;
+        double x = 0.0;
+        if (r < nr && q < kz) x = Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)];
+        val[u] = x;
+      }
+#pragma unroll
+      for (int u = 0; u < NV; ++u) {
+        const int e = threadIdx.x + u * kThreads;
+        const int ql = e % kEmuKT, r = e / kEmuKT;
+        if (r >= TM) continue;
+        float sl[kEmuSlices];
+        emu_split(val[u], eR[r], sl);
+#pragma unroll
+        for (int p = 0; p < kEmuSlices; ++p) Vs[(p * TM + r) * kEmuLd + ql] = bf16_bits(sl[p]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int tile = warp + 8 * u;
+        if (tile >= ntiles) continue;
+        const int mt = tile / NT, nt = tile % NT;
+        const bool imag = C && nt * 8 >= kpe;
+        const int jb = (imag ? nt * 8 - kpe : nt * 8) + g;
+        for (int ks = 0; ks < kEmuKT; ks += 16) {
+          unsigned bf[kEmuSlices][2];
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            const unsigned* row = reinterpret_cast<const unsigned*>(Zs + (qq * kpe + jb) * kEmuLd + ks);
+            unsigned b0 = row[t4], b1 = row[t4 + 4];
+            if (imag) {
+              b0 = im_pair_update(b0);
+              b1 = im_pair_update(b1);
+            }
+            bf[qq][0] = b0;
+            bf[qq][1] = b1;
+          }
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) {
+            const unsigned* ra = reinterpret_cast<const unsigned*>(Vs + (p * TM + mt * 16 + g) * kEmuLd + ks);
+            const unsigned* rb = reinterpret_cast<const unsigned*>(Vs + (p * TM + mt * 16 + g + 8) * kEmuLd + ks);
+            const unsigned a0 = ra[t4], a1 = rb[t4], a2 = ra[t4 + 4], a3 = rb[t4 + 4];
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              if (p + qq > kEmuLevels - 1) continue;
+              mma_bf16(acc[u][p + qq], a0, a1, a2, a3, bf[qq][0], bf[qq][1]);
+            }
+          }
+        }
+        emu_fold(acc[u], hi[u], lo[u]);
+      }
+    }
+    // out = base + (hi 2^-35 + lo 2^-63) 2^(eR + eZ - 2044)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int tile = warp + 8 * u;
+      if (tile >= ntiles) continue;
+      const int mt = tile / NT, nt = tile % NT;
+      const bool imag = C && nt * 8 >= kpe;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = (imag ? nt * 8 - kpe : nt * 8) + 2 * t4 + (e & 1);
+        if (r >= nr || j >= k) continue;
+        const int sc = eR[r] + eZ[j] - 2044;
+        const double v = ldexp((double)hi[u][e], sc - 35) + ldexp((double)lo[u][e], sc - 63);
+        const int64_t ob = (int64_t)j * ldb + (r0 + r) * RPE + (imag ? 1 : 0);
+        const int64_t oq = (int64_t)j * ldq + (r0 + r) * RPE + (imag ? 1 : 0);
+        Qd[oq] = Bd[ob] + v;
+      }
+    }
+  }
+}
+
 }  // namespace tho

@@ -302,8 +302,11 @@ __global__ void __launch_bounds__(kThreads) k_gram(const Inst* insts, const Io* 
 //   Z(:, j) = T^{-*} G(:, j)             (T^* = I + R1 upper triangular)
 //   A'_1(:, j) = A_1(:, j) - Wtop Z(:, j);  S(:, j) = P^* A'_1(:, j) = -Q1^* A'_1(:, j)
 template <class S>
+__device__ void emu_split_column(const S* z, int k0, int j, int kpe, int kzp, unsigned short* out, int* eZ);
+
+template <class S>
 __global__ void __launch_bounds__(kThreads) k_solve_z(const Inst* insts, const Io* iot, Io io0, void* ws,
-                                                      int* status, uint32_t flags) {
+                                                      int* status, uint32_t flags, int emu) {
   const int inst = blockIdx.x, j = blockIdx.y;
   const Inst& I = insts[inst];
   const int k0 = (int)I.k0, k = (int)I.k;
@@ -338,6 +341,9 @@ __global__ void __launch_bounds__(kThreads) k_solve_z(const Inst* insts, const I
     }
   }
   __syncthreads();
+  if (emu)  // bf16 slices of Z for the emulated update
+    emu_split_column<S>(z, k0, j, (k + 7) / 8 * 8, ((Tr<S>::C ? 2 : 1) * k0 + 63) / 64 * 64,
+                        reinterpret_cast<unsigned short*>(wsp<S>(ws, I.oZsl1)), reinterpret_cast<int*>(wsp<S>(ws, I.oEz1)));
   S* Zo = wsp<S>(ws, I.oZ);
   for (int i = threadIdx.x; i < k0; i += kThreads) {
     Zo[i + j * k0] = z[i];
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_z(const Inst* insts, const I
 // Shared memory: Lb (P x kp, ld P) | Zs (k0p x kp, ld k0p) | Vs (tile) | small.
 template <class S, class B>
 __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* iot, Io io0,
-                                                   const WorkItem* items, void* ws, int P) {
+                                                   const WorkItem* items, void* ws, int P, int from_q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -388,12 +394,15 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
     int i = e % k0p, c = e / k0p;
     Zs[e] = (i < k0 && c < k) ? cvt<B, S>(Zg[i + c * k0]) : zero<B>();
   }
+  // from_q: A'_b was already formed (emulated update) and parked in Q's rows.
+  const S* Asrc = from_q ? reinterpret_cast<const S*>(io.Q) : A;
+  const int64_t ldsrc = from_q ? io.ldq : io.lda;
   for (int e = threadIdx.x; e < P * kp; e += kThreads) {
     int r = e % P, c = e / P;
-    Lb[e] = (r < rb && c < k) ? cvt<B, S>(A[(lo + r) + (int64_t)c * io.lda]) : zero<B>();
+    Lb[e] = (r < rb && c < k) ? cvt<B, S>(Asrc[(lo + r) + (int64_t)c * ldsrc]) : zero<B>();
   }
   __syncthreads();
-  if (k0 > 0) {
+  if (k0 > 0 && !from_q) {
     for (int t0 = 0; t0 < rb; t0 += kTileRows) {
       const int nr = min(kTileRows, rb - t0);
       load_tile<B, S>(Vs, V, io.ldv, lo + t0, nr, k0, k0p);
@@ -685,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_gram(const Inst* insts, cons
 // substitution, T lower triangular); Q_{1:k0}(:, j) = -Wtop Z2(:, j).
 template <class S>
 __global__ void __launch_bounds__(kThreads) k_solve_z2(const Inst* insts, const Io* iot, Io io0, void* ws,
-                                                       int* status, uint32_t flags) {
+                                                       int* status, uint32_t flags, int emu) {
   const int inst = blockIdx.x, j = blockIdx.y;
   const Inst& I = insts[inst];
   const int k0 = (int)I.k0, k = (int)I.k;
@@ -713,6 +722,9 @@ __global__ void __launch_bounds__(kThreads) k_solve_z2(const Inst* insts, const 
     }
   }
   __syncthreads();
+  if (emu)  // bf16 slices of Z2 for the emulated update
+    emu_split_column<S>(z, k0, j, (k + 7) / 8 * 8, ((Tr<S>::C ? 2 : 1) * k0 + 63) / 64 * 64,
+                        reinterpret_cast<unsigned short*>(wsp<S>(ws, I.oZsl2)), reinterpret_cast<int*>(wsp<S>(ws, I.oEz2)));
   S* Z2 = wsp<S>(ws, I.oZ2);
   S* Q = reinterpret_cast<S*>(io.Q);
   for (int i = threadIdx.x; i < k0; i += kThreads) {

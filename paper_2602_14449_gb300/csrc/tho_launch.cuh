@@ -15,6 +15,7 @@ cudaError_t configure_impl(PlanCore& pc) {
   {
     const int kpe = (pc.kmax + 7) / 8 * 8;
     pc.smem_gram_emu = (size_t)kEmuSlices * kEmuLd * 2 * (64 + kpe) + sizeof(int) * (pc.k0pmax + 16 + pc.kpmax + 16);
+    pc.smem_upd_emu = (size_t)kEmuSlices * kEmuLd * 2 * (64 + kpe) + sizeof(int) * 64;
   }
   pc.smem_gram = std::max<size_t>((size_t)kTileRows * (pc.k0pmax + pc.kpmax), kRedElems) * b;
   pc.smem_apply = std::max<size_t>((size_t)(2 * kTileRows * pc.kpmax + pc.kpmax * pc.kpmax +
@@ -42,6 +43,7 @@ cudaError_t configure_impl(PlanCore& pc) {
   };
   if ((e = raise((const void*)k_gram<S, B>, pc.smem_gram)) != cudaSuccess) return e;
   if (EMU && (e = raise((const void*)k_gram_emu<S>, pc.smem_gram_emu)) != cudaSuccess) return e;
+  if (EMU && (e = raise((const void*)k_update_emu<S>, pc.smem_upd_emu)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
@@ -53,7 +55,7 @@ cudaError_t configure_impl(PlanCore& pc) {
   n += 1;                  // leaf
   for (int l = 1; l <= pc.Lmax; ++l) n += pc.tab.lev_n[l] > 0 ? 2 : 0;
   n += 2;                  // root, apply_gram
-  if (EMU && pc.any_k0) n += 1;  // emulated V_2^* Qbar
+  if (EMU && pc.any_k0) n += 2;  // emulated V_2^* Qbar and A' = A + V_2 Z
   if (pc.any_k0) n += 2;  // solve_z2, update_q
   pc.launches = n;
   return cudaSuccess;
@@ -78,11 +80,14 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
       hk(kPhGram, 1, st);
     }
     hk(kPhSolveZ, 0, st);
-    k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
+    k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags, EMU ? 1 : 0);
     hk(kPhSolveZ, 1, st);
   }
   hk(kPhLeaf, 0, st);
-  k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P);
+  if (EMU && pc.any_k0 && pc.tab.upd_n > 0)  // A'_2 = A_2 + V_2 Z on tensor cores, parked in Q
+    k_update_emu<S><<<pc.tab.upd_n, blk, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 0);
+  k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
+                                                         (EMU && pc.any_k0) ? 1 : 0);
   hk(kPhLeaf, 1, st);
   hk(kPhTreeUp, 0, st);
   for (int l = 1; l <= pc.Lmax; ++l)
@@ -105,11 +110,14 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   hk(kPhApply, 1, st);
   if (pc.any_k0) {
     hk(kPhSolveZ2, 0, st);
-    k_solve_z2<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
+    k_solve_z2<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags, EMU ? 1 : 0);
     hk(kPhSolveZ2, 1, st);
     if (pc.tab.upd_n > 0) {
       hk(kPhUpdateQ, 0, st);
-      k_update_q<S, B><<<pc.tab.upd_n, blk, pc.smem_upd, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws);
+      if (EMU)
+        k_update_emu<S><<<pc.tab.upd_n, blk, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 1);
+      else
+        k_update_q<S, B><<<pc.tab.upd_n, blk, pc.smem_upd, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws);
       hk(kPhUpdateQ, 1, st);
     }
   }

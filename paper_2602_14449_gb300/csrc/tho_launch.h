@@ -43,6 +43,7 @@ struct PlanCore {
   int* d_status = nullptr;
   size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
   size_t smem_gram_emu = 0;  // emulated split-n Gram (THO_PREC_FP64_EMU)
+  size_t smem_upd_emu = 0;   // emulated rank-k0 update
   int launches = 0;  // kernel launches per call
 };
 

@@ -190,9 +190,11 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   pc.k0pmax = (int)round_up(pc.k0max, tho::kBI);
   // Leaf height: the largest of 256/128/64 rows whose panel fits in shared memory.
   pc.P = 0;
+  // Emulated mode forms A' outside the leaf kernel: no Z / V staging there.
+  const int leaf_k0p = pc.prec == THO_PREC_FP64_EMU && pc.any_k0 ? 0 : pc.k0pmax;
   for (int P : {256, 128, 64}) {
     if (P < 2 * pc.kmax) continue;
-    if (tho::leaf_smem_bytes(P, pc.k0pmax, pc.kpmax, p->L->bulk_elem, p->L->elem) <= 200 * 1024) {
+    if (tho::leaf_smem_bytes(P, leaf_k0p, pc.kpmax, p->L->bulk_elem, p->L->elem) <= 200 * 1024) {
       pc.P = P;
       break;
     }

@@ -25,10 +25,11 @@ namespace tho {
 constexpr int kEmuSlices = 8;
 constexpr int kEmuLevels = 8;      // levels 2..9
 constexpr int kEmuKT = 64;         // real contraction steps per exact block (and per smem tile)
-constexpr int kEmuMaxLoads = 24;   // staged values per thread per tile: (64 + 32) x 64 / 256
+constexpr int kEmuBatch = 4;       // loads issued together before splitting
 // Row stride of the slice tiles: 64 + 8 bf16 = 144 bytes, so the 8 row groups
 // of a fragment load fall on distinct banks (bank = 4 g + t).
 constexpr int kEmuLd = kEmuKT + 8;
+
 
 // Biased exponent field of a double (0 for zero and subnormals).
 __device__ __forceinline__ int dexp(double x) {
@@ -95,32 +96,57 @@ __device__ __forceinline__ void emu_fold(float (&acc)[kEmuLevels][4], long long 
   }
 }
 
-// a3 (sweep 1), emulated: partial sums of V_2^* A_2 over one chunk of trailing
-// rows with the products on bf16 tensor cores.  The complex case uses the real
-// embedding along the contraction (row r -> real steps 2r (re), 2r + 1 (im)):
-//   Re G = sum_q X(q, i) Y(q, j),  Im G = sum_q X(q, i) Y~(q, j),
-//   X = V as reals, Y = A as reals, Y~(2r) = Im A, Y~(2r + 1) = -Re A.
-// Output columns n < k are Re G(:, n), n >= k are Im G(:, n - k).
-// Passes over groups of MT 16-row output tiles keep the accumulators in
-// registers (<= 2 tiles per warp).  Shared memory: Vsl [8][MT*16][KT] bf16 |
-// Asl [8][kpe][KT] bf16 | eV [k0p] | eA [kp] (ints).
-// which = 0: X = A, partials to the G1 slots (sweep 1); which = 1: X = Q (holding
-// Qbar after sweep 3a), partials to the G3 slots.
+// Fragment loads with ldmatrix: four 8x8 bf16 matrices per instruction.
+__device__ __forceinline__ void ldsm_x4(const unsigned short* p, unsigned& r0, unsigned& r1, unsigned& r2,
+                                        unsigned& r3) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
+// A fragment (16 x 16 of a [row][k] tile, ld kEmuLd) at rows m0.., steps ks..
+__device__ __forceinline__ void ld_afrag(const unsigned short* tile, int m0, int ks, unsigned (&a)[4]) {
+  const int lane = threadIdx.x & 31, i = lane >> 3, r = lane & 7;
+  ldsm_x4(tile + (m0 + ((i & 1) ? 8 : 0) + r) * kEmuLd + ks + ((i & 2) ? 8 : 0), a[0], a[1], a[2], a[3]);
+}
+
+// B fragments of two slices (n 8 x k 16 of [n][k] tiles at t0 and t1, ld kEmuLd).
+__device__ __forceinline__ void ld_bfrag2(const unsigned short* t0, const unsigned short* t1, int n0, int ks,
+                                          unsigned (&b0)[2], unsigned (&b1)[2]) {
+  const int lane = threadIdx.x & 31, i = lane >> 3, r = lane & 7;
+  const unsigned short* t = (i & 2) ? t1 : t0;
+  ldsm_x4(t + (n0 + r) * kEmuLd + ks + ((i & 1) ? 8 : 0), b0[0], b0[1], b1[0], b1[1]);
+}
+
+constexpr int kEmuThreads = 512;   // 16 warps, one 16 x 8 output tile each
+
+// a3 (sweep 1) and the V_2^* Qbar sums of a8, emulated: partial sums of
+// V_2^* X over one chunk of trailing rows, X = A (which = 0, into the G1
+// slots) or X = Q holding Qbar (which = 1, into the G3 slots), with the
+// products on bf16 tensor cores.  The complex case uses the real embedding
+// along the contraction (row r -> real steps 2r (re), 2r + 1 (im)):
+//   Re G = sum_q V(q, i) X(q, j),  Im G = sum_q V(q, i) X~(q, j),
+//   X~(2r) = Im X, X~(2r + 1) = -Re X.
+// Output columns n < kpe are Re G(:, n), n >= kpe are Im G(:, n - kpe).
+// Passes over groups of MT 16-row output tiles keep one tile per warp.
+// Shared memory: Vsl [8][MT*16][kEmuLd] | Asl [8][kpe][kEmuLd] bf16 | eV | eA.
 template <class S>
-__global__ void __launch_bounds__(kThreads) k_gram_emu(const Inst* insts, const Io* iot, Io io0,
-                                                       const WorkItem* items, void* ws, int which) {
+__global__ void __launch_bounds__(kEmuThreads, 1) k_gram_emu(const Inst* insts, const Io* iot, Io io0,
+                                                             const WorkItem* items, void* ws, int which) {
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;        // real contraction steps per row
   constexpr int TR = kEmuKT / RPE;      // rows per tile
+  constexpr int NW = kEmuThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
   const Io io = get_io(iot, io0, it.inst);
   const int k0 = (int)I.k0, k = (int)I.k;
-  const int kpe = (k + 7) / 8 * 8;                // A columns, padded to the 8-wide N tile
-  const int NT = (C ? 2 * kpe : kpe) / 8;         // N tiles (complex: Re block then Im block)
-  const int k0t = (k0 + 15) / 16;                 // 16-row output tiles of G
-  const int MT = max(1, min(k0t, min(4, 16 / NT)));  // output tiles per pass along M (<= 64 rows)
+  const int kpe = (k + 7) / 8 * 8;
+  const int NT = (C ? 2 * kpe : kpe) / 8;
+  const int k0t = (k0 + 15) / 16;
+  const int MT = max(1, min(k0t, min(4, NW / NT)));
   const int MB = MT * 16;
   unsigned short* Vsl = reinterpret_cast<unsigned short*>(smem_raw);
   unsigned short* Asl = Vsl + kEmuSlices * MB * kEmuLd;
@@ -128,13 +154,12 @@ __global__ void __launch_bounds__(kThreads) k_gram_emu(const Inst* insts, const 
   int* eA = eV + I.k0p + 16;
   const double* Vd = reinterpret_cast<const double*>(io.V);
   const double* Ad = reinterpret_cast<const double*>(which ? io.Q : io.A);
-  const int64_t ldv = io.ldv * RPE, lda = (which ? io.ldq : io.lda) * RPE;  // leading dimensions in doubles
+  const int64_t ldv = io.ldv * RPE, lda = (which ? io.ldq : io.lda) * RPE;
   const int64_t r_begin = I.k0 + (int64_t)it.idx * I.rows1;
   const int64_t r_end = min64(I.n, r_begin + I.rows1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
 
-  // Column scales over the chunk: maximal biased exponent per column.
-  for (int col = warp; col < k0 + k; col += kThreads / 32) {
+  for (int col = warp; col < k0 + k; col += NW) {
     const double* src = col < k0 ? Vd + (int64_t)col * ldv : Ad + (int64_t)(col - k0) * lda;
     int m = 0;
     for (int64_t q = r_begin * RPE + lane; q < r_end * RPE; q += 32) m = max(m, dexp(src[q]));
@@ -147,114 +172,103 @@ __global__ void __launch_bounds__(kThreads) k_gram_emu(const Inst* insts, const 
   __syncthreads();
 
   S* out = wsp<S>(ws, which ? I.oG3 : I.oG1) + (int64_t)it.idx * k0 * k;
+  const int ntiles = MT * NT;
+  const bool mine = warp < ntiles;
+  const int mt = mine ? warp / NT : 0, nt = mine ? warp % NT : 0;
+  const bool imag = C && nt * 8 >= kpe;
+  const int jb0 = imag ? nt * 8 - kpe : nt * 8;
   for (int m0 = 0; m0 < k0t * 16; m0 += MB) {
-    // This warp's output tiles: tile index w and w + 8 of MT x NT.
-    const int ntiles = MT * NT;
-    float acc[2][kEmuLevels][4];
-    long long hi[2][4], lo[2][4];
+    float acc[kEmuLevels][4];
+    long long hi[4], lo[4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int e = 0; e < 4; ++e) {
+      hi[e] = lo[e] = 0;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        hi[u][e] = lo[u][e] = 0;
-#pragma unroll
-        for (int L = 0; L < kEmuLevels; ++L) acc[u][L][e] = 0.0f;
-      }
+      for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+    }
+    int blocks = 0;
     for (int64_t r0 = r_begin; r0 < r_end; r0 += TR) {
       const int nr = (int)min64(TR, r_end - r0);
       const int nq = nr * RPE;
       __syncthreads();
-      // Split this pass's V columns and all A columns of the tile into slices:
-      // every load of the tile is issued before the first split so that the
-      // global-memory latency is paid once per tile.
       const int nv = MB * kEmuKT, ntot = (MB + kpe) * kEmuKT;
-      double val[kEmuMaxLoads];
+      for (int u0 = 0; u0 * kEmuThreads < ntot; u0 += kEmuBatch) {
+        double val[kEmuBatch];
 #pragma unroll
-      for (int u = 0; u < kEmuMaxLoads; ++u) {
-        const int e = threadIdx.x + u * kThreads;
-        double x = 0.0;
-        if (e < ntot) {
-          const int q = e % kEmuKT;
-          if (q < nq) {
-            if (e < nv) {
-              const int col = m0 + e / kEmuKT;
-              if (col < k0) x = Vd[(int64_t)col * ldv + r0 * RPE + q];
-            } else {
-              const int j = (e - nv) / kEmuKT;
-              if (j < k) x = Ad[(int64_t)j * lda + r0 * RPE + q];
+        for (int u = 0; u < kEmuBatch; ++u) {
+          const int e = threadIdx.x + (u0 + u) * kEmuThreads;
+          double x = 0.0;
+          if (e < ntot) {
+            const int q = e % kEmuKT;
+            if (q < nq) {
+              if (e < nv) {
+                const int col = m0 + e / kEmuKT;
+                if (col < k0) x = Vd[(int64_t)col * ldv + r0 * RPE + q];
+              } else {
+                const int j = (e - nv) / kEmuKT;
+                if (j < k) x = Ad[(int64_t)j * lda + r0 * RPE + q];
+              }
             }
           }
+          val[u] = x;
         }
-        val[u] = x;
-      }
 #pragma unroll
-      for (int u = 0; u < kEmuMaxLoads; ++u) {
-        const int e = threadIdx.x + u * kThreads;
-        if (e >= ntot) continue;
-        const int q = e % kEmuKT;
-        float sl[kEmuSlices];
-        if (e < nv) {
-          const int m = e / kEmuKT, col = m0 + m;
-          emu_split(val[u], col < k0 ? eV[col] : 0, sl);
+        for (int u = 0; u < kEmuBatch; ++u) {
+          const int e = threadIdx.x + (u0 + u) * kEmuThreads;
+          if (e >= ntot) continue;
+          const int q = e % kEmuKT;
+          float sl[kEmuSlices];
+          if (e < nv) {
+            const int m = e / kEmuKT, col = m0 + m;
+            emu_split(val[u], col < k0 ? eV[col] : 0, sl);
 #pragma unroll
-          for (int p = 0; p < kEmuSlices; ++p) Vsl[(p * MB + m) * kEmuLd + q] = bf16_bits(sl[p]);
-        } else {
-          const int j = (e - nv) / kEmuKT;
-          emu_split(val[u], j < k ? eA[j] : 0, sl);
+            for (int p = 0; p < kEmuSlices; ++p) Vsl[(p * MB + m) * kEmuLd + q] = bf16_bits(sl[p]);
+          } else {
+            const int j = (e - nv) / kEmuKT;
+            emu_split(val[u], j < k ? eA[j] : 0, sl);
 #pragma unroll
-          for (int p = 0; p < kEmuSlices; ++p) Asl[(p * kpe + j) * kEmuLd + q] = bf16_bits(sl[p]);
+            for (int p = 0; p < kEmuSlices; ++p) Asl[(p * kpe + j) * kEmuLd + q] = bf16_bits(sl[p]);
+          }
         }
       }
       __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int tile = warp + 8 * u;
-        if (tile >= ntiles) continue;
-        const int mt = tile / NT, nt = tile % NT;
-        const bool imag = C && nt * 8 >= kpe;
-        const int jb = (imag ? nt * 8 - kpe : nt * 8) + g;  // A column of this lane's B fragment
+      if (mine) {
         for (int ks = 0; ks < kEmuKT; ks += 16) {
           unsigned bf[kEmuSlices][2];
 #pragma unroll
-          for (int qq = 0; qq < kEmuSlices; ++qq) {
-            const unsigned* row = reinterpret_cast<const unsigned*>(Asl + (qq * kpe + jb) * kEmuLd + ks);
-            unsigned b0 = row[t4], b1 = row[t4 + 4];
-            if (imag) {
-              b0 = im_pair(b0);
-              b1 = im_pair(b1);
+          for (int qq = 0; qq < kEmuSlices; qq += 2)
+            ld_bfrag2(Asl + (qq * kpe) * kEmuLd, Asl + ((qq + 1) * kpe) * kEmuLd, jb0, ks, bf[qq], bf[qq + 1]);
+          if (imag) {
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              bf[qq][0] = im_pair(bf[qq][0]);
+              bf[qq][1] = im_pair(bf[qq][1]);
             }
-            bf[qq][0] = b0;
-            bf[qq][1] = b1;
           }
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) {
-            const unsigned* ra = reinterpret_cast<const unsigned*>(Vsl + (p * MB + mt * 16 + g) * kEmuLd + ks);
-            const unsigned* rb = reinterpret_cast<const unsigned*>(Vsl + (p * MB + mt * 16 + g + 8) * kEmuLd + ks);
-            const unsigned a0 = ra[t4], a1 = rb[t4], a2 = ra[t4 + 4], a3 = rb[t4 + 4];
+            unsigned a[4];
+            ld_afrag(Vsl + (p * MB) * kEmuLd, mt * 16, ks, a);
 #pragma unroll
             for (int qq = 0; qq < kEmuSlices; ++qq) {
-              if (p + qq > kEmuLevels - 1) continue;  // level p + qq + 2 > 9: dropped
-              mma_bf16(acc[u][p + qq], a0, a1, a2, a3, bf[qq][0], bf[qq][1]);
+              if (p + qq > kEmuLevels - 1) continue;
+              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
             }
           }
         }
-        emu_fold(acc[u], hi[u], lo[u]);
+        // Level sums stay exact for 128 steps: fold every second tile.
+        if ((++blocks & 1) == 0) emu_fold(acc, hi, lo);
       }
     }
-    // Write this pass's outputs: element (row, col) of the fragment.
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int tile = warp + 8 * u;
-      if (tile >= ntiles) continue;
-      const int mt = tile / NT, nt = tile % NT;
-      const bool imag = C && nt * 8 >= kpe;
+    if (mine) {
+      emu_fold(acc, hi, lo);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int i = m0 + mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int j = (imag ? nt * 8 - kpe : nt * 8) + 2 * t4 + (e & 1);
+        const int j = jb0 + 2 * t4 + (e & 1);
         if (i >= k0 || j >= k) continue;
         const int sc = eV[i] + eA[j] - 2044;
-        const double v = ldexp((double)hi[u][e], sc - 35) + ldexp((double)lo[u][e], sc - 63);
+        const double v = ldexp((double)hi[e], sc - 35) + ldexp((double)lo[e], sc - 63);
         double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
         if constexpr (C) o[imag ? 1 : 0] = v;
         else o[0] = v;
@@ -315,14 +329,16 @@ __device__ void emu_split_column(const S* z, int k0, int j, int kpe, int kzp, un
 //   which = 0:  Q_2 <- A_2 + V_2 Z    (A' of the trailing block, parked in Q)
 //   which = 1:  Q_2 <- Q_2 + V_2 Z2   (Q = Qbar - W Z2 with W_2 = -V_2)
 // with the products on bf16 tensor cores: per-row scales of V over its k0
-// entries, per-column scales of Z (sliced by the T-solve kernels).  Row tiles
-// of TM = 16 MTt rows; K blocks of 64 real steps (exact FP32 level sums),
-// folded into int64.  Shared: Zs [8][kpe][kEmuLd] | Vs [8][TM][kEmuLd] bf16 | eR [TM].
+// entries, per-column scales of Z (sliced by the T-solve kernels; all slices
+// stay resident in shared memory for the chunk).  Row tiles of TM = 16 MTt
+// rows, one 16 x 8 output tile per warp; K blocks of 64 real steps, folded
+// every 128 steps.  Shared: Zs [8][kpe][kzp + 8] | Vs [8][TM][kEmuLd] bf16 | eR.
 template <class S>
-__global__ void __launch_bounds__(kThreads) k_update_emu(const Inst* insts, const Io* iot, Io io0,
-                                                         const WorkItem* items, void* ws, int which) {
+__global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts, const Io* iot, Io io0,
+                                                               const WorkItem* items, void* ws, int which) {
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
+  constexpr int NW = kEmuThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -330,11 +346,11 @@ __global__ void __launch_bounds__(kThreads) k_update_emu(const Inst* insts, cons
   const int k0 = (int)I.k0, k = (int)I.k;
   const int kpe = (k + 7) / 8 * 8;
   const int NT = (C ? 2 * kpe : kpe) / 8;
-  const int MTt = max(1, min(4, 16 / NT));
+  const int MTt = max(1, min(4, NW / NT));
   const int TM = 16 * MTt;
-  const int kz = RPE * k0, kzp = (kz + kEmuKT - 1) / kEmuKT * kEmuKT;
+  const int kz = RPE * k0, kzp = (kz + kEmuKT - 1) / kEmuKT * kEmuKT, ldz = kzp + 8;
   unsigned short* Zs = reinterpret_cast<unsigned short*>(smem_raw);
-  unsigned short* Vs = Zs + kEmuSlices * kpe * kEmuLd;
+  unsigned short* Vs = Zs + kEmuSlices * kpe * ldz;
   int* eR = reinterpret_cast<int*>(Vs + kEmuSlices * TM * kEmuLd);
   const unsigned short* Zg = reinterpret_cast<const unsigned short*>(wsp<S>(ws, which ? I.oZsl2 : I.oZsl1));
   const int* eZ = reinterpret_cast<const int*>(wsp<S>(ws, which ? I.oEz2 : I.oEz1));
@@ -346,51 +362,46 @@ __global__ void __launch_bounds__(kThreads) k_update_emu(const Inst* insts, cons
   const int64_t r_end = min64(I.n, r_begin + I.rows4);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
   const int ntiles = MTt * NT;
+  const bool mine = warp < ntiles;
+  const int mt = mine ? warp / NT : 0, nt = mine ? warp % NT : 0;
+  const bool imag = C && nt * 8 >= kpe;
+  const int jb0 = imag ? nt * 8 - kpe : nt * 8;
 
+  // All Z slices for the chunk (bf16 words, from the workspace).
+  for (int e = threadIdx.x; e < kEmuSlices * kpe * (kzp / 2); e += kEmuThreads) {
+    const int w = e % (kzp / 2), pj = e / (kzp / 2);
+    reinterpret_cast<unsigned*>(Zs + pj * ldz)[w] = reinterpret_cast<const unsigned*>(Zg + (size_t)pj * kzp)[w];
+  }
   for (int64_t r0 = r_begin; r0 < r_end; r0 += TM) {
     const int nr = (int)min64(TM, r_end - r0);
     __syncthreads();
-    for (int r = threadIdx.x; r < TM; r += kThreads) eR[r] = 0;
+    for (int r = threadIdx.x; r < TM; r += kEmuThreads) eR[r] = 0;
     __syncthreads();
-    // Row scales of V over its k0 (complex: 2 k0 real) entries.
-    {
-      int m = 0, rr = -1;
+    {  // row scales of V over its k0 (complex: 2 k0 real) entries; r is fixed per thread
+      int m = 0;
+      const int r = threadIdx.x % TM;
 #pragma unroll 8
-      for (int e = threadIdx.x; e < TM * kz; e += kThreads) {
-        const int r = e % TM, q = e / TM;  // q: real index within the row; r is fixed per thread
-        if (r != rr) {
-          if (rr >= 0) atomicMax(&eR[rr], m);
-          rr = r;
-          m = 0;
-        }
+      for (int e = threadIdx.x; e < TM * kz; e += kEmuThreads) {
+        const int q = e / TM;
         if (r < nr) m = max(m, dexp(Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)]));
       }
-      if (rr >= 0) atomicMax(&eR[rr], m);
+      atomicMax(&eR[r], m);
     }
-    float acc[2][kEmuLevels][4];
-    long long hi[2][4], lo[2][4];
+    float acc[kEmuLevels][4];
+    long long hi[4], lo[4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int e = 0; e < 4; ++e) {
+      hi[e] = lo[e] = 0;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        hi[u][e] = lo[u][e] = 0;
-#pragma unroll
-        for (int L = 0; L < kEmuLevels; ++L) acc[u][L][e] = 0.0f;
-      }
+      for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+    }
     for (int kb = 0; kb < kzp; kb += kEmuKT) {
-      __syncthreads();  // eR complete; previous block's fragments consumed
-      // Z slices of this K block (bf16, from the workspace).
-      for (int e = threadIdx.x; e < kEmuSlices * kpe * (kEmuKT / 2); e += kThreads) {
-        const int w = e % (kEmuKT / 2), pj = e / (kEmuKT / 2);
-        reinterpret_cast<unsigned*>(Zs + pj * kEmuLd)[w] =
-            reinterpret_cast<const unsigned*>(Zg + (size_t)pj * kzp + kb)[w];
-      }
-      // V block: rows r0.., real steps kb..kb+63, batched loads then slices.
-      constexpr int NV = 4 * kEmuKT * 16 / kThreads;  // TM <= 64 rows: <= 16 values per thread
+      __syncthreads();  // eR complete; the previous block's fragments consumed
+      constexpr int NV = 64 * kEmuKT / kEmuThreads;  // TM <= 64 rows: <= 8 values per thread
       double val[NV];
 #pragma unroll
       for (int u = 0; u < NV; ++u) {
-        const int e = threadIdx.x + u * kThreads;  // e = q_local + 64 * r
+        const int e = threadIdx.x + u * kEmuThreads;  // e = q_local + 64 r
         const int ql = e % kEmuKT, r = e / kEmuKT, q = kb + ql;
         double x = 0.0;
         if (r < nr && q < kz) x = Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)];
@@ -398,7 +409,7 @@ __global__ void __launch_bounds__(kThreads) k_update_emu(const Inst* insts, cons
       }
 #pragma unroll
       for (int u = 0; u < NV; ++u) {
-        const int e = threadIdx.x + u * kThreads;
+        const int e = threadIdx.x + u * kEmuThreads;
         const int ql = e % kEmuKT, r = e / kEmuKT;
         if (r >= TM) continue;
         float sl[kEmuSlices];
@@ -407,55 +418,45 @@ __global__ void __launch_bounds__(kThreads) k_update_emu(const Inst* insts, cons
         for (int p = 0; p < kEmuSlices; ++p) Vs[(p * TM + r) * kEmuLd + ql] = bf16_bits(sl[p]);
       }
       __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int tile = warp + 8 * u;
-        if (tile >= ntiles) continue;
-        const int mt = tile / NT, nt = tile % NT;
-        const bool imag = C && nt * 8 >= kpe;
-        const int jb = (imag ? nt * 8 - kpe : nt * 8) + g;
+      if (mine) {
         for (int ks = 0; ks < kEmuKT; ks += 16) {
           unsigned bf[kEmuSlices][2];
 #pragma unroll
-          for (int qq = 0; qq < kEmuSlices; ++qq) {
-            const unsigned* row = reinterpret_cast<const unsigned*>(Zs + (qq * kpe + jb) * kEmuLd + ks);
-            unsigned b0 = row[t4], b1 = row[t4 + 4];
-            if (imag) {
-              b0 = im_pair_update(b0);
-              b1 = im_pair_update(b1);
+          for (int qq = 0; qq < kEmuSlices; qq += 2) {
+            const int lane8 = lane >> 3, r8 = lane & 7;
+            const unsigned short* t = Zs + ((qq + ((lane8 & 2) ? 1 : 0)) * kpe) * ldz;
+            ldsm_x4(t + (jb0 + r8) * ldz + kb + ks + ((lane8 & 1) ? 8 : 0), bf[qq][0], bf[qq][1], bf[qq + 1][0],
+                    bf[qq + 1][1]);
+          }
+          if (imag) {
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              bf[qq][0] = im_pair_update(bf[qq][0]);
+              bf[qq][1] = im_pair_update(bf[qq][1]);
             }
-            bf[qq][0] = b0;
-            bf[qq][1] = b1;
           }
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) {
-            const unsigned* ra = reinterpret_cast<const unsigned*>(Vs + (p * TM + mt * 16 + g) * kEmuLd + ks);
-            const unsigned* rb = reinterpret_cast<const unsigned*>(Vs + (p * TM + mt * 16 + g + 8) * kEmuLd + ks);
-            const unsigned a0 = ra[t4], a1 = rb[t4], a2 = ra[t4 + 4], a3 = rb[t4 + 4];
+            unsigned a[4];
+            ld_afrag(Vs + (p * TM) * kEmuLd, mt * 16, ks, a);
 #pragma unroll
             for (int qq = 0; qq < kEmuSlices; ++qq) {
               if (p + qq > kEmuLevels - 1) continue;
-              mma_bf16(acc[u][p + qq], a0, a1, a2, a3, bf[qq][0], bf[qq][1]);
+              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
             }
           }
         }
-        emu_fold(acc[u], hi[u], lo[u]);
+        if (((kb / kEmuKT) & 1) == 1 || kb + kEmuKT >= kzp) emu_fold(acc, hi, lo);
       }
     }
-    // out = base + (hi 2^-35 + lo 2^-63) 2^(eR + eZ - 2044)
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int tile = warp + 8 * u;
-      if (tile >= ntiles) continue;
-      const int mt = tile / NT, nt = tile % NT;
-      const bool imag = C && nt * 8 >= kpe;
+    if (mine) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int r = mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int j = (imag ? nt * 8 - kpe : nt * 8) + 2 * t4 + (e & 1);
+        const int j = jb0 + 2 * t4 + (e & 1);
         if (r >= nr || j >= k) continue;
         const int sc = eR[r] + eZ[j] - 2044;
-        const double v = ldexp((double)hi[u][e], sc - 35) + ldexp((double)lo[u][e], sc - 63);
+        const double v = ldexp((double)hi[e], sc - 35) + ldexp((double)lo[e], sc - 63);
         const int64_t ob = (int64_t)j * ldb + (r0 + r) * RPE + (imag ? 1 : 0);
         const int64_t oq = (int64_t)j * ldq + (r0 + r) * RPE + (imag ? 1 : 0);
         Qd[oq] = Bd[ob] + v;

@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
   const Io io = get_io(iot, io0, it.inst);
-  const int k0 = (int)I.k0, k = (int)I.k, k0p = I.k0p, kp = I.kp;
+  const int k0 = (int)I.k0, k = (int)I.k, kp = I.kp;
+  const int k0p = from_q ? 0 : I.k0p;  // from_q: no Z / V staging in shared memory
   const int64_t lo = leaf_lo(I, it.idx);
   const int rb = (int)(leaf_lo(I, it.idx + 1) - lo);
   B* Lb = reinterpret_cast<B*>(smem_raw);

@@ -14,15 +14,16 @@ cudaError_t configure_impl(PlanCore& pc) {
   const size_t b = sizeof(B);
   {
     const int kpe = (pc.kmax + 7) / 8 * 8;
+    const int kzp = ((pc.dtype == 1 ? 2 : 1) * pc.k0max + kEmuKT - 1) / kEmuKT * kEmuKT;
     pc.smem_gram_emu = (size_t)kEmuSlices * kEmuLd * 2 * (64 + kpe) + sizeof(int) * (pc.k0pmax + 16 + pc.kpmax + 16);
-    pc.smem_upd_emu = (size_t)kEmuSlices * kEmuLd * 2 * (64 + kpe) + sizeof(int) * 64;
+    pc.smem_upd_emu = (size_t)kEmuSlices * 2 * (kpe * (kzp + 8) + 64 * kEmuLd) + sizeof(int) * 64;
   }
   pc.smem_gram = std::max<size_t>((size_t)kTileRows * (pc.k0pmax + pc.kpmax), kRedElems) * b;
   pc.smem_apply = std::max<size_t>((size_t)(2 * kTileRows * pc.kpmax + pc.kpmax * pc.kpmax +
                                             kTileRows * pc.k0pmax),
                                    kRedElems) * b;
   pc.smem_upd = (size_t)(pc.k0pmax * pc.kpmax + kTileRows * pc.k0pmax) * b;
-  pc.smem_leaf = leaf_smem_bytes(pc.P, pc.k0pmax, pc.kpmax, b, sizeof(S));
+  pc.smem_leaf = leaf_smem_bytes(pc.P, (EMU && pc.any_k0) ? 0 : pc.k0pmax, pc.kpmax, b, sizeof(S));
   pc.smem_tree = (size_t)(3 * pc.kmax * pc.kmax + 2 * pc.kmax) * sizeof(S);
   // The dynamic shared-memory limit is a per-kernel, per-device attribute shared
   // by every plan: raise it to the device's opt-in maximum less the kernel's
@@ -74,7 +75,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     if (pc.tab.gram_n > 0) {
       hk(kPhGram, 0, st);
       if (EMU)
-        k_gram_emu<S><<<pc.tab.gram_n, blk, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 0);
+        k_gram_emu<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 0);
       else
         k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
       hk(kPhGram, 1, st);
@@ -85,7 +86,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   }
   hk(kPhLeaf, 0, st);
   if (EMU && pc.any_k0 && pc.tab.upd_n > 0)  // A'_2 = A_2 + V_2 Z on tensor cores, parked in Q
-    k_update_emu<S><<<pc.tab.upd_n, blk, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 0);
+    k_update_emu<S><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 0);
   k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
                                                          (EMU && pc.any_k0) ? 1 : 0);
   hk(kPhLeaf, 1, st);
@@ -106,7 +107,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws,
                                                                  EMU ? 0 : 1);
   if (EMU && pc.any_k0 && pc.tab.gram_n > 0)  // V_2^* Qbar on tensor cores, into the G3 partials
-    k_gram_emu<S><<<pc.tab.gram_n, blk, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 1);
+    k_gram_emu<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 1);
   hk(kPhApply, 1, st);
   if (pc.any_k0) {
     hk(kPhSolveZ2, 0, st);
@@ -115,7 +116,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     if (pc.tab.upd_n > 0) {
       hk(kPhUpdateQ, 0, st);
       if (EMU)
-        k_update_emu<S><<<pc.tab.upd_n, blk, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 1);
+        k_update_emu<S><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 1);
       else
         k_update_q<S, B><<<pc.tab.upd_n, blk, pc.smem_upd, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws);
       hk(kPhUpdateQ, 1, st);

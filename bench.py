@@ -43,16 +43,20 @@ FP32_PEAK_TFLOPS = 78.4
 HBM_GBS_FALLBACK = 6795.1
 
 WORKLOADS = {
-    # name: (config id, n, k0, k, dtype name, prec, description)
-    "c3": (3, 1 << 22, 128, 32, "complex128", 0,
-           "complex128 n=4194304 k0=128 k=32, A=[V C1 + 1e-14 G1, G2] (numerically rank deficient), FP64 path"),
+    # name: (config id, n, k0, k, dtype name, precision mode, description)
+    # precision 0: FP64 arithmetic; 1: FP32-bulk variant; 2: FP64-accurate split-n
+    # products on bf16 tensor cores (same tolerances as 0; the QR of the leaves,
+    # the TSQR tree and the small solves stay FP64).
+    "c3": (3, 1 << 22, 128, 32, "complex128", 2,
+           "complex128 n=4194304 k0=128 k=32, A=[V C1 + 1e-14 G1, G2] (numerically rank deficient); "
+           "FP64-accurate, split-n products on bf16 tensor cores"),
+    "c3-native": (3, 1 << 22, 128, 32, "complex128", 0,
+                  "complex128 n=4194304 k0=128 k=32, A=[V C1 + 1e-14 G1, G2], FP64 arithmetic throughout"),
     "c3-fp32": (3, 1 << 22, 128, 32, "complex128", 1,
                 "complex128 n=4194304 k0=128 k=32, FP32-bulk variant"),
-    "c3-emu": (3, 1 << 22, 128, 32, "complex128", 2,
-               "complex128 n=4194304 k0=128 k=32, FP64-accurate products emulated on bf16 tensor cores"),
-    "c2-emu": (2, 1 << 20, 64, 16, "float64", 2,
-               "real n=1048576 k0=64 k=16, A=V C + 1e-10 G, FP64-accurate products emulated on bf16 tensor cores"),
-    "c2": (2, 1 << 20, 64, 16, "float64", 0, "real n=1048576 k0=64 k=16, A=V C + 1e-10 G (cond ~1e10)"),
+    "c2": (2, 1 << 20, 64, 16, "float64", 2,
+           "real n=1048576 k0=64 k=16, A=V C + 1e-10 G (cond ~1e10); FP64-accurate, products on bf16 tensor cores"),
+    "c2-native": (2, 1 << 20, 64, 16, "float64", 0, "real n=1048576 k0=64 k=16, A=V C + 1e-10 G, FP64 arithmetic"),
     "c1": (1, 4096, 16, 4, "float64", 0, "real n=4096 k0=16 k=4, A=N(0,1)"),
     "c5": (5, 1 << 20, 64, 16, "float64", 0,
            "differentiation: real n=1048576 k0=64 k=16, A=N(0,1), dQ=N(0,1); fused forward+adjoint vs "
@@ -61,21 +65,27 @@ WORKLOADS = {
            "batched: 256 real problems, n log-uniform in [16384, 262144], k0 in {8..128}, k in {4..32}, "
            "one graph replay vs 256 looped tho_orth calls"),
 }
-CPU_SAMPLE_ROWS = {"c3": 65536, "c3-fp32": 65536, "c3-emu": 65536, "c2": 131072, "c2-emu": 131072, "c1": 4096}
-REF_STEP_ROWS = {"c3": 16384, "c3-fp32": 16384, "c3-emu": 16384, "c2": 32768, "c2-emu": 32768, "c1": 4096,
-                 "c4": 16384}
+CPU_SAMPLE_ROWS = {"c3": 65536, "c3-native": 65536, "c3-fp32": 65536, "c2": 131072, "c2-native": 131072, "c1": 4096}
+REF_STEP_ROWS = {"c3": 16384, "c3-native": 16384, "c3-fp32": 16384, "c2": 32768, "c2-native": 32768, "c1": 4096}
 
-# Algorithmic real flops per trailing row of each streaming phase (x4 for complex):
+# Algorithmic real flops per trailing row of each streaming phase (x4 for complex).
+# FP64 arithmetic (precision 0 and the FP32-bulk variant):
 #   gram: V_2^* A_2 (2 k0 k); leaf: A' = A + V_2 Z (2 k0 k), Householder QR
 #   (2 k^2) and explicit leaf Q (2 k^2); apply: Q_leaf F (2 k^2) and V_2^* Qbar
 #   (2 k0 k); update_q: V_2 Z2 (2 k0 k).
+# With the products on tensor cores (precision 2) the leaf kernel keeps only
+# the QR and the explicit leaf Q in FP64 (4 k^2); A' moves to update_a.
 PHASE_FLOPS_PER_ROW = {
     "gram": lambda k0, k: 2 * k0 * k,
     "leaf": lambda k0, k: 2 * k0 * k + 4 * k * k,
     "apply": lambda k0, k: 2 * k * k + 2 * k0 * k,
     "update_q": lambda k0, k: 2 * k0 * k,
 }
-
+LEAF_QR_FLOPS_PER_ROW = lambda k0, k: 4 * k * k
+# bf16 tensor-core flops per trailing row of one emulated rank-k0 update (36
+# slice pairs of a real-embedded (rows x 2k0) times (2k0 x 2k) product; real: k0, k).
+EMU_UPDATE_MMA_FLOPS_PER_ROW = lambda k0, k, cplx: 2 * 36 * (2 * k0 if cplx else k0) * (2 * k if cplx else k)
+BF16_MMA_SYNC_PEAK_TFLOPS = 607.0  # mma.sync m16n8k16 bf16, measured by csrc/peak_probe.cu
 
 def b_alg(n, k0, k, cplx):
     return (16 if cplx else 8) * n * (3 * k0 + 4 * k)
@@ -83,6 +93,22 @@ def b_alg(n, k0, k, cplx):
 
 def f_alg(n, k0, k, cplx):
     return n * (8 * k0 * k + 4 * k * k) * (4 if cplx else 1)
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(bytes_per_step: float, steps: int, world_size: int, elapsed_ms: float) -> float:
+    """GB/s of the whole job: every rank ran `steps` independent problems."""
+    return bytes_per_step * world_size * steps / (elapsed_ms * 1e-3) / 1e9
 
 
 def _dist():
@@ -155,14 +181,28 @@ def _hbm_peak():
         return HBM_GBS_FALLBACK, "fallback"
 
 
+def kernel_source_hash() -> str:
+    """sha256[:16] of the device-kernel sources (FP64 and emulated kernels), with
+    comments and blank lines removed so that documentation edits keep it."""
+    import hashlib
+    import re
+    d = os.path.join(ROOT, "paper_2602_14449_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("tho_kernels.cuh", "tho_emu.cuh"):
+        for line in open(os.path.join(d, f)):
+            code = re.sub(r"//.*", "", line).strip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
 def _traffic_for(kernel: str):
     """DRAM bytes per trailing row of `kernel` from the committed ncu summary,
     or None when the kernel source changed since that capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    src = os.path.join(ROOT, "paper_2602_14449_gb300", "csrc", "tho_kernels.cuh")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = kernel_source_hash()
         for line in open(path):
             f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
             if f.get("kernel") == kernel and f.get("src") == h:
@@ -270,13 +310,7 @@ def run_batched(args):
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms / args.steps
+        return max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
 
     smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index)).split(",")[0] if ws == 1 else str(local)
     sampler = ClockSampler(smi_index)
@@ -478,29 +512,37 @@ def run_gpu(args):
     el_ms = e0.elapsed_time(e1)
     phases = plan.read_phase_timing()
     plan.set_phase_timing(False)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([el_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
+    el_ms = max_over_ranks(el_ms, dev)
     ms_step = el_ms / args.steps
     B = b_alg(n, k0, k, cplx)
-    value = B * ws * args.steps / (el_ms * 1e-3) / 1e9
+    value = replica_throughput(B, args.steps, ws, el_ms)
 
-    # Roofline of the dominant streaming kernel (FP64-ALU bound on GB300).
+    # Roofline of the dominant kernel, from the live CUDA-event phase times.
     m = n - k0
-    dom = max(PHASE_FLOPS_PER_ROW, key=lambda ph: phases[ph][0])
+    kernel_of = {"gram": "k_gram", "leaf": "k_leaf", "apply": "k_apply_gram", "update_q": "k_update_q"}
+    if prec == 2:
+        dom, flops_row = "leaf", LEAF_QR_FLOPS_PER_ROW(k0, k)
+    else:
+        dom = max(PHASE_FLOPS_PER_ROW, key=lambda ph: phases[ph][0])
+        flops_row = PHASE_FLOPS_PER_ROW[dom](k0, k)
     dom_ms, dom_groups = phases[dom]
-    flops_launch = PHASE_FLOPS_PER_ROW[dom](k0, k) * m * (4 if cplx else 1)
+    flops_launch = flops_row * m * (4 if cplx else 1)
     achieved = flops_launch / (dom_ms / dom_groups * 1e-3) / 1e12
     peak = FP32_PEAK_TFLOPS if prec == 1 else FP64_PEAK_TFLOPS
-    tr_row = _traffic_for({"gram": "k_gram", "leaf": "k_leaf", "apply": "k_apply_gram",
-                           "update_q": "k_update_q"}[dom])
+    tr_row = _traffic_for(kernel_of[dom] + ("@emu" if prec == 2 else ""))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": (tr_row * m if tr_row is not None else None), "kernel": {"gram": "k_gram", "leaf": "k_leaf",
-                "apply": "k_apply_gram", "update_q": "k_update_q"}[dom],
-                "peak_source": ("2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal; probe 1.04, k_gram sustains 1.23)" if prec == 0
-                                else "FP32 FFMA measured by peak_probe (of measured)")}
+                "traffic": (tr_row * m if tr_row is not None else None), "kernel": kernel_of[dom],
+                "share_of_step": dom_ms / args.steps / ms_step,
+                "peak_source": ("2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal; probe 1.04, k_gram sustains 1.23)"
+                                if prec != 1 else "FP32 FFMA measured by peak_probe (of measured)")}
+    roofline_tensor = None
+    if prec == 2 and phases["update_q"][1] > 0:
+        t_ms, t_groups = phases["update_q"]
+        mma = EMU_UPDATE_MMA_FLOPS_PER_ROW(k0, k, cplx) * m / (t_ms / t_groups * 1e-3) / 1e12
+        roofline_tensor = {"bound": "tensor", "kernel": "k_update_emu", "achieved": mma,
+                           "peak": BF16_MMA_SYNC_PEAK_TFLOPS, "unit": "TFLOP/s (bf16 mma.sync)",
+                           "frac": mma / BF16_MMA_SYNC_PEAK_TFLOPS,
+                           "peak_source": "mma.sync m16n8k16 bf16 measured by peak_probe (of measured)"}
     hbm, hbm_src = _hbm_peak()
     step_tflops = f_alg(n, k0, k, cplx) / (ms_step * 1e-3) / 1e12
 
@@ -535,14 +577,9 @@ def run_gpu(args):
             e2e_step()
         f1.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = f0.elapsed_time(f1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(f0.elapsed_time(f1), dev)
         esz = V.element_size()
-        e2e = {"value": B * ws * ne2e / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": replica_throughput(B, ne2e, ws, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int((V.numel() + A.numel()) * esz),
                "d2h_bytes_per_step": int((n * k + k * k + k0 * k) * esz), "steps": ne2e,
                "ms_per_step": e2e_ms / ne2e}
@@ -558,6 +595,35 @@ def run_gpu(args):
     except Exception as ex:  # the metric helper is optional for the bench line
         check = {"error": str(ex)}
 
+    # The same workload with FP64 arithmetic throughout, in the same run.
+    native = None
+    if prec == 2 and not args.no_native:
+        nplan = tho.Plan([(n, k0, k)], V.dtype, 0, 0)
+        nplan.set_phase_timing(True)
+        for _ in range(2):
+            tho.orth(V, A, prec=0, plan=nplan, Q=Q, R=R, S=S)
+        torch.cuda.synchronize(dev)
+        nplan.read_phase_timing()
+        nsteps = max(1, min(args.steps, 3))
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(nsteps):
+            tho.orth(V, A, prec=0, plan=nplan, Q=Q, R=R, S=S)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        nms = g0.elapsed_time(g1) / nsteps
+        nph = nplan.read_phase_timing()
+        lms, lgr = nph["leaf"]
+        nleaf = PHASE_FLOPS_PER_ROW["leaf"](k0, k) * (n - k0) * (4 if cplx else 1) / (lms / lgr * 1e-3) / 1e12
+        native = {"ms_per_step": nms, "value": B * ws / (nms * 1e-3) / 1e9, "unit": UNIT, "steps": nsteps,
+                  "fp64_tflops": f_alg(n, k0, k, cplx) / (nms * 1e-3) / 1e12,
+                  "roofline": {"bound": "alu", "kernel": "k_leaf", "achieved": nleaf, "peak": FP64_PEAK_TFLOPS,
+                               "unit": "TFLOP/s", "frac": nleaf / FP64_PEAK_TFLOPS,
+                               "traffic": (lambda t: t * (n - k0) if t is not None else None)(_traffic_for("k_leaf"))},
+                  "phases_ms_per_step": {ph: v[0] / nsteps for ph, v in nph.items()}}
+        nplan.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, CPU_SAMPLE_ROWS[wl])
@@ -566,12 +632,14 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": ("c128" if cplx else "f64") + {0: "", 1: "/fp32-bulk", 2: "/bf16-emulated"}[prec],
+            "vs_baseline": None,
+            "dtype": ("c128" if cplx else "f64") + {0: "", 1: " (fp32-bulk)", 2: " (fp64-accurate; products on bf16 tensor cores)"}[prec],
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "k0": k0, "k": k,
                        "l2": f"inputs larger than L2 ({(V.numel() + A.numel()) * V.element_size() / 1e9:.1f} GB)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "roofline": roofline,
+            "roofline": roofline, "roofline_tensor": roofline_tensor,
+            "fp64_native": native,
             "hbm_roof": {"peak_gbs": hbm, "source": hbm_src, "frac_of_hbm": value / ws / hbm},
             "fp64_step": {"tflops": step_tflops, "frac_of_fp64_peak": step_tflops / FP64_PEAK_TFLOPS,
                           "F_alg": f_alg(n, k0, k, cplx), "B_alg": B},
@@ -597,6 +665,7 @@ def main():
     ap.add_argument("--rows", type=int, default=0, help="override n (smaller problem of the same structure)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-native", action="store_true", help="skip the FP64-arithmetic comparison run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

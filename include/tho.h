@@ -163,9 +163,11 @@ tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, cons
  *   7 apply     Qbar = Q_leaf F and V_2^* Qbar partials (Algorithm 1, Q <- H [0; Qbar])
  *   8 solve_z2  Z2 = T^{-1} G2, head rows of Q
  *   9 update_q  Q_2 = Qbar + V_2 Z2
+ *  10 update_a  A'_2 = A_2 + V_2 Z formed before the leaf QR (THO_PREC_FP64_EMU;
+ *               otherwise the leaf phase forms it)
  * While enabled, every tho_orth call records a CUDA event pair around each
  * phase on the call's stream (tho_orth_batched is not traced). */
-#define THO_NUM_PHASES 10
+#define THO_NUM_PHASES 11
 tho_status_t tho_plan_set_phase_timing(tho_plan_t plan, int32_t enable);
 
 /* Accumulated device time (ms) and launch groups per phase of every traced

@@ -104,8 +104,8 @@ void phase_hook(void* ctx, int phase, int end, cudaStream_t st) {
   }
 }
 
-const char* const kPhaseNames[tho::kNumPhases] = {"qr_v1", "gram", "solve_z", "leaf", "tree_up",
-                                                 "root", "tree_down", "apply", "solve_z2", "update_q"};
+const char* const kPhaseNames[tho::kNumPhases] = {"qr_v1", "gram", "solve_z", "leaf", "tree_up", "root",
+                                                 "tree_down", "apply", "solve_z2", "update_q", "update_a"};
 
 }  // namespace
 
@@ -192,12 +192,17 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   pc.P = 0;
   // Emulated mode forms A' outside the leaf kernel: no Z / V staging there.
   const int leaf_k0p = pc.prec == THO_PREC_FP64_EMU && pc.any_k0 ? 0 : pc.k0pmax;
-  for (int P : {256, 128, 64}) {
-    if (P < 2 * pc.kmax) continue;
-    if (tho::leaf_smem_bytes(P, leaf_k0p, pc.kpmax, p->L->bulk_elem, p->L->elem) <= 200 * 1024) {
-      pc.P = P;
-      break;
+  // Largest leaf height whose panel lets three CTAs share an SM, else the
+  // largest that fits at all (the leaf QR's serial steps hide behind other CTAs).
+  for (int limit : {76 * 1024, 220 * 1024}) {
+    for (int P : {256, 128, 64}) {
+      if (P < 2 * pc.kmax) continue;
+      if (tho::leaf_smem_bytes(P, leaf_k0p, pc.kpmax, p->L->bulk_elem, p->L->elem) <= (size_t)limit) {
+        pc.P = P;
+        break;
+      }
     }
+    if (pc.P) break;
   }
   if (pc.P == 0) { free_plan(p); return THO_ERR_UNSUPPORTED; }
 

@@ -8,11 +8,11 @@
 // with signed 7-bit slices |s_p| <= 127, each exactly representable in bf16.
 // A slice product s_p t_q is an integer below 2^14, so FP32 accumulation of
 // the products of one "level" L = p + q (at most 8 pairs, 128 contraction
-// steps) stays below 2^24 and is exact (64 steps are used: <= 2^23).  Levels 2..9 are kept (36 slice
+// steps: at most 128 x 8 x 127^2 = 16 516 096) stays below 2^24 and is exact.  Levels 2..9 are kept (36 slice
 // pairs); the dropped levels weigh <= 2^-63 relative per product, which with
 // the 56-bit slicing leaves a normwise error of the FP64 kind, bounded by
 // (contraction length) x 2^-52 x (scale of the column of x) x (scale of y).
-// After each 64-step block the level sums are folded into two exact int64
+// After every 128 contraction steps the level sums are folded into two exact int64
 // accumulators (levels 2..5 and 6..9) and converted to FP64 once at the end.
 #pragma once
 

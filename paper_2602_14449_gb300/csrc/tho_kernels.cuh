@@ -415,32 +415,99 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
       __syncthreads();
     }
   }
-  // Householder QR of Lb(0:rb, 0:k).
-  for (int j = 0; j < k; ++j) {
-    if (warp == 0) {
-      double s = 0.0;
-      for (int i = j + lane; i < rb; i += 32) s += abs2d(Lb[i + j * P]);
-      s = warp_sum(s);
-      if (lane == 0) {
-        double b;
-        S vj, rjj;
-        make_reflector<S>(s, cvt<S, B>(Lb[j + j * P]), b, vj, rjj);
-        beta_s[j] = b;
-        vdiag[j] = cvt<B, S>(vj);
-        rdiag[j] = rjj;
+  // Blocked Householder QR of Lb(0:rb, 0:k): panels of kNB columns are
+  // factorized column by column; the trailing columns are updated with the
+  // compact form H_J ... H_{J+jb-1} = I - Y T Y^* (forward accumulation of T),
+  // as small products with one thread per output (no cross-thread reductions).
+  B* Tb = reinterpret_cast<B*>(rdiag + kMaxKP);  // T of block b: Tb[b * kNB * kNB + i + l * kNB]
+  B* Wb = Tb + kMaxKP * kNB;                      // W(l, c) = Wb[l + c * kNB]
+  auto Yv = [&](int r, int l) -> B {               // reflector l at row r (zero above its diagonal)
+    return r == l ? vdiag[l] : (r > l ? Lb[r + l * P] : zero<B>());
+  };
+  for (int J = 0; J < k; J += kNB) {
+    const int jb = min(kNB, k - J);
+    for (int j = J; j < J + jb; ++j) {
+      if (warp == 0) {
+        double sn = 0.0;
+        for (int i = j + lane; i < rb; i += 32) sn += abs2d(Lb[i + j * P]);
+        sn = warp_sum(sn);
+        if (lane == 0) {
+          double b;
+          S vj, rjj;
+          make_reflector<S>(sn, cvt<S, B>(Lb[j + j * P]), b, vj, rjj);
+          beta_s[j] = b;
+          vdiag[j] = cvt<B, S>(vj);
+          rdiag[j] = rjj;
+        }
+      }
+      __syncthreads();
+      const double b = beta_s[j];
+      if (b != 0.0) {
+        for (int c = j + 1 + warp; c < J + jb; c += nw) {
+          B d = zero<B>();
+          for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
+          d = scale(warp_sum(d), b);
+          for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
+        }
+      }
+      __syncthreads();
+    }
+    // T of this block: T(i, i) = beta_i, T(0:i, i) = -beta_i T(0:i, 0:i) (Y(:, 0:i)^* v_i).
+    B* T = Tb + (J / kNB) * kNB * kNB;
+    for (int pr = warp; pr < jb * jb; pr += nw) {  // dots t(l, i) = Y(:, J+l)^* v_{J+i}, l < i
+      const int l = pr % jb, i = pr / jb;
+      if (l >= i) continue;
+      B d = zero<B>();
+      for (int r = J + i + lane; r < rb; r += 32) d = cmadd(d, Yv(r, J + l), Yv(r, J + i));
+      d = warp_sum(d);
+      if (lane == 0) Wb[l + i * kNB] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x < jb) {
+      const int l = threadIdx.x;
+      for (int i = 0; i < jb; ++i) T[l + i * kNB] = zero<B>();
+      T[l + l * kNB] = from_real<B>(beta_s[J + l]);
+      for (int i = l + 1; i < jb; ++i) {
+        B s2 = zero<B>();
+        for (int lp = l; lp < i; ++lp) s2 = madd(s2, T[l + lp * kNB], Wb[lp + i * kNB]);
+        T[l + i * kNB] = scale(s2, -beta_s[J + i]);
       }
     }
     __syncthreads();
-    const double b = beta_s[j];
-    if (b != 0.0) {
-      for (int c = j + 1 + warp; c < k; c += nw) {
-        B d = zero<B>();
-        for (int i = j + lane; i < rb; i += 32) d = cmadd(d, i == j ? vdiag[j] : Lb[i + j * P], Lb[i + c * P]);
-        d = scale(warp_sum(d), b);
-        for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], i == j ? vdiag[j] : Lb[i + j * P], d);
+    const int c0 = J + jb, nc = k - c0;
+    if (nc > 0) {
+      // W = Y^* C (rows J..), then W <- T^* W, then C <- C - Y W.
+      for (int o = threadIdx.x; o < jb * nc; o += kThreads) {
+        const int l = o % jb, c = c0 + o / jb;
+        B d0 = zero<B>(), d1 = zero<B>();
+        int r = J + l;
+        d0 = cmadd(d0, vdiag[J + l], Lb[r + c * P]);
+        for (r = J + l + 1; r + 1 < rb; r += 2) {
+          d0 = cmadd(d0, Lb[r + (J + l) * P], Lb[r + c * P]);
+          d1 = cmadd(d1, Lb[r + 1 + (J + l) * P], Lb[r + 1 + c * P]);
+        }
+        if (r < rb) d0 = cmadd(d0, Lb[r + (J + l) * P], Lb[r + c * P]);
+        Wb[l + (c - c0) * kNB] = add(d0, d1);
       }
+      __syncthreads();
+      for (int c = threadIdx.x; c < nc; c += kThreads) {  // W(l) <- sum_{l' <= l} conj(T(l', l)) W(l'), l descending
+        for (int l = jb - 1; l >= 0; --l) {
+          B s2 = zero<B>();
+          for (int lp = 0; lp <= l; ++lp) s2 = cmadd(s2, T[lp + l * kNB], Wb[lp + c * kNB]);
+          Wb[l + c * kNB] = s2;
+        }
+      }
+      __syncthreads();
+      const int nrr = rb - J;
+      for (int o = threadIdx.x; o < nrr * nc; o += kThreads) {
+        const int r = J + o % nrr, c = c0 + o / nrr;
+        B v = Lb[r + c * P];
+        const int lmax = min(jb - 1, r - J);
+        for (int l = 0; l <= lmax; ++l) v = msub(v, Yv(r, J + l), Wb[l + (c - c0) * kNB]);
+        Lb[r + c * P] = v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   // Leaf R_b -> node (0, b); strictly upper part is in Lb rows < column.
   {
@@ -454,29 +521,67 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
     }
   }
   __syncthreads();
-  // Explicit Q_leaf = H_0 ... H_{k-1} [I; 0], in place (right to left).
-  for (int j = k - 1; j >= 0; --j) {
-    const double b = beta_s[j];
-    if (b != 0.0) {
-      for (int c = j + 1 + warp; c < k; c += nw) {
-        B d = zero<B>();
-        for (int i = j + lane; i < rb; i += 32) d = cmadd(d, i == j ? vdiag[j] : Lb[i + j * P], Lb[i + c * P]);
-        d = scale(warp_sum(d), b);
-        for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], i == j ? vdiag[j] : Lb[i + j * P], d);
+  // Explicit Q_leaf = H_0 ... H_{k-1} [I; 0], in place, blocks from the last:
+  // the block reflector on the formed columns, then the panel column by column.
+  for (int J = ((k - 1) / kNB) * kNB; J >= 0; J -= kNB) {
+    const int jb = min(kNB, k - J);
+    const B* T = Tb + (J / kNB) * kNB * kNB;
+    const int c0 = J + jb, nc = k - c0;
+    if (nc > 0) {
+      // Formed columns are zero above row c0: W = Y^* E over rows c0.., W <- T W, E <- E - Y W.
+      for (int o = threadIdx.x; o < jb * nc; o += kThreads) {
+        const int l = o % jb, c = c0 + o / jb;
+        B d0 = zero<B>(), d1 = zero<B>();
+        int r = c0;
+        for (; r + 1 < rb; r += 2) {
+          d0 = cmadd(d0, Lb[r + (J + l) * P], Lb[r + c * P]);
+          d1 = cmadd(d1, Lb[r + 1 + (J + l) * P], Lb[r + 1 + c * P]);
+        }
+        if (r < rb) d0 = cmadd(d0, Lb[r + (J + l) * P], Lb[r + c * P]);
+        Wb[l + (c - c0) * kNB] = add(d0, d1);
       }
-    }
-    __syncthreads();
-    const B vj = vdiag[j];
-    const B cvj = scale(conj_(vj), b);
-    for (int i = threadIdx.x; i < rb; i += kThreads) {
-      B v = zero<B>();
-      if (i >= j) {
-        B vi = (i == j) ? vj : Lb[i + j * P];
-        v = msub(from_real<B>(i == j ? 1.0 : 0.0), vi, cvj);
+      __syncthreads();
+      for (int c = threadIdx.x; c < nc; c += kThreads) {  // W(l) <- sum_{l' >= l} T(l, l') W(l'), l ascending
+        for (int l = 0; l < jb; ++l) {
+          B s2 = zero<B>();
+          for (int lp = l; lp < jb; ++lp) s2 = madd(s2, T[l + lp * kNB], Wb[lp + c * kNB]);
+          Wb[l + c * kNB] = s2;
+        }
       }
-      Lb[i + j * P] = v;
+      __syncthreads();
+      const int nrr = rb - J;
+      for (int o = threadIdx.x; o < nrr * nc; o += kThreads) {
+        const int r = J + o % nrr, c = c0 + o / nrr;
+        B v = Lb[r + c * P];
+        const int lmax = min(jb - 1, r - J);
+        for (int l = 0; l <= lmax; ++l) v = msub(v, Yv(r, J + l), Wb[l + (c - c0) * kNB]);
+        Lb[r + c * P] = v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    for (int j = J + jb - 1; j >= J; --j) {
+      const double b = beta_s[j];
+      if (b != 0.0) {
+        for (int c = j + 1 + warp; c < J + jb; c += nw) {
+          B d = zero<B>();
+          for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
+          d = scale(warp_sum(d), b);
+          for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
+        }
+      }
+      __syncthreads();
+      const B vj = vdiag[j];
+      const B cvj = scale(conj_(vj), b);
+      for (int i = threadIdx.x; i < rb; i += kThreads) {
+        B v = zero<B>();
+        if (i >= j) {
+          B vi = (i == j) ? vj : Lb[i + j * P];
+          v = msub(from_real<B>(i == j ? 1.0 : 0.0), vi, cvj);
+        }
+        Lb[i + j * P] = v;
+      }
+      __syncthreads();
+    }
   }
   S* Q = reinterpret_cast<S*>(io.Q);
   for (int e = threadIdx.x; e < rb * k; e += kThreads) {

@@ -84,9 +84,12 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags, EMU ? 1 : 0);
     hk(kPhSolveZ, 1, st);
   }
-  hk(kPhLeaf, 0, st);
-  if (EMU && pc.any_k0 && pc.tab.upd_n > 0)  // A'_2 = A_2 + V_2 Z on tensor cores, parked in Q
+  if (EMU && pc.any_k0 && pc.tab.upd_n > 0) {  // A'_2 = A_2 + V_2 Z on tensor cores, parked in Q
+    hk(kPhUpdateA, 0, st);
     k_update_emu<S><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 0);
+    hk(kPhUpdateA, 1, st);
+  }
+  hk(kPhLeaf, 0, st);
   k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
                                                          (EMU && pc.any_k0) ? 1 : 0);
   hk(kPhLeaf, 1, st);

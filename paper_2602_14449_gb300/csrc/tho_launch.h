@@ -57,7 +57,7 @@ struct PhaseHook {
 };
 
 enum Phase { kPhQrV1 = 0, kPhGram, kPhSolveZ, kPhLeaf, kPhTreeUp, kPhRoot, kPhTreeDown, kPhApply,
-             kPhSolveZ2, kPhUpdateQ, kNumPhases };
+             kPhSolveZ2, kPhUpdateQ, kPhUpdateA, kNumPhases };
 
 struct Launcher {
   size_t elem;       // bytes of the FP64 storage type
@@ -78,7 +78,8 @@ extern const Launcher kLaunchC128Emu;   // complex, FP64-accurate products on bf
 
 // Leaf-kernel shared memory for leaf height P (bytes).
 inline size_t leaf_smem_bytes(int P, int k0p, int kp, size_t bulk, size_t elem) {
-  return (size_t)(P * kp + k0p * kp + kTileRows * k0p) * bulk + kMaxKP * (8 + bulk + elem);
+  return (size_t)(P * kp + k0p * kp + kTileRows * k0p) * bulk + kMaxKP * (8 + bulk + elem) +
+         (size_t)2 * kMaxKP * kNB * bulk;  // T blocks and W of the blocked QR
 }
 
 }  // namespace tho

@@ -100,12 +100,15 @@ extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int
   pc.kpmax = (int)(cdiv(d->k, tho::kBJ) * tho::kBJ);
   pc.k0pmax = (int)(cdiv(d->k0, tho::kBI) * tho::kBI);
   pc.P = 0;
-  for (int P : {256, 128, 64}) {
-    if (P < 2 * pc.kmax) continue;
-    if (tho::leaf_smem_bytes(P, pc.k0pmax, pc.kpmax, L->bulk_elem, L->elem) <= 200 * 1024) {
-      pc.P = P;
-      break;
+  for (int limit : {76 * 1024, 220 * 1024}) {
+    for (int P : {256, 128, 64}) {
+      if (P < 2 * pc.kmax) continue;
+      if (tho::leaf_smem_bytes(P, pc.k0pmax, pc.kpmax, L->bulk_elem, L->elem) <= (size_t)limit) {
+        pc.P = P;
+        break;
+      }
     }
+    if (pc.P) break;
   }
   if (pc.P == 0) return THO_ERR_UNSUPPORTED;
   Inst I;

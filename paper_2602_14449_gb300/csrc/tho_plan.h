@@ -15,6 +15,7 @@ constexpr int kBR = 2, kBC = 2;  // register block of the rank-update outputs
 constexpr int kMaxK0 = 128;      // largest k0 (THO_MAX_K0)
 constexpr int kMaxKP = 32;       // largest k, padded (THO_MAX_K)
 constexpr int kRedElems = kThreads * kBI * kBJ;  // Gram cross-phase scratch (elements)
+constexpr int kNB = 8;           // panel width of the blocked leaf Householder QR
 
 // Per-call pointers of one problem (device pointers, column-major).
 struct Io {

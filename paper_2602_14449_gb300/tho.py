@@ -31,7 +31,7 @@ EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_pla
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
             "tho_orth_noalloc")
-THO_NUM_PHASES = 10
+THO_NUM_PHASES = 11
 
 
 class ThoError(RuntimeError):

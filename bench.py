@@ -181,14 +181,28 @@ def _hbm_peak():
         return HBM_GBS_FALLBACK, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """sha256[:16] of the device-kernel sources (FP64 and emulated kernels), with
-    comments and blank lines removed so that documentation edits keep it."""
+# Source files each streaming kernel is built from (its own file and the
+# helpers it includes): a traffic record stays valid while these are unchanged.
+_KERNEL_FILES = {
+    "k_gram": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh"),
+    "k_leaf": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh"),
+    "k_apply_gram": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh"),
+    "k_update_q": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh"),
+    "k_gram_emu": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh"),
+    "k_update_emu": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh"),
+    "k_tree_up": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_tree.cuh"),
+    "k_tree_down": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_tree.cuh"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """sha256[:16] of the sources `kernel` is built from, with comments and
+    blank lines removed so that documentation edits keep it."""
     import hashlib
     import re
     d = os.path.join(ROOT, "paper_2602_14449_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("tho_kernels.cuh", "tho_emu.cuh"):
+    for f in _KERNEL_FILES[kernel.split("@")[0]]:
         for line in open(os.path.join(d, f)):
             code = re.sub(r"//.*", "", line).strip()
             if code:
@@ -198,11 +212,10 @@ def kernel_source_hash() -> str:
 
 def _traffic_for(kernel: str):
     """DRAM bytes per trailing row of `kernel` from the committed ncu summary,
-    or None when the kernel source changed since that capture."""
-    import hashlib
+    or None when the kernel's sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
-        h = kernel_source_hash()
+        h = kernel_source_hash(kernel)
         for line in open(path):
             f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
             if f.get("kernel") == kernel and f.get("src") == h:
@@ -542,6 +555,7 @@ def run_gpu(args):
         roofline_tensor = {"bound": "tensor", "kernel": "k_update_emu", "achieved": mma,
                            "peak": BF16_MMA_SYNC_PEAK_TFLOPS, "unit": "TFLOP/s (bf16 mma.sync)",
                            "frac": mma / BF16_MMA_SYNC_PEAK_TFLOPS,
+                           "traffic": (lambda t: t * m if t is not None else None)(_traffic_for("k_update_emu@emu")),
                            "peak_source": "mma.sync m16n8k16 bf16 measured by peak_probe (of measured)"}
     hbm, hbm_src = _hbm_peak()
     step_tflops = f_alg(n, k0, k, cplx) / (ms_step * 1e-3) / 1e12

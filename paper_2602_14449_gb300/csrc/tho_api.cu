@@ -259,16 +259,9 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
     I.np3 = pc.prec == THO_PREC_FP64_EMU ? I.g1 : I.g3;
     I.oG3 = take((int64_t)std::max(I.g3, I.g1) * k0 * k);
     {
-      // Emulated products: 8 bf16 slices x kpe columns x padded real K (bytes -> elements).
-      const bool emu = pc.prec == THO_PREC_FP64_EMU;
-      const int64_t kpe = (k + 7) / 8 * 8, kzp = ((cplx ? 2 : 1) * k0 + 63) / 64 * 64;
+      // Emulated products: column exponents of V per chunk (ints -> elements).
       const int64_t esz = (int64_t)p->L->elem;
-      const int64_t sl = emu ? (8 * kpe * kzp * 2 + esz - 1) / esz : 1;
-      const int64_t ez = emu ? (kpe * 4 + esz - 1) / esz : 1;
-      I.oZsl1 = take(sl);
-      I.oZsl2 = take(sl);
-      I.oEz1 = take(ez);
-      I.oEz2 = take(ez);
+      I.oEv = take(pc.prec == THO_PREC_FP64_EMU ? ((int64_t)I.g1 * I.k0p * 4 + esz - 1) / esz : 1);
     }
     I.oRn = take(nodes * kk);
     I.oRef = take((nodes - I.nb) * (kk + 2 * k));

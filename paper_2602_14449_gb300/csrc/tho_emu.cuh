@@ -159,16 +159,26 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_gram_emu(const Inst* insts, 
   const int64_t r_end = min64(I.n, r_begin + I.rows1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
 
-  for (int col = warp; col < k0 + k; col += NW) {
+  // Column scales over the chunk (maximal biased exponents).  Those of V are
+  // computed by the first sweep, kept in the workspace for this chunk and
+  // reused by the later Gram and by the rank-k0 updates.
+  int* eVg = reinterpret_cast<int*>(wsp<S>(ws, I.oEv)) + (int64_t)it.idx * I.k0p;
+  for (int col = warp + (which ? k0 : 0); col < k0 + k; col += NW) {
     const double* src = col < k0 ? Vd + (int64_t)col * ldv : Ad + (int64_t)(col - k0) * lda;
     int m = 0;
     for (int64_t q = r_begin * RPE + lane; q < r_end * RPE; q += 32) m = max(m, dexp(src[q]));
     m = __reduce_max_sync(0xffffffffu, m);
     if (lane == 0) {
-      if (col < k0) eV[col] = m;
-      else eA[col - k0] = m;
+      if (col < k0) {
+        eV[col] = m;
+        eVg[col] = m;
+      } else {
+        eA[col - k0] = m;
+      }
     }
   }
+  if (which)
+    for (int col = threadIdx.x; col < k0; col += kEmuThreads) eV[col] = eVg[col];
   __syncthreads();
 
   S* out = wsp<S>(ws, which ? I.oG3 : I.oG1) + (int64_t)it.idx * k0 * k;
@@ -286,59 +296,28 @@ __device__ __forceinline__ unsigned im_pair_update(unsigned w) {
   return ((w >> 16) | (w << 16)) ^ 0x00008000u;
 }
 
-// Slices of column j of Z (k0 values of S, in shared memory) into the update's
-// B operand: out[(p * kpe + j) * kzp + q] (bf16), eZ[j] = maximal biased exponent.
-// Called by the CTA of column j of the T-solves; kzp = padded real length.
-template <class S>
-__device__ void emu_split_column(const S* z, int k0, int j, int kpe, int kzp, unsigned short* out, int* eZ) {
-  constexpr bool C = Tr<S>::C;
-  __shared__ int emax_s;
-  if (threadIdx.x == 0) emax_s = 0;
-  __syncthreads();
-  int m = 0;
-  for (int l = threadIdx.x; l < k0; l += blockDim.x) {
-    if constexpr (C) {
-      const z64 v = *reinterpret_cast<const z64*>(z + l);
-      m = max(m, max(dexp(v.x), dexp(v.y)));
-    } else {
-      m = max(m, dexp(*reinterpret_cast<const double*>(z + l)));
-    }
-  }
-  atomicMax(&emax_s, m);
-  __syncthreads();
-  const int em = emax_s;
-  if (threadIdx.x == 0) eZ[j] = em;
-  for (int q = threadIdx.x; q < kzp; q += blockDim.x) {
-    double x = 0.0;
-    if constexpr (C) {
-      if (q < 2 * k0) {
-        const z64 v = *reinterpret_cast<const z64*>(z + q / 2);
-        x = (q & 1) ? -v.y : v.x;
-      }
-    } else {
-      if (q < k0) x = *reinterpret_cast<const double*>(z + q);
-    }
-    float sl[kEmuSlices];
-    emu_split(x, em, sl);
-#pragma unroll
-    for (int p = 0; p < kEmuSlices; ++p) out[((size_t)p * kpe + j) * kzp + q] = bf16_bits(sl[p]);
-  }
-}
-
 // a5 / a9 (rank-k0 update), emulated: over one chunk of trailing rows,
 //   which = 0:  Q_2 <- A_2 + V_2 Z    (A' of the trailing block, parked in Q)
 //   which = 1:  Q_2 <- Q_2 + V_2 Z2   (Q = Qbar - W Z2 with W_2 = -V_2)
-// with the products on bf16 tensor cores: per-row scales of V over its k0
-// entries, per-column scales of Z (sliced by the T-solve kernels; all slices
-// stay resident in shared memory for the chunk).  Row tiles of TM = 16 MTt
-// rows, one 16 x 8 output tile per warp; K blocks of 64 real steps, folded
-// every 128 steps.  Shared: Zs [8][kpe][kzp + 8] | Vs [8][TM][kEmuLd] bf16 | eR.
+// with the products on bf16 tensor cores.  V is sliced with the chunk's column
+// scales 2^(e_i - 1078) of the first Gram sweep; those powers of two are moved
+// exactly into the second operand, Z'(q, j) = 2^(e_i - 1078) B(q, j) (q over the
+// real contraction index of column i), which is sliced here per column j.  So
+//   sum_q x(r, q) B(q, j) = sum_q X(r, q) Z'(q, j)
+// with X the 56-bit integers of V and every product on a common scale per j.
+// B(q, j), real:    Z(q, j);
+//          complex: B(2i, j) = Re Z(i, j), B(2i + 1, j) = -Im Z(i, j) (Re outputs);
+//          Im outputs use Im Z, Re Z, built from the packed pair by im_pair_update.
+// The V blocks (TM rows x 64 real steps) are loaded one block ahead, split into
+// a double buffer after the current block's MMAs, one barrier per block.
+// Shared: Zs [8][kpe][kzp + 8] | Vs [2][8][TM][kEmuLd] bf16 | eV [k0p] | eZ [kpe].
 template <class S>
 __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts, const Io* iot, Io io0,
                                                                const WorkItem* items, void* ws, int which) {
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
   constexpr int NW = kEmuThreads / 32;
+  constexpr int NV = 64 * kEmuKT / kEmuThreads;  // V values per thread per block (TM <= 64)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -349,11 +328,14 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
   const int MTt = max(1, min(4, NW / NT));
   const int TM = 16 * MTt;
   const int kz = RPE * k0, kzp = (kz + kEmuKT - 1) / kEmuKT * kEmuKT, ldz = kzp + 8;
+  const int nkb = kzp / kEmuKT;
   unsigned short* Zs = reinterpret_cast<unsigned short*>(smem_raw);
   unsigned short* Vs = Zs + kEmuSlices * kpe * ldz;
-  int* eR = reinterpret_cast<int*>(Vs + kEmuSlices * TM * kEmuLd);
-  const unsigned short* Zg = reinterpret_cast<const unsigned short*>(wsp<S>(ws, which ? I.oZsl2 : I.oZsl1));
-  const int* eZ = reinterpret_cast<const int*>(wsp<S>(ws, which ? I.oEz2 : I.oEz1));
+  const int vbuf = kEmuSlices * TM * kEmuLd;
+  int* eV = reinterpret_cast<int*>(Vs + 2 * vbuf);
+  int* eZ = eV + I.k0p;
+  const S* Zg = wsp<S>(ws, which ? I.oZ2 : I.oZ);
+  const int* eVg = reinterpret_cast<const int*>(wsp<S>(ws, I.oEv)) + (int64_t)it.idx * I.k0p;
   const double* Vd = reinterpret_cast<const double*>(io.V);
   const double* Bd = reinterpret_cast<const double*>(which ? io.Q : io.A);
   double* Qd = reinterpret_cast<double*>(io.Q);
@@ -367,101 +349,130 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
   const bool imag = C && nt * 8 >= kpe;
   const int jb0 = imag ? nt * 8 - kpe : nt * 8;
 
-  // All Z slices for the chunk (bf16 words, from the workspace).
-  for (int e = threadIdx.x; e < kEmuSlices * kpe * (kzp / 2); e += kEmuThreads) {
-    const int w = e % (kzp / 2), pj = e / (kzp / 2);
-    reinterpret_cast<unsigned*>(Zs + pj * ldz)[w] = reinterpret_cast<const unsigned*>(Zg + (size_t)pj * kzp)[w];
+  // Z' = diag(2^(e_i - 1078)) B, sliced per column j with its own scale.
+  for (int i = threadIdx.x; i < k0; i += kEmuThreads) eV[i] = eVg[i];
+  __syncthreads();
+  auto zp = [&](int q, int j) -> double {
+    if (q >= kz || j >= k) return 0.0;
+    const int i = q / RPE;
+    double b;
+    if constexpr (C) {
+      const z64 z = Zg[i + (int64_t)j * k0];
+      b = (q & 1) ? -z.y : z.x;
+    } else {
+      b = reinterpret_cast<const double*>(Zg)[i + (int64_t)j * k0];
+    }
+    return ldexp(b, eV[i] - 1078);
+  };
+  for (int j = warp; j < kpe; j += NW) {
+    int m = 0;
+    for (int q = lane; q < kz; q += 32) m = max(m, dexp(zp(q, j)));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) eZ[j] = m;
   }
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += TM) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < kpe * kzp; e += kEmuThreads) {
+    const int q = e % kzp, j = e / kzp;
+    float sl[kEmuSlices];
+    emu_split(zp(q, j), eZ[j], sl);
+#pragma unroll
+    for (int p = 0; p < kEmuSlices; ++p) Zs[(p * kpe + j) * ldz + q] = bf16_bits(sl[p]);
+  }
+
+  const int ntile = (int)((r_end - r_begin + TM - 1) / TM);
+  const int nblocks = ntile * nkb;
+  double val[NV];
+  auto load_block = [&](int b) {  // raw V values of block b into registers
+    const int64_t r0 = r_begin + (int64_t)(b / nkb) * TM;
+    const int kb = (b % nkb) * kEmuKT;
     const int nr = (int)min64(TM, r_end - r0);
-    __syncthreads();
-    for (int r = threadIdx.x; r < TM; r += kEmuThreads) eR[r] = 0;
-    __syncthreads();
-    {  // row scales of V over its k0 (complex: 2 k0 real) entries; r is fixed per thread
-      int m = 0;
-      const int r = threadIdx.x % TM;
-#pragma unroll 8
-      for (int e = threadIdx.x; e < TM * kz; e += kEmuThreads) {
-        const int q = e / TM;
-        if (r < nr) m = max(m, dexp(Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)]));
-      }
-      atomicMax(&eR[r], m);
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int e = threadIdx.x + u * kEmuThreads;  // e = q_local + 64 r
+      const int ql = e % kEmuKT, r = e / kEmuKT, q = kb + ql;
+      double x = 0.0;
+      if (b < nblocks && r < nr && q < kz) x = Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)];
+      val[u] = x;
     }
-    float acc[kEmuLevels][4];
-    long long hi[4], lo[4];
+  };
+  auto split_block = [&](int b, unsigned short* buf) {
+    const int kb = (b % nkb) * kEmuKT;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      hi[e] = lo[e] = 0;
+    for (int u = 0; u < NV; ++u) {
+      const int e = threadIdx.x + u * kEmuThreads;
+      const int ql = e % kEmuKT, r = e / kEmuKT, q = kb + ql;
+      if (r >= TM) continue;
+      float sl[kEmuSlices];
+      emu_split(val[u], q < kz ? eV[q / RPE] : 0, sl);
 #pragma unroll
-      for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+      for (int p = 0; p < kEmuSlices; ++p) buf[(p * TM + r) * kEmuLd + ql] = bf16_bits(sl[p]);
     }
-    for (int kb = 0; kb < kzp; kb += kEmuKT) {
-      __syncthreads();  // eR complete; the previous block's fragments consumed
-      constexpr int NV = 64 * kEmuKT / kEmuThreads;  // TM <= 64 rows: <= 8 values per thread
-      double val[NV];
+  };
+
+  float acc[kEmuLevels][4];
+  long long hi[4], lo[4];
 #pragma unroll
-      for (int u = 0; u < NV; ++u) {
-        const int e = threadIdx.x + u * kEmuThreads;  // e = q_local + 64 r
-        const int ql = e % kEmuKT, r = e / kEmuKT, q = kb + ql;
-        double x = 0.0;
-        if (r < nr && q < kz) x = Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)];
-        val[u] = x;
-      }
+  for (int e = 0; e < 4; ++e) {
+    hi[e] = lo[e] = 0;
 #pragma unroll
-      for (int u = 0; u < NV; ++u) {
-        const int e = threadIdx.x + u * kEmuThreads;
-        const int ql = e % kEmuKT, r = e / kEmuKT;
-        if (r >= TM) continue;
-        float sl[kEmuSlices];
-        emu_split(val[u], eR[r], sl);
+    for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+  }
+  load_block(0);
+  split_block(0, Vs);
+  __syncthreads();
+  for (int b = 0; b < nblocks; ++b) {
+    const int kbi = b % nkb, kb = kbi * kEmuKT;
+    const unsigned short* cur = Vs + (b & 1) * vbuf;
+    load_block(b + 1);  // in flight during the MMAs
+    if (mine) {
+      for (int ks = 0; ks < kEmuKT; ks += 16) {
+        unsigned bf[kEmuSlices][2];
 #pragma unroll
-        for (int p = 0; p < kEmuSlices; ++p) Vs[(p * TM + r) * kEmuLd + ql] = bf16_bits(sl[p]);
-      }
-      __syncthreads();
-      if (mine) {
-        for (int ks = 0; ks < kEmuKT; ks += 16) {
-          unsigned bf[kEmuSlices][2];
+        for (int qq = 0; qq < kEmuSlices; qq += 2) {
+          const int lane8 = lane >> 3, r8 = lane & 7;
+          const unsigned short* t = Zs + ((qq + ((lane8 & 2) ? 1 : 0)) * kpe) * ldz;
+          ldsm_x4(t + (jb0 + r8) * ldz + kb + ks + ((lane8 & 1) ? 8 : 0), bf[qq][0], bf[qq][1], bf[qq + 1][0],
+                  bf[qq + 1][1]);
+        }
+        if (imag) {
 #pragma unroll
-          for (int qq = 0; qq < kEmuSlices; qq += 2) {
-            const int lane8 = lane >> 3, r8 = lane & 7;
-            const unsigned short* t = Zs + ((qq + ((lane8 & 2) ? 1 : 0)) * kpe) * ldz;
-            ldsm_x4(t + (jb0 + r8) * ldz + kb + ks + ((lane8 & 1) ? 8 : 0), bf[qq][0], bf[qq][1], bf[qq + 1][0],
-                    bf[qq + 1][1]);
-          }
-          if (imag) {
-#pragma unroll
-            for (int qq = 0; qq < kEmuSlices; ++qq) {
-              bf[qq][0] = im_pair_update(bf[qq][0]);
-              bf[qq][1] = im_pair_update(bf[qq][1]);
-            }
-          }
-#pragma unroll
-          for (int p = 0; p < kEmuSlices; ++p) {
-            unsigned a[4];
-            ld_afrag(Vs + (p * TM) * kEmuLd, mt * 16, ks, a);
-#pragma unroll
-            for (int qq = 0; qq < kEmuSlices; ++qq) {
-              if (p + qq > kEmuLevels - 1) continue;
-              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
-            }
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            bf[qq][0] = im_pair_update(bf[qq][0]);
+            bf[qq][1] = im_pair_update(bf[qq][1]);
           }
         }
-        if (((kb / kEmuKT) & 1) == 1 || kb + kEmuKT >= kzp) emu_fold(acc, hi, lo);
-      }
-    }
-    if (mine) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int j = jb0 + 2 * t4 + (e & 1);
-        if (r >= nr || j >= k) continue;
-        const int sc = eR[r] + eZ[j] - 2044;
-        const double v = ldexp((double)hi[e], sc - 35) + ldexp((double)lo[e], sc - 63);
-        const int64_t ob = (int64_t)j * ldb + (r0 + r) * RPE + (imag ? 1 : 0);
-        const int64_t oq = (int64_t)j * ldq + (r0 + r) * RPE + (imag ? 1 : 0);
-        Qd[oq] = Bd[ob] + v;
+        for (int p = 0; p < kEmuSlices; ++p) {
+          unsigned a[4];
+          ld_afrag(cur + (p * TM) * kEmuLd, mt * 16, ks, a);
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            if (p + qq > kEmuLevels - 1) continue;
+            mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+          }
+        }
+      }
+      if ((kbi & 1) == 1 || kbi == nkb - 1) emu_fold(acc, hi, lo);
+      if (kbi == nkb - 1) {  // last K block of the row tile: write out = base + product
+        const int64_t r0 = r_begin + (int64_t)(b / nkb) * TM;
+        const int nr = (int)min64(TM, r_end - r0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = mt * 16 + g + (e >= 2 ? 8 : 0);
+          const int j = jb0 + 2 * t4 + (e & 1);
+          if (r < nr && j < k) {
+            const int sc = eZ[j] - 966;
+            const double v = ldexp((double)hi[e], sc - 35) + ldexp((double)lo[e], sc - 63);
+            const int64_t ob = (int64_t)j * ldb + (r0 + r) * RPE + (imag ? 1 : 0);
+            const int64_t oq = (int64_t)j * ldq + (r0 + r) * RPE + (imag ? 1 : 0);
+            Qd[oq] = Bd[ob] + v;
+          }
+          hi[e] = lo[e] = 0;
+        }
       }
     }
+    if (b + 1 < nblocks) split_block(b + 1, Vs + ((b + 1) & 1) * vbuf);
+    __syncthreads();
   }
 }
 

@@ -6,6 +6,7 @@
 #include "tho_emu.cuh"
 #include "tho_kernels.cuh"
 #include "tho_launch.h"
+#include "tho_tree.cuh"
 
 namespace tho {
 
@@ -16,7 +17,17 @@ cudaError_t configure_impl(PlanCore& pc) {
     const int kpe = (pc.kmax + 7) / 8 * 8;
     const int kzp = ((pc.dtype == 1 ? 2 : 1) * pc.k0max + kEmuKT - 1) / kEmuKT * kEmuKT;
     pc.smem_gram_emu = (size_t)kEmuSlices * kEmuLd * 2 * (64 + kpe) + sizeof(int) * (pc.k0pmax + 16 + pc.kpmax + 16);
-    pc.smem_upd_emu = (size_t)kEmuSlices * 2 * (kpe * (kzp + 8) + 64 * kEmuLd) + sizeof(int) * 64;
+    // Row tile of the update: TM = 16 MTt rows with MTt = max(1, min(4, 16 / NT)), NT output tiles.
+    pc.smem_upd_emu = 0;
+    for (const Inst& I : pc.h_insts) {
+      const int kpi = (int)(I.k + 7) / 8 * 8;
+      const int NT = ((pc.dtype == 1) ? 2 * kpi : kpi) / 8;
+      const int TM = 16 * std::max(1, std::min(4, (kEmuThreads / 32) / NT));
+      const int kzi = ((pc.dtype == 1 ? 2 : 1) * (int)I.k0 + kEmuKT - 1) / kEmuKT * kEmuKT;
+      const size_t need = (size_t)kEmuSlices * 2 * (kpi * (kzi + 8) + 2 * TM * kEmuLd) + sizeof(int) * (I.k0p + kpi);
+      pc.smem_upd_emu = std::max(pc.smem_upd_emu, need);
+    }
+    (void)kzp;
   }
   pc.smem_gram = std::max<size_t>((size_t)kTileRows * (pc.k0pmax + pc.kpmax), kRedElems) * b;
   pc.smem_apply = std::max<size_t>((size_t)(2 * kTileRows * pc.kpmax + pc.kpmax * pc.kpmax +
@@ -81,7 +92,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
       hk(kPhGram, 1, st);
     }
     hk(kPhSolveZ, 0, st);
-    k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags, EMU ? 1 : 0);
+    k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
     hk(kPhSolveZ, 1, st);
   }
   if (EMU && pc.any_k0 && pc.tab.upd_n > 0) {  // A'_2 = A_2 + V_2 Z on tensor cores, parked in Q
@@ -114,7 +125,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   hk(kPhApply, 1, st);
   if (pc.any_k0) {
     hk(kPhSolveZ2, 0, st);
-    k_solve_z2<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags, EMU ? 1 : 0);
+    k_solve_z2<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
     hk(kPhSolveZ2, 1, st);
     if (pc.tab.upd_n > 0) {
       hk(kPhUpdateQ, 0, st);

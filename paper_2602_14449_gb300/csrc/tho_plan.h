@@ -39,7 +39,7 @@ struct Inst {
   int32_t np3;           // partials of V_2^* Qbar summed by k_solve_z2 (g3, or g1 when emulated)
   int64_t rows1, rows4;  // rows per chunk of sweeps 1 and 3b (multiples of kTileRows)
   int64_t oX, oQ1, oR1, oT, oWt, oZ, oZ2, oG1, oG3, oRn, oRef, oF;
-  int64_t oZsl1, oZsl2, oEz1, oEz2;  // emulated products: bf16 slices of Z, Z2 and their column exponents
+  int64_t oEv;  // emulated products: column exponents of V per sweep-1 chunk (g1 x k0p ints)
   int64_t lev_off[kMaxLevels + 1];  // first node index of each level (R and F arrays)
   int32_t lev_cnt[kMaxLevels + 1];  // nodes per level; level 0 = leaves
 };

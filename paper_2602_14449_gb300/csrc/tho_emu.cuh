@@ -59,6 +59,12 @@ __device__ __forceinline__ void emu_split(double x, int emax, float (&s)[kEmuSli
   s[7] = sg * (float)(lo & 127u);
 }
 
+// x 2^e for an integer-valued x (|x| < 2^64): one exact multiply by 2^e built
+// from its bit pattern when 2^e is a normal number, else ldexp.
+__device__ __forceinline__ double scale2(double x, int e) {
+  return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(x, e);
+}
+
 __device__ __forceinline__ unsigned short bf16_bits(float v) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));  // exact: |v| <= 127 integer
 }
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_gram_emu(const Inst* insts, 
         const int j = jb0 + 2 * t4 + (e & 1);
         if (i >= k0 || j >= k) continue;
         const int sc = eV[i] + eA[j] - 2044;
-        const double v = ldexp((double)hi[e], sc - 35) + ldexp((double)lo[e], sc - 63);
+        const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo[e], sc - 63);
         double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
         if constexpr (C) o[imag ? 1 : 0] = v;
         else o[0] = v;
@@ -311,13 +317,15 @@ __device__ __forceinline__ unsigned im_pair_update(unsigned w) {
 // The V blocks (TM rows x 64 real steps) are loaded one block ahead, split into
 // a double buffer after the current block's MMAs, one barrier per block.
 // Shared: Zs [8][kpe][kzp + 8] | Vs [2][8][TM][kEmuLd] bf16 | eV [k0p] | eZ [kpe].
-template <class S>
+// MTM bounds the 16-row output tiles per warp column (TM <= 16 MTM rows), so
+// that the prefetched V values of a block fit in registers.
+template <class S, int MTM>
 __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts, const Io* iot, Io io0,
                                                                const WorkItem* items, void* ws, int which) {
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
   constexpr int NW = kEmuThreads / 32;
-  constexpr int NV = 64 * kEmuKT / kEmuThreads;  // V values per thread per block (TM <= 64)
+  constexpr int NV = 16 * MTM * kEmuKT / kEmuThreads;  // V values per thread per block
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
   const int k0 = (int)I.k0, k = (int)I.k;
   const int kpe = (k + 7) / 8 * 8;
   const int NT = (C ? 2 * kpe : kpe) / 8;
-  const int MTt = max(1, min(4, NW / NT));
+  const int MTt = max(1, min(MTM, NW / NT));
   const int TM = 16 * MTt;
   const int kz = RPE * k0, kzp = (kz + kEmuKT - 1) / kEmuKT * kEmuKT, ldz = kzp + 8;
   const int nkb = kzp / kEmuKT;
@@ -462,7 +470,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
           const int j = jb0 + 2 * t4 + (e & 1);
           if (r < nr && j < k) {
             const int sc = eZ[j] - 966;
-            const double v = ldexp((double)hi[e], sc - 35) + ldexp((double)lo[e], sc - 63);
+            const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo[e], sc - 63);
             const int64_t ob = (int64_t)j * ldb + (r0 + r) * RPE + (imag ? 1 : 0);
             const int64_t oq = (int64_t)j * ldq + (r0 + r) * RPE + (imag ? 1 : 0);
             Qd[oq] = Bd[ob] + v;

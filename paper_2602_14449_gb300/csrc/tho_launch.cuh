@@ -10,6 +10,17 @@
 
 namespace tho {
 
+template <class S>
+void launch_update_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
+                       void* ws, int which, cudaStream_t st) {
+  if (pc.upd_mt == 1)
+    k_update_emu<S, 1><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items, ws, which);
+  else if (pc.upd_mt == 2)
+    k_update_emu<S, 2><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items, ws, which);
+  else
+    k_update_emu<S, 4><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items, ws, which);
+}
+
 template <class S, class B, bool EMU>
 cudaError_t configure_impl(PlanCore& pc) {
   const size_t b = sizeof(B);
@@ -19,10 +30,13 @@ cudaError_t configure_impl(PlanCore& pc) {
     pc.smem_gram_emu = (size_t)kEmuSlices * kEmuLd * 2 * (64 + kpe) + sizeof(int) * (pc.k0pmax + 16 + pc.kpmax + 16);
     // Row tile of the update: TM = 16 MTt rows with MTt = max(1, min(4, 16 / NT)), NT output tiles.
     pc.smem_upd_emu = 0;
+    pc.upd_mt = 1;
     for (const Inst& I : pc.h_insts) {
       const int kpi = (int)(I.k + 7) / 8 * 8;
       const int NT = ((pc.dtype == 1) ? 2 * kpi : kpi) / 8;
-      const int TM = 16 * std::max(1, std::min(4, (kEmuThreads / 32) / NT));
+      const int MTt = std::max(1, std::min(4, (kEmuThreads / 32) / NT));
+      const int TM = 16 * MTt;
+      pc.upd_mt = std::max(pc.upd_mt, MTt == 3 ? 4 : MTt);
       const int kzi = ((pc.dtype == 1 ? 2 : 1) * (int)I.k0 + kEmuKT - 1) / kEmuKT * kEmuKT;
       const size_t need = (size_t)kEmuSlices * 2 * (kpi * (kzi + 8) + 2 * TM * kEmuLd) + sizeof(int) * (I.k0p + kpi);
       pc.smem_upd_emu = std::max(pc.smem_upd_emu, need);
@@ -35,7 +49,7 @@ cudaError_t configure_impl(PlanCore& pc) {
                                    kRedElems) * b;
   pc.smem_upd = (size_t)(pc.k0pmax * pc.kpmax + kTileRows * pc.k0pmax) * b;
   pc.smem_leaf = leaf_smem_bytes(pc.P, (EMU && pc.any_k0) ? 0 : pc.k0pmax, pc.kpmax, b, sizeof(S));
-  pc.smem_tree = (size_t)(3 * pc.kmax * pc.kmax + 2 * pc.kmax) * sizeof(S);
+  pc.smem_tree = (size_t)(pc.kmax * pc.kmax + 2 * pc.kmax) * sizeof(S);  // reflectors of one node
   // The dynamic shared-memory limit is a per-kernel, per-device attribute shared
   // by every plan: raise it to the device's opt-in maximum less the kernel's
   // static shared memory (never lower it), so a plan built later with smaller
@@ -55,11 +69,14 @@ cudaError_t configure_impl(PlanCore& pc) {
   };
   if ((e = raise((const void*)k_gram<S, B>, pc.smem_gram)) != cudaSuccess) return e;
   if (EMU && (e = raise((const void*)k_gram_emu<S>, pc.smem_gram_emu)) != cudaSuccess) return e;
-  if (EMU && (e = raise((const void*)k_update_emu<S>, pc.smem_upd_emu)) != cudaSuccess) return e;
+  if (EMU) {
+    const void* f = pc.upd_mt == 1 ? (const void*)k_update_emu<S, 1>
+                    : pc.upd_mt == 2 ? (const void*)k_update_emu<S, 2> : (const void*)k_update_emu<S, 4>;
+    if ((e = raise(f, pc.smem_upd_emu)) != cudaSuccess) return e;
+  }
   if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
-  if ((e = raise((const void*)k_tree_up<S>, pc.smem_tree)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
   int n = 0;
@@ -97,7 +114,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   }
   if (EMU && pc.any_k0 && pc.tab.upd_n > 0) {  // A'_2 = A_2 + V_2 Z on tensor cores, parked in Q
     hk(kPhUpdateA, 0, st);
-    k_update_emu<S><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 0);
+    launch_update_emu<S>(pc, insts, d_io, io0, items + pc.tab.upd_off, ws, 0, st);
     hk(kPhUpdateA, 1, st);
   }
   hk(kPhLeaf, 0, st);
@@ -107,7 +124,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   hk(kPhTreeUp, 0, st);
   for (int l = 1; l <= pc.Lmax; ++l)
     if (pc.tab.lev_n[l] > 0)
-      k_tree_up<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+      k_tree_up<S><<<pc.tab.lev_n[l], kTreeThreads, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   hk(kPhTreeUp, 1, st);
   hk(kPhRoot, 0, st);
   k_root<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
@@ -130,7 +147,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     if (pc.tab.upd_n > 0) {
       hk(kPhUpdateQ, 0, st);
       if (EMU)
-        k_update_emu<S><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws, 1);
+        launch_update_emu<S>(pc, insts, d_io, io0, items + pc.tab.upd_off, ws, 1, st);
       else
         k_update_q<S, B><<<pc.tab.upd_n, blk, pc.smem_upd, st>>>(insts, d_io, io0, items + pc.tab.upd_off, ws);
       hk(kPhUpdateQ, 1, st);

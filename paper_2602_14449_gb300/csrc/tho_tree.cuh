@@ -9,16 +9,45 @@
 namespace tho {
 
 // ------------------------------------------------------------------------------
+// Thread layout of the tree kernels: one CTA per node, one thread per (column
+// c, row group g) with g = 0..3 holding the rows r = g + 4 i (i < 8) of column
+// c.  The four threads of a column are adjacent lanes of one warp and combine
+// their partial sums with two xor shuffles; the combination is symmetric, so
+// all four hold bitwise the same sum and update their copies of the column's
+// top entry identically.
+constexpr int kTreeRG = 4;                      // row groups per column
+constexpr int kTreeRows = kMaxKP / kTreeRG;     // rows per thread
+constexpr int kTreeThreads = kMaxKP * kTreeRG;  // 128
+
+__device__ __forceinline__ unsigned tree_mask4() { return 0xFu << (threadIdx.x & 28u); }
+
+__device__ __forceinline__ double tree_sum4(double v, unsigned m) {
+  v += __shfl_xor_sync(m, v, 1);
+  return v + __shfl_xor_sync(m, v, 2);
+}
+__device__ __forceinline__ z64 tree_sum4(z64 v, unsigned m) {
+  v.x += __shfl_xor_sync(m, v.x, 1);
+  v.y += __shfl_xor_sync(m, v.y, 1);
+  v.x += __shfl_xor_sync(m, v.x, 2);
+  v.y += __shfl_xor_sync(m, v.y, 2);
+  return v;
+}
+
 // a7 (tree, upward): node i of level `lev` combines children 2i, 2i+1 of level
 // lev-1 by a Householder QR of [R_a; R_b].  With both blocks upper triangular,
-// reflector j touches only top row j and bottom rows 0..j.  One thread owns one
-// trailing column (no cross-thread reductions: every FP64 instruction is useful
-// work).  Reflectors are kept (bottom part k x k upper triangular, top
-// entries, betas) for the downward pass.  Launched with kTreeThreads threads.
-constexpr int kTreeThreads = 64;
+// reflector j touches only top row j and bottom rows 0..j; its vector is
+// (v_j at top row j, column j of the bottom block below).  The bottom block
+// stays in registers; the top row j of each column is read when step j
+// reaches it (prefetched one step ahead) and is final after that step.  The
+// reflector of step j is formed by the threads of column j and broadcast
+// through a double-buffered shared array: one barrier per step.  Kept per node
+// for the downward pass: the bottom parts (k x k upper triangular), the top
+// entries v_j and the betas.
 template <class S>
 __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, const WorkItem* items, void* ws, int lev) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ S ush[2][kMaxKP];
+  __shared__ S vsh[2];
+  __shared__ double bsh[2];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
   const int k = (int)I.k, kk = k * k;
@@ -32,52 +61,82 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
     for (int e = threadIdx.x; e < kk; e += blockDim.x) Rdst[e] = Rn[c0 * kk + e];
     return;
   }
-  S* X = reinterpret_cast<S*>(smem_raw);  // 2k x k, ld 2k
-  __shared__ double beta_s[kMaxKP];
-  __shared__ S vtop[kMaxKP];
-  __shared__ S rdiag[kMaxKP];
-  const int ld = 2 * k;
-  for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
-    int r = e % ld, c = e / ld;
-    X[e] = (r < k) ? Rn[c0 * kk + r + c * k] : Rn[(c0 + 1) * kk + (r - k) + c * k];
+  const S* Ra = Rn + c0 * kk;
+  const S* Rb = Ra + kk;
+  const int c = threadIdx.x / kTreeRG, g = threadIdx.x % kTreeRG;
+  const bool own = c < k;
+  const unsigned m4 = tree_mask4();
+  S xb[kTreeRows];
+#pragma unroll
+  for (int q = 0; q < kTreeRows; ++q) {
+    const int r = g + kTreeRG * q;
+    xb[q] = (own && r <= c) ? Rb[r + c * k] : zero<S>();
   }
-  __syncthreads();
-  const int t = threadIdx.x;
-  for (int j = 0; j < k; ++j) {
-    if (t == 0) {
-      S xj = X[j + j * ld];
-      double s = abs2d(xj);
-      for (int r = 0; r <= j; ++r) s += abs2d(X[k + r + j * ld]);
-      double b;
-      S vj, rjj;
-      make_reflector<S>(s, xj, b, vj, rjj);
-      beta_s[j] = b;
-      vtop[j] = vj;
-      rdiag[j] = rjj;
+  S xt = own ? Ra[c * k] : zero<S>();  // top row j of column c at step j
+  S vmine = zero<S>(), rmine = zero<S>();
+  double bmine = 0.0;
+  // Steps are unrolled so that every row loop stops at step j's last row
+  // (the FP64 pipe is charged for predicated-off lanes too).
+#pragma unroll
+  for (int j = 0; j < kMaxKP; ++j) {
+    if (j >= k) break;
+    const int buf = j & 1;
+    const S xt_next = (own && j + 1 < k) ? Ra[(j + 1) + c * k] : zero<S>();
+    if (c == j) {
+      double s = (g == 0) ? abs2d(xt) : 0.0;
+#pragma unroll
+      for (int q = 0; q <= j / kTreeRG; ++q)
+        if (g + kTreeRG * q <= j) s += abs2d(xb[q]);
+      s = tree_sum4(s, m4);
+      make_reflector<S>(s, xt, bmine, vmine, rmine);
+      if (g == 0) {
+        bsh[buf] = bmine;
+        vsh[buf] = vmine;
+      }
+#pragma unroll
+      for (int q = 0; q <= j / kTreeRG; ++q) {
+        const int r = g + kTreeRG * q;
+        if (r <= j) ush[buf][r] = xb[q];
+      }
     }
     __syncthreads();
-    const double b = beta_s[j];
-    const int c = j + 1 + t;
-    if (b != 0.0 && c < k) {
-      S* xc = X + c * ld;
-      const S* xv = X + j * ld;
-      S d = cmadd(zero<S>(), vtop[j], xc[j]);
-      for (int r = 0; r <= j; ++r) d = cmadd(d, xv[k + r], xc[k + r]);
-      d = scale(d, b);
-      xc[j] = msub(xc[j], vtop[j], d);
-      for (int r = 0; r <= j; ++r) xc[k + r] = msub(xc[k + r], xv[k + r], d);
+    if (own && c > j) {
+      const double b = bsh[buf];
+      if (b != 0.0) {
+        const S vj = vsh[buf];
+        S d = (g == 0) ? cmadd(zero<S>(), vj, xt) : zero<S>();
+#pragma unroll
+        for (int q = 0; q <= j / kTreeRG; ++q) {
+          const int r = g + kTreeRG * q;
+          if (r <= j) d = cmadd(d, ush[buf][r], xb[q]);
+        }
+        d = scale(tree_sum4(d, m4), b);
+        xt = msub(xt, vj, d);
+#pragma unroll
+        for (int q = 0; q <= j / kTreeRG; ++q) {
+          const int r = g + kTreeRG * q;
+          if (r <= j) xb[q] = msub(xb[q], ush[buf][r], d);
+        }
+      }
+      if (g == 0) Rdst[j + c * k] = xt;  // entry (j, c) of the node's R is final
     }
-    __syncthreads();
+    xt = xt_next;
   }
+  if (!own) return;
+  // Column c is untouched after its own step: its bottom part is reflector c's.
   S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
-  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-    int r = e % k, c = e / k;
-    Rdst[e] = (r < c) ? X[r + c * ld] : (r == c ? rdiag[c] : zero<S>());
-    ref[e] = (r <= c) ? X[k + r + c * ld] : zero<S>();
+#pragma unroll
+  for (int q = 0; q < kTreeRows; ++q) {
+    const int r = g + kTreeRG * q;
+    if (r < k) {
+      ref[r + c * k] = (r <= c) ? xb[q] : zero<S>();
+      if (r > c) Rdst[r + c * k] = zero<S>();
+    }
   }
-  for (int e = threadIdx.x; e < k; e += blockDim.x) {
-    ref[kk + e] = vtop[e];
-    ref[kk + k + e] = from_real<S>(beta_s[e]);
+  if (g == 0) {
+    Rdst[c + c * k] = rmine;
+    ref[kk + c] = vmine;
+    ref[kk + k + c] = from_real<S>(bmine);
   }
 }
 
@@ -108,8 +167,10 @@ __global__ void k_root(const Inst* insts, const Io* iot, Io io0, void* ws, int* 
 }
 
 // a7 (tree, downward): parent node i of level `lev` (lev >= 1) gives its children
-// [F_{2i}; F_{2i+1}] = H_0 ... H_{k-1} [F_i; 0].  One thread per column of F; the
-// node's reflectors are staged in shared memory.  Launched with kTreeThreads threads.
+// [F_{2i}; F_{2i+1}] = H_0 ... H_{k-1} [F_i; 0].  The node's reflectors are
+// staged in shared memory once; the bottom block stays in registers, the top
+// row j of each column is read at step j (prefetched one step ahead) and is
+// final after it.  Columns are independent: no barrier inside the loop.
 template <class S>
 __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, const WorkItem* items, void* ws, int lev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -126,36 +187,50 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, c
     for (int e = threadIdx.x; e < kk; e += blockDim.x) F[c0 * kk + e] = Fi[e];
     return;
   }
-  S* E = reinterpret_cast<S*>(smem_raw);  // 2k x k, ld 2k
-  S* Rf = E + 2 * kk;                     // reflectors: k x k bottom parts | k tops | k betas
-  const int ld = 2 * k;
+  S* Rf = reinterpret_cast<S*>(smem_raw);  // k x k bottom parts | k tops | k betas
   const S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
-  for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
-    int r = e % ld, c = e / ld;
-    E[e] = (r < k) ? Fi[r + c * k] : zero<S>();
-  }
   for (int e = threadIdx.x; e < kk + 2 * k; e += blockDim.x) Rf[e] = ref[e];
   __syncthreads();
-  const int c = threadIdx.x;
-  if (c < k) {
-    S* ec = E + c * ld;
-    for (int j = k - 1; j >= 0; --j) {
-      const double b = real_(Rf[kk + k + j]);
-      if (b == 0.0) continue;
+  const int c = threadIdx.x / kTreeRG, g = threadIdx.x % kTreeRG;
+  if (c >= k) return;
+  const unsigned m4 = tree_mask4();
+  S* Fa = F + c0 * kk;
+  S* Fb = Fa + kk;
+  S eb[kTreeRows];
+#pragma unroll
+  for (int q = 0; q < kTreeRows; ++q) eb[q] = zero<S>();
+  S et = Fi[(k - 1) + c * k];
+  // Unrolled steps (j = k-1 down to 0): row loops stop at step j's last row.
+#pragma unroll
+  for (int jj = 0; jj < kMaxKP; ++jj) {
+    const int j = kMaxKP - 1 - jj;
+    if (j >= k) continue;
+    const S et_next = j > 0 ? Fi[(j - 1) + c * k] : zero<S>();
+    const double b = real_(Rf[kk + k + j]);
+    if (b != 0.0) {
       const S vt = Rf[kk + j];
-      const S* vb = Rf + j * k;
-      S d = cmadd(zero<S>(), vt, ec[j]);
-      for (int r = 0; r <= j; ++r) d = cmadd(d, vb[r], ec[k + r]);
-      d = scale(d, b);
-      ec[j] = msub(ec[j], vt, d);
-      for (int r = 0; r <= j; ++r) ec[k + r] = msub(ec[k + r], vb[r], d);
+      const S* u = Rf + j * k;
+      S d = (g == 0) ? cmadd(zero<S>(), vt, et) : zero<S>();
+#pragma unroll
+      for (int q = 0; q <= j / kTreeRG; ++q) {
+        const int r = g + kTreeRG * q;
+        if (r <= j) d = cmadd(d, u[r], eb[q]);
+      }
+      d = scale(tree_sum4(d, m4), b);
+      et = msub(et, vt, d);
+#pragma unroll
+      for (int q = 0; q <= j / kTreeRG; ++q) {
+        const int r = g + kTreeRG * q;
+        if (r <= j) eb[q] = msub(eb[q], u[r], d);
+      }
     }
+    if (g == 0) Fa[j + c * k] = et;
+    et = et_next;
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-    int r = e % k, cc = e / k;
-    F[c0 * kk + e] = E[r + cc * ld];
-    F[(c0 + 1) * kk + e] = E[k + r + cc * ld];
+#pragma unroll
+  for (int q = 0; q < kTreeRows; ++q) {
+    const int r = g + kTreeRG * q;
+    if (r < k) Fb[r + c * k] = eb[q];
   }
 }
 

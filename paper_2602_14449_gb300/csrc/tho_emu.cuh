@@ -59,8 +59,9 @@ __device__ __forceinline__ void emu_split(double x, int emax, float (&s)[kEmuSli
   s[7] = sg * (float)(lo & 127u);
 }
 
-// x 2^e for an integer-valued x (|x| < 2^64): one exact multiply by 2^e built
-// from its bit pattern when 2^e is a normal number, else ldexp.
+// x 2^e: one multiply by the power of two 2^e, built from its bit pattern,
+// when 2^e is a normal number (the product is then x 2^e correctly rounded,
+// exact unless it leaves the normal range), else ldexp.
 __device__ __forceinline__ double scale2(double x, int e) {
   return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(x, e);
 }
@@ -481,6 +482,148 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
     }
     if (b + 1 < nblocks) split_block(b + 1, Vs + ((b + 1) & 1) * vbuf);
     __syncthreads();
+  }
+}
+
+// a8 (sweep 3a), emulated: for each leaf b of a chunk, Qbar_b = Q_leaf,b F_b in
+// place in the rows of Q, with the product on bf16 tensor cores.  The leaf's Q
+// factor is staged in shared memory (row-major, padded rows); its column scales
+// 2^(e_i - 1078) (maximal exponent of column i over the leaf) are moved exactly
+// into the second operand, F'(q, j) = 2^(e_i - 1078) B(q, j) with B the real
+// embedding of F_b used by the rank-k0 update, which is sliced per column j.
+// The contraction (k columns, real-embedded) is at most 64 steps: one fold.
+// Shared: Qr [P][k+1] S | Fr [k][k] S | Zs [8][kpe][kEmuLd] | Vs [8][TM][kEmuLd] bf16 | eV | eZ.
+template <class S, int MTM>
+__global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
+                                                              const WorkItem* items, void* ws, int P) {
+  constexpr bool C = Tr<S>::C;
+  constexpr int RPE = C ? 2 : 1;
+  constexpr int NW = kEmuThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const Io io = get_io(iot, io0, it.inst);
+  const int k = (int)I.k, kk = k * k, ldr = k + 1;
+  const int kpe = (k + 7) / 8 * 8;
+  const int NT = (C ? 2 * kpe : kpe) / 8;
+  const int MTt = max(1, min(MTM, NW / NT));
+  const int TM = 16 * MTt;
+  const int kz = RPE * k, kzp = (kz + 15) / 16 * 16;
+  S* Qr = reinterpret_cast<S*>(smem_raw);
+  S* Fr = Qr + ((size_t)P * ldr + 1) / 2 * 2;
+  unsigned short* Zs = reinterpret_cast<unsigned short*>(Fr + (kk + 1) / 2 * 2);
+  unsigned short* Vs = Zs + kEmuSlices * kpe * kEmuLd;
+  int* eV = reinterpret_cast<int*>(Vs + kEmuSlices * TM * kEmuLd);
+  int* eZ = eV + kMaxKP;
+  S* Qg = reinterpret_cast<S*>(io.Q);
+  const int64_t ldq = io.ldq;
+  const S* Fg = wsp<S>(ws, I.oF);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+  const bool mine = warp < MTt * NT;
+  const int mt = mine ? warp / NT : 0, nt = mine ? warp % NT : 0;
+  const bool imag = C && nt * 8 >= kpe;
+  const int jb0 = imag ? nt * 8 - kpe : nt * 8;
+  const int b_begin = it.idx * I.leaves3;
+  const int b_end = min(I.nb, b_begin + I.leaves3);
+  for (int lb = b_begin; lb < b_end; ++lb) {
+    const int64_t lo = leaf_lo(I, lb);
+    const int rb = (int)(leaf_lo(I, lb + 1) - lo);
+    const S* Fb = Fg + (I.lev_off[0] + lb) * (int64_t)kk;
+    __syncthreads();  // the previous leaf is done with every buffer
+    for (int e = threadIdx.x; e < k * rb; e += kEmuThreads) {
+      const int r = e % rb, i = e / rb;
+      Qr[r * ldr + i] = Qg[(lo + r) + (int64_t)i * ldq];
+    }
+    for (int e = threadIdx.x; e < kk; e += kEmuThreads) Fr[e] = Fb[e];
+    __syncthreads();
+    for (int i = warp; i < k; i += NW) {
+      int m = 0;
+      for (int q = lane; q < rb * RPE; q += 32)
+        m = max(m, dexp(reinterpret_cast<const double*>(Qr + (q / RPE) * ldr + i)[q % RPE]));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) eV[i] = m;
+    }
+    __syncthreads();
+    auto fp = [&](int q, int j) -> double {
+      if (q >= kz || j >= k) return 0.0;
+      const int i = q / RPE;
+      double b;
+      if constexpr (C) {
+        const z64 z = Fr[i + j * k];
+        b = (q & 1) ? -z.y : z.x;
+      } else {
+        b = reinterpret_cast<const double*>(Fr)[i + j * k];
+      }
+      return scale2(b, eV[i] - 1078);
+    };
+    for (int j = warp; j < kpe; j += NW) {
+      int m = 0;
+      for (int q = lane; q < kz; q += 32) m = max(m, dexp(fp(q, j)));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) eZ[j] = m;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kpe * kzp; e += kEmuThreads) {
+      const int q = e % kzp, j = e / kzp;
+      float sl[kEmuSlices];
+      emu_split(fp(q, j), eZ[j], sl);
+#pragma unroll
+      for (int p = 0; p < kEmuSlices; ++p) Zs[(p * kpe + j) * kEmuLd + q] = bf16_bits(sl[p]);
+    }
+    for (int r0 = 0; r0 < rb; r0 += TM) {
+      __syncthreads();  // Zs complete; the previous row tile's MMAs are done with Vs
+      for (int e = threadIdx.x; e < TM * kzp; e += kEmuThreads) {
+        const int q = e % kzp, r = e / kzp;
+        double x = 0.0;
+        if (q < kz && r0 + r < rb) x = reinterpret_cast<const double*>(Qr + (r0 + r) * ldr + q / RPE)[q % RPE];
+        float sl[kEmuSlices];
+        emu_split(x, q < kz ? eV[q / RPE] : 0, sl);
+#pragma unroll
+        for (int p = 0; p < kEmuSlices; ++p) Vs[(p * TM + r) * kEmuLd + q] = bf16_bits(sl[p]);
+      }
+      __syncthreads();
+      if (!mine) continue;
+      float acc[kEmuLevels][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+      for (int ks = 0; ks < kzp; ks += 16) {
+        unsigned bf[kEmuSlices][2];
+#pragma unroll
+        for (int qq = 0; qq < kEmuSlices; qq += 2)
+          ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, jb0, ks, bf[qq], bf[qq + 1]);
+        if (imag) {
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            bf[qq][0] = im_pair_update(bf[qq][0]);
+            bf[qq][1] = im_pair_update(bf[qq][1]);
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < kEmuSlices; ++p) {
+          unsigned a[4];
+          ld_afrag(Vs + (p * TM) * kEmuLd, mt * 16, ks, a);
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            if (p + qq > kEmuLevels - 1) continue;
+            mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+          }
+        }
+      }
+      long long hi[4] = {0, 0, 0, 0}, lo4[4] = {0, 0, 0, 0};
+      emu_fold(acc, hi, lo4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = r0 + mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = jb0 + 2 * t4 + (e & 1);
+        if (r < rb && j < k) {
+          const int sc = eZ[j] - 966;
+          const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+          reinterpret_cast<double*>(Qg + (lo + r) + (int64_t)j * ldq)[imag ? 1 : 0] = v;
+        }
+      }
+    }
   }
 }
 

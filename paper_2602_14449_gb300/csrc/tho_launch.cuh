@@ -21,6 +21,17 @@ void launch_update_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, co
     k_update_emu<S, 4><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items, ws, which);
 }
 
+template <class S>
+void launch_apply_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
+                      void* ws, cudaStream_t st) {
+  if (pc.upd_mt == 1)
+    k_apply_emu<S, 1><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P);
+  else if (pc.upd_mt == 2)
+    k_apply_emu<S, 2><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P);
+  else
+    k_apply_emu<S, 4><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P);
+}
+
 template <class S, class B, bool EMU>
 cudaError_t configure_impl(PlanCore& pc) {
   const size_t b = sizeof(B);
@@ -42,6 +53,10 @@ cudaError_t configure_impl(PlanCore& pc) {
       pc.smem_upd_emu = std::max(pc.smem_upd_emu, need);
     }
     (void)kzp;
+    // Emulated apply: staged leaf Q (P x (k+1)), F_b, slices of F' and of one row tile.
+    const int kpm = (pc.kmax + 7) / 8 * 8;
+    pc.smem_apply_emu = (((size_t)pc.P * (pc.kmax + 1) + 1) / 2 * 2 + ((size_t)pc.kmax * pc.kmax + 1) / 2 * 2) * sizeof(S) +
+                        (size_t)kEmuSlices * 2 * kEmuLd * (kpm + 16 * pc.upd_mt) + sizeof(int) * 2 * kMaxKP;
   }
   pc.smem_gram = std::max<size_t>((size_t)kTileRows * (pc.k0pmax + pc.kpmax), kRedElems) * b;
   pc.smem_apply = std::max<size_t>((size_t)(2 * kTileRows * pc.kpmax + pc.kpmax * pc.kpmax +
@@ -73,6 +88,9 @@ cudaError_t configure_impl(PlanCore& pc) {
     const void* f = pc.upd_mt == 1 ? (const void*)k_update_emu<S, 1>
                     : pc.upd_mt == 2 ? (const void*)k_update_emu<S, 2> : (const void*)k_update_emu<S, 4>;
     if ((e = raise(f, pc.smem_upd_emu)) != cudaSuccess) return e;
+    const void* fa = pc.upd_mt == 1 ? (const void*)k_apply_emu<S, 1>
+                     : pc.upd_mt == 2 ? (const void*)k_apply_emu<S, 2> : (const void*)k_apply_emu<S, 4>;
+    if ((e = raise(fa, pc.smem_apply_emu)) != cudaSuccess) return e;
   }
   if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
@@ -135,8 +153,10 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
       k_tree_down<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   hk(kPhTreeDown, 1, st);
   hk(kPhApply, 0, st);
-  k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws,
-                                                                 EMU ? 0 : 1);
+  if (EMU)  // Qbar_b = Q_leaf,b F_b on tensor cores
+    launch_apply_emu<S>(pc, insts, d_io, io0, items + pc.tab.apply_off, ws, st);
+  else
+    k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws, 1);
   if (EMU && pc.any_k0 && pc.tab.gram_n > 0)  // V_2^* Qbar on tensor cores, into the G3 partials
     k_gram_emu<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 1);
   hk(kPhApply, 1, st);

@@ -42,7 +42,8 @@ struct PlanCore {
   size_t ws_elems = 0;
   int* d_status = nullptr;
   size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
-  int upd_mt = 4;  // emulated update: 16-row tiles per warp column (max over problems)
+  int upd_mt = 4;  // emulated update / apply: 16-row tiles per warp column (max over problems)
+  size_t smem_apply_emu = 0;
   size_t smem_gram_emu = 0;  // emulated split-n Gram (THO_PREC_FP64_EMU)
   size_t smem_upd_emu = 0;   // emulated rank-k0 update
   int launches = 0;  // kernel launches per call

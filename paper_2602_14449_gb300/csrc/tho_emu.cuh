@@ -66,6 +66,45 @@ __device__ __forceinline__ double scale2(double x, int e) {
   return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(x, e);
 }
 
+// The 56-bit fixed-point magnitude of x relative to emax, as its top and bottom
+// 28 bits, and the sign (the integer emu_split slices).
+__device__ __forceinline__ void emu_fixed56(double x, int emax, unsigned& h, unsigned& l, bool& neg) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  unsigned long long X = 0;
+  if (e != 0) {
+    const unsigned long long M = (bits & 0xfffffffffffffULL) | 0x10000000000000ULL;
+    const int sh = e - emax + 3;  // <= 3
+    X = sh >= 0 ? (M << sh) : (-sh >= 64 ? 0ULL : (M >> -sh));
+  }
+  h = (unsigned)(X >> 28);
+  l = (unsigned)(X & 0xfffffffu);
+  neg = bits < 0;
+}
+
+// The eight slices of two values (x0 with scale emax0, x1 with emax1) as packed
+// bf16 pairs: w[p] holds slice p of x0 in its low half and of x1 in its high
+// half.  A slice magnitude a <= 127 becomes a float by the exact magic-number
+// subtraction (2^23 + a) - 2^23; its top 16 bits are its bf16 pattern (exact:
+// a has at most 7 significant bits); the signs are OR-ed in.
+__device__ __forceinline__ void emu_split2(double x0, double x1, int emax0, int emax1,
+                                           unsigned (&w)[kEmuSlices]) {
+  unsigned h0, l0, h1, l1;
+  bool n0, n1;
+  emu_fixed56(x0, emax0, h0, l0, n0);
+  emu_fixed56(x1, emax1, h1, l1, n1);
+  const unsigned sg = (n0 ? 0x8000u : 0u) | (n1 ? 0x80000000u : 0u);
+#pragma unroll
+  for (int p = 0; p < kEmuSlices; ++p) {
+    const int sh = 21 - 7 * (p & 3);
+    const unsigned a0 = ((p < 4 ? h0 : l0) >> sh) & 127u;
+    const unsigned a1 = ((p < 4 ? h1 : l1) >> sh) & 127u;
+    const float f0 = __uint_as_float(0x4B000000u | a0) - 8388608.0f;
+    const float f1 = __uint_as_float(0x4B000000u | a1) - 8388608.0f;
+    w[p] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | sg;
+  }
+}
+
 __device__ __forceinline__ unsigned short bf16_bits(float v) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));  // exact: |v| <= 127 integer
 }
@@ -294,6 +333,199 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_gram_emu(const Inst* insts, 
   }
 }
 
+// Asynchronous global -> shared copy of one double (zero-filled when !valid; the
+// source pointer is then only a placeholder and is not read).
+__device__ __forceinline__ void cp_async8(void* dst, const double* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared-memory bytes of the pipelined Gram kernel for MB output rows per pass
+// and kpe second-operand columns: two slice buffers and two raw tiles.
+__host__ __device__ inline size_t gram_emu_pipe_smem(int MB, int kpe, int k0p) {
+  return (size_t)2 * kEmuSlices * (MB + kpe) * kEmuLd * 2 + (size_t)2 * (MB + kpe) * kEmuKT * 8 +
+         sizeof(int) * (k0p + 16 + kpe + 16);
+}
+
+// The Gram sums of k_gram_emu, software-pipelined: the raw values of tile t+2
+// are copied asynchronously (cp.async) while tile t is multiplied, and tile
+// t+1 is split from its raw copy into the second slice buffer a quarter at a
+// time between the K steps of tile t, so that the integer splitting of some
+// warps overlaps the tensor-core work of others.  One barrier per tile.
+// Shared: Sl [2][8][MB + kpe][kEmuLd] bf16 | Raw [2][MB + kpe][kEmuKT] f64 | eV | eA.
+template <class S>
+__global__ void __launch_bounds__(kEmuThreads, 1) k_gram_emu_pipe(const Inst* insts, const Io* iot, Io io0,
+                                                                  const WorkItem* items, void* ws, int which) {
+  constexpr bool C = Tr<S>::C;
+  constexpr int RPE = C ? 2 : 1;
+  constexpr int TR = kEmuKT / RPE;
+  constexpr int NW = kEmuThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const Io io = get_io(iot, io0, it.inst);
+  const int k0 = (int)I.k0, k = (int)I.k;
+  const int kpe = (k + 7) / 8 * 8;
+  const int NT = (C ? 2 * kpe : kpe) / 8;
+  const int k0t = (k0 + 15) / 16;
+  const int MT = max(1, min(k0t, min(4, NW / NT)));
+  const int MB = MT * 16, RW = MB + kpe;
+  const int slsz = kEmuSlices * RW * kEmuLd;
+  unsigned short* Sl = reinterpret_cast<unsigned short*>(smem_raw);
+  double* Raw = reinterpret_cast<double*>(Sl + 2 * slsz);
+  int* eV = reinterpret_cast<int*>(Raw + 2 * RW * kEmuKT);
+  int* eA = eV + I.k0p + 16;
+  const double* Vd = reinterpret_cast<const double*>(io.V);
+  const double* Ad = reinterpret_cast<const double*>(which ? io.Q : io.A);
+  const int64_t ldv = io.ldv * RPE, lda = (which ? io.ldq : io.lda) * RPE;
+  const int64_t r_begin = I.k0 + (int64_t)it.idx * I.rows1;
+  const int64_t r_end = min64(I.n, r_begin + I.rows1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+
+  // Column scales, as in k_gram_emu (V's are kept for the later sweeps).
+  int* eVg = reinterpret_cast<int*>(wsp<S>(ws, I.oEv)) + (int64_t)it.idx * I.k0p;
+  for (int col = warp + (which ? k0 : 0); col < k0 + k; col += NW) {
+    const double* src = col < k0 ? Vd + (int64_t)col * ldv : Ad + (int64_t)(col - k0) * lda;
+    int m = 0;
+    for (int64_t q = r_begin * RPE + lane; q < r_end * RPE; q += 32) m = max(m, dexp(src[q]));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) {
+      if (col < k0) {
+        eV[col] = m;
+        eVg[col] = m;
+      } else {
+        eA[col - k0] = m;
+      }
+    }
+  }
+  if (which)
+    for (int col = threadIdx.x; col < k0; col += kEmuThreads) eV[col] = eVg[col];
+
+  S* out = wsp<S>(ws, which ? I.oG3 : I.oG1) + (int64_t)it.idx * k0 * k;
+  const bool mine = warp < MT * NT;
+  const int mt = mine ? warp / NT : 0, nt = mine ? warp % NT : 0;
+  const bool imag = C && nt * 8 >= kpe;
+  const int jb0 = imag ? nt * 8 - kpe : nt * 8;
+  const int ntile = (int)((r_end - r_begin + TR - 1) / TR);
+  const int ntot = RW * kEmuKT;
+  const int npair = ntot / 2;
+  const int nvt = (npair + kEmuThreads - 1) / kEmuThreads;  // value pairs per thread per tile
+  int m0 = 0;
+  // Raw values of tile t (rows [r0, r0 + TR)) into raw buffer `rb`: row < MB is
+  // column m0 + row of V, row >= MB column row - MB of A; zeros outside.
+  auto issue = [&](int t, double* rb) {
+    const int64_t r0 = r_begin + (int64_t)t * TR;
+    const int nq = t < ntile ? (int)min64(TR, r_end - r0) * RPE : 0;
+    for (int e = threadIdx.x; e < ntot; e += kEmuThreads) {
+      const int q = e % kEmuKT, row = e / kEmuKT;
+      const double* src = Vd;
+      bool valid = false;
+      if (q < nq) {
+        if (row < MB) {
+          const int col = m0 + row;
+          valid = col < k0;
+          if (valid) src = Vd + (int64_t)col * ldv + r0 * RPE + q;
+        } else {
+          const int j = row - MB;
+          valid = j < k;
+          if (valid) src = Ad + (int64_t)j * lda + r0 * RPE + q;
+        }
+      }
+      cp_async8(rb + e, src, valid);
+    }
+    cp_async_commit();
+  };
+  // Split value pairs u in [u0, u1) of this thread: pair e2 is steps q, q + 1
+  // (q = 2 (e2 % 32)) of raw row e2 / 32, which share the row's scale.
+  auto split_part = [&](const double* rb, unsigned short* sb, int u0, int u1) {
+    for (int u = u0; u < u1; ++u) {
+      const int e2 = threadIdx.x + u * kEmuThreads;
+      if (e2 >= npair) continue;
+      const int q = 2 * (e2 % (kEmuKT / 2)), row = e2 / (kEmuKT / 2);
+      int emax;
+      if (row < MB) emax = m0 + row < k0 ? eV[m0 + row] : 0;
+      else emax = row - MB < k ? eA[row - MB] : 0;
+      const double2 x = *reinterpret_cast<const double2*>(rb + row * kEmuKT + q);
+      unsigned w[kEmuSlices];
+      emu_split2(x.x, x.y, emax, emax, w);
+#pragma unroll
+      for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(sb + (p * RW + row) * kEmuLd + q) = w[p];
+    }
+  };
+  for (m0 = 0; m0 < k0t * 16; m0 += MB) {
+    float acc[kEmuLevels][4];
+    long long hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      hi[e] = lo[e] = 0;
+#pragma unroll
+      for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+    }
+    __syncthreads();  // exponents written; the previous pass is done with every buffer
+    issue(0, Raw);
+    issue(1, Raw + ntot);
+    cp_async_wait_all();
+    __syncthreads();
+    split_part(Raw, Sl, 0, nvt);
+    __syncthreads();
+    for (int t = 0; t < ntile; ++t) {
+      const unsigned short* cur = Sl + (t & 1) * slsz;
+      unsigned short* nxt = Sl + ((t + 1) & 1) * slsz;
+      const double* rawn = Raw + ((t + 1) & 1) * ntot;
+      if (t + 2 < ntile) issue(t + 2, Raw + (t & 1) * ntot);  // tile t's raw copy is spent
+#pragma unroll
+      for (int ks = 0; ks < kEmuKT; ks += 16) {
+        if (mine) {
+          unsigned bf[kEmuSlices][2];
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; qq += 2)
+            ld_bfrag2(cur + (qq * RW + MB) * kEmuLd, cur + ((qq + 1) * RW + MB) * kEmuLd, jb0, ks, bf[qq],
+                      bf[qq + 1]);
+          if (imag) {
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              bf[qq][0] = im_pair(bf[qq][0]);
+              bf[qq][1] = im_pair(bf[qq][1]);
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) {
+            unsigned a[4];
+            ld_afrag(cur + (p * RW) * kEmuLd, mt * 16, ks, a);
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              if (p + qq > kEmuLevels - 1) continue;
+              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+            }
+          }
+        }
+        if (t + 1 < ntile) split_part(rawn, nxt, (ks / 16) * nvt / 4, (ks / 16 + 1) * nvt / 4);
+      }
+      // Level sums stay exact for 128 steps: fold every second tile.
+      if (mine && (t & 1) == 1) emu_fold(acc, hi, lo);
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    if (mine) {
+      emu_fold(acc, hi, lo);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = m0 + mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = jb0 + 2 * t4 + (e & 1);
+        if (i >= k0 || j >= k) continue;
+        const int sc = eV[i] + eA[j] - 2044;
+        const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo[e], sc - 63);
+        double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
+        if constexpr (C) o[imag ? 1 : 0] = v;
+        else o[0] = v;
+      }
+    }
+  }
+}
+
 // Real-embedded second operand of the rank-k0 update out = base + V_2 Z:
 //   real:    B(q, j) = Z(q, j)
 //   complex: B(2l, j) = Re Z(l, j), B(2l + 1, j) = -Im Z(l, j)   (Re outputs);
@@ -326,7 +558,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
   constexpr int NW = kEmuThreads / 32;
-  constexpr int NV = 16 * MTM * kEmuKT / kEmuThreads;  // V values per thread per block
+  constexpr int NV = 16 * MTM * kEmuKT / kEmuThreads;  // V values per thread per block (NV / 2 pairs)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -390,31 +622,40 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
 
   const int ntile = (int)((r_end - r_begin + TM - 1) / TM);
   const int nblocks = ntile * nkb;
+  constexpr int NP = NV / 2;
   double val[NV];
-  auto load_block = [&](int b) {  // raw V values of block b into registers
+  // Raw V values of block b into registers, as pairs of consecutive real
+  // contraction steps (q, q + 1), q = kb + 2 (e2 % 32), row e2 / 32.
+  auto load_block = [&](int b) {
     const int64_t r0 = r_begin + (int64_t)(b / nkb) * TM;
     const int kb = (b % nkb) * kEmuKT;
     const int nr = (int)min64(TM, r_end - r0);
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int e = threadIdx.x + u * kEmuThreads;  // e = q_local + 64 r
-      const int ql = e % kEmuKT, r = e / kEmuKT, q = kb + ql;
-      double x = 0.0;
-      if (b < nblocks && r < nr && q < kz) x = Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)];
-      val[u] = x;
+    for (int u = 0; u < NP; ++u) {
+      const int e2 = threadIdx.x + u * kEmuThreads;
+      const int ql = 2 * (e2 % (kEmuKT / 2)), r = e2 / (kEmuKT / 2), q = kb + ql;
+      double x0 = 0.0, x1 = 0.0;
+      if (b < nblocks && r < nr) {
+        if (q < kz) x0 = Vd[(int64_t)(q / RPE) * ldv + (r0 + r) * RPE + (q % RPE)];
+        if (q + 1 < kz) x1 = Vd[(int64_t)((q + 1) / RPE) * ldv + (r0 + r) * RPE + ((q + 1) % RPE)];
+      }
+      val[2 * u] = x0;
+      val[2 * u + 1] = x1;
     }
   };
-  auto split_block = [&](int b, unsigned short* buf) {
+  // Split the prefetched pairs u in [u0, u1) of block b into buf.
+  auto split_block = [&](int b, unsigned short* buf, int u0, int u1) {
     const int kb = (b % nkb) * kEmuKT;
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int e = threadIdx.x + u * kEmuThreads;
-      const int ql = e % kEmuKT, r = e / kEmuKT, q = kb + ql;
+    for (int u = 0; u < NP; ++u) {
+      if (u < u0 || u >= u1) continue;
+      const int e2 = threadIdx.x + u * kEmuThreads;
+      const int ql = 2 * (e2 % (kEmuKT / 2)), r = e2 / (kEmuKT / 2), q = kb + ql;
       if (r >= TM) continue;
-      float sl[kEmuSlices];
-      emu_split(val[u], q < kz ? eV[q / RPE] : 0, sl);
+      unsigned w[kEmuSlices];
+      emu_split2(val[2 * u], val[2 * u + 1], q < kz ? eV[q / RPE] : 0, q + 1 < kz ? eV[(q + 1) / RPE] : 0, w);
 #pragma unroll
-      for (int p = 0; p < kEmuSlices; ++p) buf[(p * TM + r) * kEmuLd + ql] = bf16_bits(sl[p]);
+      for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(buf + (p * TM + r) * kEmuLd + ql) = w[p];
     }
   };
 
@@ -427,14 +668,16 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
     for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
   }
   load_block(0);
-  split_block(0, Vs);
+  split_block(0, Vs, 0, NP);
   __syncthreads();
   for (int b = 0; b < nblocks; ++b) {
     const int kbi = b % nkb, kb = kbi * kEmuKT;
     const unsigned short* cur = Vs + (b & 1) * vbuf;
-    load_block(b + 1);  // in flight during the MMAs
-    if (mine) {
-      for (int ks = 0; ks < kEmuKT; ks += 16) {
+    unsigned short* nxt = Vs + ((b + 1) & 1) * vbuf;
+    load_block(b + 1);  // in flight during the first MMAs
+#pragma unroll
+    for (int ks = 0; ks < kEmuKT; ks += 16) {
+      if (mine) {
         unsigned bf[kEmuSlices][2];
 #pragma unroll
         for (int qq = 0; qq < kEmuSlices; qq += 2) {
@@ -461,6 +704,11 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
           }
         }
       }
+      // A quarter of the next block's values split between K steps, so that
+      // the integer splitting overlaps the tensor-core work of other warps.
+      if (b + 1 < nblocks) split_block(b + 1, nxt, (ks / 16) * NP / 4, (ks / 16 + 1) * NP / 4);
+    }
+    if (mine) {
       if ((kbi & 1) == 1 || kbi == nkb - 1) emu_fold(acc, hi, lo);
       if (kbi == nkb - 1) {  // last K block of the row tile: write out = base + product
         const int64_t r0 = r_begin + (int64_t)(b / nkb) * TM;
@@ -480,7 +728,6 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
         }
       }
     }
-    if (b + 1 < nblocks) split_block(b + 1, Vs + ((b + 1) & 1) * vbuf);
     __syncthreads();
   }
 }
@@ -572,14 +819,18 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
     }
     for (int r0 = 0; r0 < rb; r0 += TM) {
       __syncthreads();  // Zs complete; the previous row tile's MMAs are done with Vs
-      for (int e = threadIdx.x; e < TM * kzp; e += kEmuThreads) {
-        const int q = e % kzp, r = e / kzp;
-        double x = 0.0;
-        if (q < kz && r0 + r < rb) x = reinterpret_cast<const double*>(Qr + (r0 + r) * ldr + q / RPE)[q % RPE];
-        float sl[kEmuSlices];
-        emu_split(x, q < kz ? eV[q / RPE] : 0, sl);
+      for (int e2 = threadIdx.x; e2 < TM * kzp / 2; e2 += kEmuThreads) {
+        const int q = 2 * (e2 % (kzp / 2)), r = e2 / (kzp / 2);
+        double x0 = 0.0, x1 = 0.0;
+        if (r0 + r < rb) {
+          const double* row = reinterpret_cast<const double*>(Qr + (r0 + r) * ldr);
+          if (q < kz) x0 = row[q];
+          if (q + 1 < kz) x1 = row[q + 1];
+        }
+        unsigned w[kEmuSlices];
+        emu_split2(x0, x1, q < kz ? eV[q / RPE] : 0, q + 1 < kz ? eV[(q + 1) / RPE] : 0, w);
 #pragma unroll
-        for (int p = 0; p < kEmuSlices; ++p) Vs[(p * TM + r) * kEmuLd + q] = bf16_bits(sl[p]);
+        for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * TM + r) * kEmuLd + q) = w[p];
       }
       __syncthreads();
       if (!mine) continue;

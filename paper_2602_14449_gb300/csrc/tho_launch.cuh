@@ -22,6 +22,15 @@ void launch_update_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, co
 }
 
 template <class S>
+void launch_gram_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
+                     void* ws, int which, cudaStream_t st) {
+  if (pc.gram_pipe)
+    k_gram_emu_pipe<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_pipe, st>>>(insts, d_io, io0, items, ws, which);
+  else
+    k_gram_emu<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_emu, st>>>(insts, d_io, io0, items, ws, which);
+}
+
+template <class S>
 void launch_apply_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
                       void* ws, cudaStream_t st) {
   if (pc.upd_mt == 1)
@@ -53,6 +62,14 @@ cudaError_t configure_impl(PlanCore& pc) {
       pc.smem_upd_emu = std::max(pc.smem_upd_emu, need);
     }
     (void)kzp;
+    // Pipelined Gram: MB = 16 MT output rows per pass, MT = max(1, min(k0t, min(4, 16 / NT))).
+    pc.smem_gram_pipe = 0;
+    for (const Inst& I : pc.h_insts) {
+      const int kpi = (int)(I.k + 7) / 8 * 8;
+      const int NT = ((pc.dtype == 1) ? 2 * kpi : kpi) / 8;
+      const int MT = std::max(1, std::min((int)(I.k0 + 15) / 16, std::min(4, (kEmuThreads / 32) / NT)));
+      pc.smem_gram_pipe = std::max(pc.smem_gram_pipe, gram_emu_pipe_smem(16 * MT, kpi, I.k0p));
+    }
     // Emulated apply: staged leaf Q (P x (k+1)), F_b, slices of F' and of one row tile.
     const int kpm = (pc.kmax + 7) / 8 * 8;
     pc.smem_apply_emu = (((size_t)pc.P * (pc.kmax + 1) + 1) / 2 * 2 + ((size_t)pc.kmax * pc.kmax + 1) / 2 * 2) * sizeof(S) +
@@ -84,6 +101,9 @@ cudaError_t configure_impl(PlanCore& pc) {
   };
   if ((e = raise((const void*)k_gram<S, B>, pc.smem_gram)) != cudaSuccess) return e;
   if (EMU && (e = raise((const void*)k_gram_emu<S>, pc.smem_gram_emu)) != cudaSuccess) return e;
+  // The pipelined Gram runs where its two slice buffers and raw tiles fit.
+  pc.gram_pipe = EMU && pc.smem_gram_pipe <= (size_t)optin &&
+                 raise((const void*)k_gram_emu_pipe<S>, pc.smem_gram_pipe) == cudaSuccess;
   if (EMU) {
     const void* f = pc.upd_mt == 1 ? (const void*)k_update_emu<S, 1>
                     : pc.upd_mt == 2 ? (const void*)k_update_emu<S, 2> : (const void*)k_update_emu<S, 4>;
@@ -121,7 +141,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     if (pc.tab.gram_n > 0) {
       hk(kPhGram, 0, st);
       if (EMU)
-        k_gram_emu<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 0);
+        launch_gram_emu<S>(pc, insts, d_io, io0, items + pc.tab.gram_off, ws, 0, st);
       else
         k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
       hk(kPhGram, 1, st);
@@ -158,7 +178,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   else
     k_apply_gram<S, B><<<pc.tab.apply_n, blk, pc.smem_apply, st>>>(insts, d_io, io0, items + pc.tab.apply_off, ws, 1);
   if (EMU && pc.any_k0 && pc.tab.gram_n > 0)  // V_2^* Qbar on tensor cores, into the G3 partials
-    k_gram_emu<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_emu, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws, 1);
+    launch_gram_emu<S>(pc, insts, d_io, io0, items + pc.tab.gram_off, ws, 1, st);
   hk(kPhApply, 1, st);
   if (pc.any_k0) {
     hk(kPhSolveZ2, 0, st);

@@ -56,7 +56,8 @@ typedef enum {
   THO_ERR_ALIGN = 3,       /* matrix pointer not aligned to its element size      */
   THO_ERR_NOMEM = 4,       /* device or pinned-host allocation failed              */
   THO_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed                 */
-  THO_ERR_TIMEOUT = 6,     /* reserved: no entry point waits on the device         */
+  THO_ERR_TIMEOUT = 6,     /* a bounded device-side wait of a tcgen05 kernel ran   *
+                            * out (results invalid); latched like NONFINITE        */
   THO_ERR_NONFINITE = 7,   /* device check found NaN/Inf (THO_FLAG_CHECK_FINITE)   */
   THO_ERR_UNSUPPORTED = 8  /* shape or mode beyond what this build implements      */
 } tho_status_t;

@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "tho_emu.cuh"
+#include "tho_umma.cuh"
 #include "tho_kernels.cuh"
 #include "tho_launch.h"
 #include "tho_tree.cuh"
@@ -24,7 +25,10 @@ void launch_update_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, co
 template <class S>
 void launch_gram_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
                      void* ws, int which, cudaStream_t st) {
-  if (pc.gram_pipe)
+  if (pc.gram_umma)
+    k_gram_umma<S><<<pc.tab.gram_n, kUmmaThreads, pc.smem_gram_umma, st>>>(insts, d_io, io0, items, ws, which,
+                                                                          pc.d_status);
+  else if (pc.gram_pipe)
     k_gram_emu_pipe<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_pipe, st>>>(insts, d_io, io0, items, ws, which);
   else
     k_gram_emu<S><<<pc.tab.gram_n, kEmuThreads, pc.smem_gram_emu, st>>>(insts, d_io, io0, items, ws, which);
@@ -70,6 +74,12 @@ cudaError_t configure_impl(PlanCore& pc) {
       const int MT = std::max(1, std::min((int)(I.k0 + 15) / 16, std::min(4, (kEmuThreads / 32) / NT)));
       pc.smem_gram_pipe = std::max(pc.smem_gram_pipe, gram_emu_pipe_smem(16 * MT, kpi, I.k0p));
     }
+    // Gram on tcgen05: two stages of 8 A (128 x 32) and 8 B (N x 32) slices.
+    pc.smem_gram_umma = 0;
+    for (const Inst& I : pc.h_insts) {
+      const int kpi = (int)(I.k + 7) / 8 * 8;
+      pc.smem_gram_umma = std::max(pc.smem_gram_umma, gram_umma_smem(gram_umma_n(pc.dtype == 1, (int)I.k), I.k0p, kpi));
+    }
     // Emulated apply: staged leaf Q (P x (k+1)), F_b, slices of F' and of one row tile.
     const int kpm = (pc.kmax + 7) / 8 * 8;
     pc.smem_apply_emu = (((size_t)pc.P * (pc.kmax + 1) + 1) / 2 * 2 + ((size_t)pc.kmax * pc.kmax + 1) / 2 * 2) * sizeof(S) +
@@ -101,7 +111,10 @@ cudaError_t configure_impl(PlanCore& pc) {
   };
   if ((e = raise((const void*)k_gram<S, B>, pc.smem_gram)) != cudaSuccess) return e;
   if (EMU && (e = raise((const void*)k_gram_emu<S>, pc.smem_gram_emu)) != cudaSuccess) return e;
-  // The pipelined Gram runs where its two slice buffers and raw tiles fit.
+  // The Gram runs on tcgen05 where its stages fit, else the pipelined
+  // mma.sync kernel where its buffers fit, else the plain one.
+  pc.gram_umma = EMU && pc.smem_gram_umma <= (size_t)optin &&
+                 raise((const void*)k_gram_umma<S>, pc.smem_gram_umma) == cudaSuccess;
   pc.gram_pipe = EMU && pc.smem_gram_pipe <= (size_t)optin &&
                  raise((const void*)k_gram_emu_pipe<S>, pc.smem_gram_pipe) == cudaSuccess;
   if (EMU) {

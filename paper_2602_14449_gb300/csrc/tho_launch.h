@@ -44,7 +44,8 @@ struct PlanCore {
   size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
   int upd_mt = 4;  // emulated update / apply: 16-row tiles per warp column (max over problems)
   size_t smem_apply_emu = 0;
-  size_t smem_gram_pipe = 0;
+  size_t smem_gram_pipe = 0, smem_gram_umma = 0;
+  bool gram_umma = false;  // emulated Gram on tcgen05 (when its stages fit)
   bool gram_pipe = false;  // emulated Gram: pipelined variant (when its buffers fit)
   size_t smem_gram_emu = 0;  // emulated split-n Gram (THO_PREC_FP64_EMU)
   size_t smem_upd_emu = 0;   // emulated rank-k0 update

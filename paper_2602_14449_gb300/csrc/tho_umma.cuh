@@ -1,0 +1,357 @@
+// FP64-accurate Gram sums on the 5th-generation tensor cores (tcgen05.mma).
+//
+// The integer-slice method of tho_emu.cuh, with the slice products issued as
+// tcgen05.mma (kind::f16: bf16 operands from shared memory, FP32 accumulators
+// in tensor memory) by one thread, while the other warps split the next row
+// tile.  The eight level sums live in TMEM (8 x N columns, one lane per output
+// row); every 128 contraction steps all warps fold them into int64 registers.
+// FP32 accumulation of integer slice products stays exact below 2^24 (the
+// probe's tcgen05 self-check confirms 0 mismatches at 16 516 096).
+//
+// Operand layout in shared memory: K-major, no swizzle, in 8-row x 16-byte core
+// matrices; element (r, k) of an R x 32 tile at byte
+//   ((r / 8) * 4 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// so the stride between core matrices is 128 bytes along K and 512 bytes along R.
+#pragma once
+
+#include <cstdint>
+
+#include "tho_emu.cuh"
+
+namespace tho {
+
+constexpr int kUmmaKT = 32;        // real contraction steps per pipeline stage
+constexpr int kUmmaThreads = 512;  // warp 0 issues the MMAs; warps 1..15 split; all fold
+constexpr int kUmmaStages = 2;
+constexpr int kUmmaM = 128;        // MMA rows: the (padded) columns of V
+constexpr int kUmmaGroup = 4;      // stages per fold (4 x 32 = 128 steps)
+constexpr int kUmmaSpins = 1 << 25;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of a K-major operand without swizzle.
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05
+  return d;              // base offset 0, no swizzle
+}
+
+// Instruction descriptor (kind::f16): FP32 accumulator, bf16 A and B, both
+// K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+// Arrive once on the mbarrier when every tcgen05 operation issued so far by this thread completes.
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+// Wait for the phase with the given parity to complete; false after the spin
+// bound (the caller then abandons its loop and the kernel latches an error).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < kUmmaSpins; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Generic-proxy shared-memory writes made visible to the tensor core (async proxy).
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Four consecutive 32-bit TMEM columns of this warp's lane quadrant.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Output columns N of the Gram MMA: complex 2 kpe (Re then Im), real k rounded up to 16.
+__host__ __device__ inline int gram_umma_n(bool cplx, int k) {
+  const int kpe = (k + 7) / 8 * 8;
+  return cplx ? 2 * kpe : (k + 15) / 16 * 16;
+}
+__host__ __device__ inline int gram_umma_cols(int N) {  // TMEM columns allocated (power of two >= 32)
+  int c = 32;
+  while (c < 8 * N) c *= 2;
+  return c;
+}
+__host__ __device__ inline size_t gram_umma_smem(int N, int k0p, int kpe) {
+  return (size_t)kUmmaStages * kEmuSlices * (kUmmaM + N) * kUmmaKT * 2 + 8 * 8 + 16 +
+         sizeof(int) * (k0p + 16 + kpe + 16);
+}
+
+// a3 (sweep 1) / the V_2^* Qbar sums of a8 on tcgen05: the partial sums of
+// k_gram_emu (same scales, slices, levels and output), one CTA per row chunk.
+// Shared: stages [2][8 A slices (128 x 32) | 8 B slices (N x 32)] bf16 | mbarriers
+// full[2], empty[2], fold, free, done | TMEM slot, abort flag | eV | eA.
+template <class S>
+__global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts, const Io* iot, Io io0,
+                                                               const WorkItem* items, void* ws, int which,
+                                                               int* status) {
+  constexpr bool C = Tr<S>::C;
+  constexpr int RPE = C ? 2 : 1;
+  constexpr int TR = kUmmaKT / RPE;  // rows per stage
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const Io io = get_io(iot, io0, it.inst);
+  const int k0 = (int)I.k0, k = (int)I.k;
+  const int kpe = (k + 7) / 8 * 8;
+  const int N = gram_umma_n(C, k);
+  const int abytes = kUmmaM * kUmmaKT * 2, bbytes = N * kUmmaKT * 2;
+  const int stage_bytes = kEmuSlices * (abytes + bbytes);
+  unsigned char* stages = smem_raw;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + kUmmaStages * stage_bytes);
+  const uint32_t b_full = smem_u32(bars), b_empty = b_full + 16, b_fold = b_full + 32, b_free = b_full + 40,
+                 b_done = b_full + 48;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  int* eV = reinterpret_cast<int*>(tslot + 4);
+  int* eA = eV + I.k0p + 16;
+  const double* Vd = reinterpret_cast<const double*>(io.V);
+  const double* Ad = reinterpret_cast<const double*>(which ? io.Q : io.A);
+  const int64_t ldv = io.ldv * RPE, lda = (which ? io.ldq : io.lda) * RPE;
+  const int64_t r_begin = I.k0 + (int64_t)it.idx * I.rows1;
+  const int64_t r_end = min64(I.n, r_begin + I.rows1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // Column scales (maximal biased exponents over the chunk), as k_gram_emu.
+  int* eVg = reinterpret_cast<int*>(wsp<S>(ws, I.oEv)) + (int64_t)it.idx * I.k0p;
+  for (int col = warp + (which ? k0 : 0); col < k0 + k; col += kUmmaThreads / 32) {
+    const double* src = col < k0 ? Vd + (int64_t)col * ldv : Ad + (int64_t)(col - k0) * lda;
+    int m = 0;
+    for (int64_t q = r_begin * RPE + lane; q < r_end * RPE; q += 32) m = max(m, dexp(src[q]));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) {
+      if (col < k0) {
+        eV[col] = m;
+        eVg[col] = m;
+      } else {
+        eA[col - k0] = m;
+      }
+    }
+  }
+  if (which)
+    for (int col = threadIdx.x; col < k0; col += kUmmaThreads) eV[col] = eVg[col];
+  if (threadIdx.x == 0) {
+    mbar_init(b_full, kUmmaThreads / 32 - 1);
+    mbar_init(b_full + 8, kUmmaThreads / 32 - 1);
+    mbar_init(b_empty, 1);
+    mbar_init(b_empty + 8, 1);
+    mbar_init(b_fold, 1);
+    mbar_init(b_free, kUmmaThreads / 32);
+    mbar_init(b_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const int ncols = gram_umma_cols(N);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int ntile = (int)((r_end - r_begin + TR - 1) / TR);
+  auto group_end = [&](int t) { return (t % kUmmaGroup) == kUmmaGroup - 1 || t == ntile - 1; };
+
+  // Fold accumulators: warp w reads lane quadrant w % 4 (output row i) and
+  // the w / 4-th quarter of the N columns.  Per output the running sum is
+  // hi 2^28 + lo with 0 <= lo < 2^28 (carries moved into hi at every fold).
+  const int qd = warp & 3, cpw = N / 4, c0 = (warp >> 2) * cpw;
+  long long hi[16];
+  unsigned lo[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    hi[c] = 0;
+    lo[c] = 0;
+  }
+  auto fold = [&](int g) {
+    if (!mbar_wait(b_fold, g & 1)) {
+      *abort_flag = 1;
+      return;
+    }
+    tc_fence_after();
+    const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + c0;
+#pragma unroll
+    for (int c = 0; c < 16; c += 4) {
+      if (c >= cpw) continue;
+      long long h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int L = 0; L < kEmuLevels; ++L) {
+        uint32_t r[4];
+        tmem_ld4(tb + L * N + c, r);
+        tmem_ld_wait();
+        const int sh = 21 - 7 * (L & 3);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const long long v = (long long)__float2int_rz(__uint_as_float(r[e])) << sh;
+          if (L < 4) h[e] += v;
+          else l[e] += v;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const long long t = (long long)lo[c + e] + l[e];  // |t| < 2^47
+        hi[c + e] += h[e] + (t >> 28);                     // arithmetic shift: floor
+        lo[c + e] = (unsigned)(t & 0xfffffff);
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b_free);
+  };
+
+  if (warp == 0) {
+    // MMA issue (lane 0); the warp folds after each group's last stage.
+    for (int t = 0; t < ntile && !*abort_flag; ++t) {
+      const int s = t & 1;
+      bool ok = true;
+      if (lane == 0) {
+        ok = mbar_wait(b_full + 8 * s, (t >> 1) & 1);
+        if (ok && (t % kUmmaGroup) == 0 && t > 0) ok = mbar_wait(b_free, ((t / kUmmaGroup) - 1) & 1);
+        if (ok) {
+          tc_fence_after();
+          const uint32_t id = umma_idesc_bf16(kUmmaM, N);
+          const uint32_t sb = smem_u32(stages + s * stage_bytes);
+          const bool first = (t % kUmmaGroup) == 0;
+          // Descriptors advance by (byte offset >> 4) in their address field.
+          const uint64_t d0 = umma_sdesc(sb, 128, (kUmmaKT / 8) * 128);
+#pragma unroll 1
+          for (int kk = 0; kk < kUmmaKT; kk += 16) {
+#pragma unroll 1
+            for (int p = 0; p < kEmuSlices; ++p) {
+              const uint64_t ad = d0 + (uint64_t)((p * abytes + (kk / 8) * 128) >> 4);
+              const uint64_t bd0 = d0 + (uint64_t)((kEmuSlices * abytes + (kk / 8) * 128) >> 4);
+              const uint32_t acc = (first && kk == 0 && p == 0) ? 0u : 1u;
+#pragma unroll
+              for (int q = 0; q < kEmuSlices; ++q) {
+                if (p + q > kEmuLevels - 1) continue;
+                umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd0 + (uint64_t)((q * bbytes) >> 4), id, acc);
+              }
+            }
+          }
+          umma_commit(b_empty + 8 * s);
+          if (group_end(t)) umma_commit(b_fold);
+        } else {
+          *abort_flag = 1;
+        }
+      }
+      __syncwarp();
+      if (group_end(t) && !*abort_flag) fold(t / kUmmaGroup);
+    }
+    if (lane == 0) {
+      umma_commit(b_done);
+      if (!mbar_wait(b_done, 0)) *abort_flag = 1;
+    }
+    __syncwarp();
+  } else {
+    // Producers: split stage t of V (A operand rows = columns of V) and of
+    // X = A or Qbar (B operand rows; complex: the swapped copy for Im G too).
+    const int npA = kUmmaM * (kUmmaKT / 2), npB = (C ? kpe : N) * (kUmmaKT / 2);
+    for (int t = 0; t < ntile && !*abort_flag; ++t) {
+      const int s = t & 1;
+      if (t >= 2 && !mbar_wait(b_empty + 8 * s, ((t >> 1) - 1) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      unsigned char* sb = stages + s * stage_bytes;
+      const int64_t r0 = r_begin + (int64_t)t * TR;
+      const int nq = (int)min64(TR, r_end - r0) * RPE;
+      for (int e2 = threadIdx.x - 32; e2 < npA + npB; e2 += kUmmaThreads - 32) {
+        const bool isA = e2 < npA;
+        const int f = isA ? e2 : e2 - npA;
+        const int g32 = f >> 5, l = f & 31;
+        const int kp = (g32 & 3) * 4 + (l >> 3), row = (g32 >> 2) * 8 + (l & 7), q = 2 * kp;
+        const int off = ((row >> 3) * 4 + (kp >> 2)) * 128 + (row & 7) * 16 + (kp & 3) * 4;
+        double x0 = 0.0, x1 = 0.0;
+        int emax = 0;
+        if (isA) {
+          if (row < k0) {
+            const double* src = Vd + (int64_t)row * ldv + r0 * RPE;
+            if (q < nq) x0 = src[q];
+            if (q + 1 < nq) x1 = src[q + 1];
+            emax = eV[row];
+          }
+        } else if (row < k) {
+          const double* src = Ad + (int64_t)row * lda + r0 * RPE;
+          if (q < nq) x0 = src[q];
+          if (q + 1 < nq) x1 = src[q + 1];
+          emax = eA[row];
+        }
+        unsigned w[kEmuSlices];
+        emu_split2(x0, x1, emax, emax, w);
+        if (isA) {
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(sb + p * abytes + off) = w[p];
+        } else {
+          unsigned char* bb = sb + kEmuSlices * abytes;
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(bb + p * bbytes + off) = w[p];
+          if (C) {  // row kpe + row: (Im, -Re) pairs for the imaginary outputs
+            const int offs = (((kpe + row) >> 3) * 4 + (kp >> 2)) * 128 + (row & 7) * 16 + (kp & 3) * 4;
+#pragma unroll
+            for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(bb + p * bbytes + offs) = im_pair(w[p]);
+          }
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_full + 8 * s);
+      if (t >= 1 && group_end(t - 1)) fold((t - 1) / kUmmaGroup);
+    }
+    if (ntile > 0 && !*abort_flag) fold((ntile - 1) / kUmmaGroup);
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicExch(status, 6);  // THO_ERR_TIMEOUT
+  if (!*abort_flag) {
+    S* out = wsp<S>(ws, which ? I.oG3 : I.oG1) + (int64_t)it.idx * k0 * k;
+    const int i = qd * 32 + lane;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c >= cpw || i >= k0) continue;
+      const int cg = c0 + c;
+      const bool imag = C && cg >= kpe;
+      const int j = imag ? cg - kpe : cg;
+      if (j >= k) continue;
+      // value = (hi 2^28 + lo) 2^(sc - 63), as hi 2^(sc - 35) + lo 2^(sc - 63)
+      const int sc = eV[i] + eA[j] - 2044;
+      const double v = scale2((double)hi[c], sc - 35) + scale2((double)lo[c], sc - 63);
+      double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
+      if constexpr (C) o[imag ? 1 : 0] = v;
+      else o[0] = v;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+}  // namespace tho

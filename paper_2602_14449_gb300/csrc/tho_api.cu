@@ -262,6 +262,11 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
       // Emulated products: column exponents of V per chunk (ints -> elements).
       const int64_t esz = (int64_t)p->L->elem;
       I.oEv = take(pc.prec == THO_PREC_FP64_EMU ? ((int64_t)I.g1 * I.k0p * 4 + esz - 1) / esz : 1);
+      // bf16 slices of V, written by the first Gram sweep and read by the
+      // later sweeps: one kVsTileBytes block per row tile of kUmmaKT real steps.
+      const int64_t tr = tho::kUmmaKT / (cplx ? 2 : 1);
+      I.vs_tiles = pc.prec == THO_PREC_FP64_EMU && I.k0 > 0 ? ceil_div(I.rows1, tr) : 0;
+      I.oVs = take(((int64_t)I.g1 * I.vs_tiles * tho::kVsTileBytes + esz - 1) / esz);
     }
     I.oRn = take(nodes * kk);
     I.oRef = take((nodes - I.nb) * (kk + 2 * k));

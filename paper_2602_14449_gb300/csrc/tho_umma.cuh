@@ -8,6 +8,10 @@
 // FP32 accumulation of integer slice products stays exact below 2^24 (the
 // probe's tcgen05 self-check confirms 0 mismatches at 16 516 096).
 //
+// The first sweep (which = 0) also stores every stage's V slices to HBM (one
+// bulk copy per stage); the second sweep (which = 1) loads them back with bulk
+// copies instead of splitting V again, and its producers split only Qbar.
+//
 // Operand layout in shared memory: K-major, no swizzle, in 8-row x 16-byte core
 // matrices; element (r, k) of an R x 32 tile at byte
 //   ((r / 8) * 4 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
@@ -20,12 +24,13 @@
 
 namespace tho {
 
-constexpr int kUmmaKT = 32;        // real contraction steps per pipeline stage
 constexpr int kUmmaThreads = 512;  // warp 0 issues the MMAs; warps 1..15 split; all fold
 constexpr int kUmmaStages = 2;
 constexpr int kUmmaM = 128;        // MMA rows: the (padded) columns of V
 constexpr int kUmmaGroup = 4;      // stages per fold (4 x 32 = 128 steps)
 constexpr int kUmmaSpins = 1 << 25;
+// Value pairs per producer thread per stage: (128 + 32) rows x 16 pairs over 480 threads.
+constexpr int kUmmaPairs = ((kUmmaM + 32) * (kUmmaKT / 2) + kUmmaThreads - 33) / (kUmmaThreads - 32);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -74,6 +79,28 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   }
   return false;
 }
+// Bulk (TMA engine) copies between shared and global memory, 16-byte aligned.
+__device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until at most n of this thread's bulk stores still read shared memory.
+template <int n>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(n) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_load(uint32_t sdst, const void* gsrc, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sdst),
+               "l"(gsrc), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // Generic-proxy shared-memory writes made visible to the tensor core (async proxy).
@@ -158,8 +185,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
   if (threadIdx.x == 0) {
     mbar_init(b_full, kUmmaThreads / 32 - 1);
     mbar_init(b_full + 8, kUmmaThreads / 32 - 1);
-    mbar_init(b_empty, 1);
-    mbar_init(b_empty + 8, 1);
+    // Stage reuse waits for the MMAs and, in the first sweep, for the bulk
+    // store of the V slices to have read the stage.
+    mbar_init(b_empty, which ? 1 : 2);
+    mbar_init(b_empty + 8, which ? 1 : 2);
     mbar_init(b_fold, 1);
     mbar_init(b_free, kUmmaThreads / 32);
     mbar_init(b_done, 1);
@@ -177,6 +206,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const int ntile = (int)((r_end - r_begin + TR - 1) / TR);
+  unsigned char* gvs = reinterpret_cast<unsigned char*>(wsp<S>(ws, I.oVs)) + (int64_t)it.idx * I.vs_tiles * kVsTileBytes;
   auto group_end = [&](int t) { return (t % kUmmaGroup) == kUmmaGroup - 1 || t == ntile - 1; };
 
   // Fold accumulators: warp w reads lane quadrant w % 4 (output row i) and
@@ -239,19 +269,28 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
           const uint32_t id = umma_idesc_bf16(kUmmaM, N);
           const uint32_t sb = smem_u32(stages + s * stage_bytes);
           const bool first = (t % kUmmaGroup) == 0;
-          // Descriptors advance by (byte offset >> 4) in their address field.
+          if (!which) {
+            if (t > 0) {  // the previous stage's slices have been read out: release it
+              bulk_wait_read<0>();
+              mbar_arrive(b_empty + 8 * ((t - 1) & 1));
+            }
+            bulk_store(gvs + (int64_t)t * kVsTileBytes, sb, (uint32_t)kVsTileBytes);
+          }
+          // Level by level, so that consecutive MMAs accumulate into the
+          // same TMEM columns.  Descriptors advance by (byte offset >> 4) in
+          // their address field.
           const uint64_t d0 = umma_sdesc(sb, 128, (kUmmaKT / 8) * 128);
+          const uint64_t db = d0 + (uint64_t)((kEmuSlices * abytes) >> 4);
 #pragma unroll 1
-          for (int kk = 0; kk < kUmmaKT; kk += 16) {
-#pragma unroll 1
-            for (int p = 0; p < kEmuSlices; ++p) {
-              const uint64_t ad = d0 + (uint64_t)((p * abytes + (kk / 8) * 128) >> 4);
-              const uint64_t bd0 = d0 + (uint64_t)((kEmuSlices * abytes + (kk / 8) * 128) >> 4);
-              const uint32_t acc = (first && kk == 0 && p == 0) ? 0u : 1u;
+          for (int L = 0; L < kEmuLevels; ++L) {
+            const uint32_t dt = tmem + (uint32_t)(L * N);
 #pragma unroll
-              for (int q = 0; q < kEmuSlices; ++q) {
-                if (p + q > kEmuLevels - 1) continue;
-                umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd0 + (uint64_t)((q * bbytes) >> 4), id, acc);
+            for (int kk = 0; kk < kUmmaKT; kk += 16) {
+#pragma unroll 1
+              for (int p = 0; p <= L; ++p) {
+                const uint64_t ad = d0 + (uint64_t)((p * abytes + (kk / 8) * 128) >> 4);
+                const uint64_t bd = db + (uint64_t)(((L - p) * bbytes + (kk / 8) * 128) >> 4);
+                umma_bf16(dt, ad, bd, id, (first && kk == 0 && p == 0) ? 0u : 1u);
               }
             }
           }
@@ -267,12 +306,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
     if (lane == 0) {
       umma_commit(b_done);
       if (!mbar_wait(b_done, 0)) *abort_flag = 1;
+      if (!which) bulk_wait_all();  // the V slices are in HBM before the kernel ends
     }
     __syncwarp();
   } else {
-    // Producers: split stage t of V (A operand rows = columns of V) and of
-    // X = A or Qbar (B operand rows; complex: the swapped copy for Im G too).
-    const int npA = kUmmaM * (kUmmaKT / 2), npB = (C ? kpe : N) * (kUmmaKT / 2);
+    // Producers: split stage t of V (A operand rows = columns of V; in the
+    // second sweep warp 1 bulk-loads them instead) and of X = A or Qbar (B
+    // operand rows; complex: the swapped copy for Im G too).
+    const bool loader = which && warp == 1;
+    const int pbase = which ? 64 : 32, nprod = kUmmaThreads - pbase;
+    const int npA = which ? 0 : kUmmaM * (kUmmaKT / 2), npB = (C ? kpe : N) * (kUmmaKT / 2);
     for (int t = 0; t < ntile && !*abort_flag; ++t) {
       const int s = t & 1;
       if (t >= 2 && !mbar_wait(b_empty + 8 * s, ((t >> 1) - 1) & 1)) {
@@ -280,31 +323,48 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
         break;
       }
       unsigned char* sb = stages + s * stage_bytes;
+      if (loader) {
+        if (lane == 0) {
+          mbar_arrive_tx(b_full + 8 * s, (uint32_t)kVsTileBytes);
+          bulk_load(smem_u32(sb), gvs + (int64_t)t * kVsTileBytes, (uint32_t)kVsTileBytes, b_full + 8 * s);
+        }
+        __syncwarp();
+        if (t >= 1 && group_end(t - 1)) fold((t - 1) / kUmmaGroup);
+        continue;
+      }
       const int64_t r0 = r_begin + (int64_t)t * TR;
       const int nq = (int)min64(TR, r_end - r0) * RPE;
-      for (int e2 = threadIdx.x - 32; e2 < npA + npB; e2 += kUmmaThreads - 32) {
+      // All of this thread's loads first (one memory round trip per stage),
+      // then the splitting.
+      double xv[2 * kUmmaPairs];
+#pragma unroll
+      for (int u = 0; u < kUmmaPairs; ++u) {
+        const int e2 = threadIdx.x - pbase + u * nprod;
         const bool isA = e2 < npA;
         const int f = isA ? e2 : e2 - npA;
         const int g32 = f >> 5, l = f & 31;
         const int kp = (g32 & 3) * 4 + (l >> 3), row = (g32 >> 2) * 8 + (l & 7), q = 2 * kp;
-        const int off = ((row >> 3) * 4 + (kp >> 2)) * 128 + (row & 7) * 16 + (kp & 3) * 4;
         double x0 = 0.0, x1 = 0.0;
-        int emax = 0;
-        if (isA) {
-          if (row < k0) {
-            const double* src = Vd + (int64_t)row * ldv + r0 * RPE;
-            if (q < nq) x0 = src[q];
-            if (q + 1 < nq) x1 = src[q + 1];
-            emax = eV[row];
-          }
-        } else if (row < k) {
-          const double* src = Ad + (int64_t)row * lda + r0 * RPE;
+        if (e2 < npA + npB && row < (isA ? k0 : k)) {
+          const double* src = isA ? Vd + (int64_t)row * ldv + r0 * RPE : Ad + (int64_t)row * lda + r0 * RPE;
           if (q < nq) x0 = src[q];
           if (q + 1 < nq) x1 = src[q + 1];
-          emax = eA[row];
         }
+        xv[2 * u] = x0;
+        xv[2 * u + 1] = x1;
+      }
+#pragma unroll
+      for (int u = 0; u < kUmmaPairs; ++u) {
+        const int e2 = threadIdx.x - pbase + u * nprod;
+        if (e2 >= npA + npB) continue;
+        const bool isA = e2 < npA;
+        const int f = isA ? e2 : e2 - npA;
+        const int g32 = f >> 5, l = f & 31;
+        const int kp = (g32 & 3) * 4 + (l >> 3), row = (g32 >> 2) * 8 + (l & 7);
+        const int off = ((row >> 3) * 4 + (kp >> 2)) * 128 + (row & 7) * 16 + (kp & 3) * 4;
+        const int emax = isA ? (row < k0 ? eV[row] : 0) : (row < k ? eA[row] : 0);
         unsigned w[kEmuSlices];
-        emu_split2(x0, x1, emax, emax, w);
+        emu_split2(xv[2 * u], xv[2 * u + 1], emax, emax, w);
         if (isA) {
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(sb + p * abytes + off) = w[p];

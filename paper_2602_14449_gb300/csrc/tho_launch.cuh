@@ -14,7 +14,10 @@ namespace tho {
 template <class S>
 void launch_update_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
                        void* ws, int which, cudaStream_t st) {
-  if (pc.upd_mt == 1)
+  if (pc.upd_umma)
+    k_update_umma<S><<<pc.tab.upd_n, kUpdThreads, pc.smem_upd_umma, st>>>(insts, d_io, io0, items, ws, which,
+                                                                         pc.d_status);
+  else if (pc.upd_mt == 1)
     k_update_emu<S, 1><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items, ws, which);
   else if (pc.upd_mt == 2)
     k_update_emu<S, 2><<<pc.tab.upd_n, kEmuThreads, pc.smem_upd_emu, st>>>(insts, d_io, io0, items, ws, which);
@@ -80,6 +83,9 @@ cudaError_t configure_impl(PlanCore& pc) {
       const int kpi = (int)(I.k + 7) / 8 * 8;
       pc.smem_gram_umma = std::max(pc.smem_gram_umma, gram_umma_smem(gram_umma_n(pc.dtype == 1, (int)I.k), I.k0p, kpi));
     }
+    pc.smem_upd_umma = 0;
+    for (const Inst& I : pc.h_insts)
+      pc.smem_upd_umma = std::max(pc.smem_upd_umma, upd_umma_smem(upd_umma_n(pc.dtype == 1, (int)I.k)));
     // Emulated apply: staged leaf Q (P x (k+1)), F_b, slices of F' and of one row tile.
     const int kpm = (pc.kmax + 7) / 8 * 8;
     pc.smem_apply_emu = (((size_t)pc.P * (pc.kmax + 1) + 1) / 2 * 2 + ((size_t)pc.kmax * pc.kmax + 1) / 2 * 2) * sizeof(S) +
@@ -115,6 +121,8 @@ cudaError_t configure_impl(PlanCore& pc) {
   // mma.sync kernel where its buffers fit, else the plain one.
   pc.gram_umma = EMU && pc.smem_gram_umma <= (size_t)optin &&
                  raise((const void*)k_gram_umma<S>, pc.smem_gram_umma) == cudaSuccess;
+  pc.upd_umma = pc.gram_umma && pc.smem_upd_umma <= (size_t)optin &&
+                raise((const void*)k_update_umma<S>, pc.smem_upd_umma) == cudaSuccess;
   pc.gram_pipe = EMU && pc.smem_gram_pipe <= (size_t)optin &&
                  raise((const void*)k_gram_emu_pipe<S>, pc.smem_gram_pipe) == cudaSuccess;
   if (EMU) {

@@ -414,4 +414,268 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
   }
 }
 
+// ------------------------------------------------------------------------------
+// a5 / a9 (rank-k0 update) on tcgen05:
+//   which = 0:  Q_2 <- A_2 + V_2 Z    (A' of the trailing block, parked in Q)
+//   which = 1:  Q_2 <- Q_2 + V_2 Z2   (Q = Qbar - W Z2 with W_2 = -V_2)
+// No splitting of V: the MMA's A operand is the V slices the first Gram sweep
+// kept in HBM, read MN-major (a stored core matrix, 8 columns i x 8 real steps,
+// is also an MN-major core matrix of the transposed use) and brought in by
+// bulk copies.  Complex rows are embedded along M: row r gives MMA rows 2r
+// (Re V) and 2r + 1 (Im V), so that the contraction runs over the k0 complex
+// columns i and the second operand is B = [Re Z' | Im Z'] (N = 2 kpe), with
+// Z'(i, j) = 2^(e_i - 1078) Z(i, j) (the chunk's V column scales moved into Z)
+// sliced per column j with one scale for both parts.  Then, exactly in int64,
+//   Re out(r, j) = D(2r, j) - D(2r + 1, kpe + j),  Im out(r, j) = D(2r, kpe + j) + D(2r + 1, j),
+// one lane shuffle apart.  The contraction (k0 <= 128) fits one fold.
+// Warps 0..15 build B, then fold and write each 128-row tile; warp 16 issues
+// the MMAs (and owns TMEM); warp 17 issues the bulk copies.
+// Shared: Bz [8][N x 128] bf16 | stages [2][8][2 i-groups][4 tiles][4 step groups][128 B] |
+// mbarriers full[2], empty[2], done, free, fin | TMEM slot, abort | eV | eZ.
+constexpr int kUpdWarps = 18;
+constexpr int kUpdThreads = 32 * kUpdWarps;
+constexpr int kUpdStageBytes = kEmuSlices * 2 * 4 * 512;
+
+__host__ __device__ inline int upd_umma_n(bool cplx, int k) {
+  const int kpe = (k + 7) / 8 * 8;
+  return cplx ? 2 * kpe : (k + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t upd_umma_smem(int N) {
+  return (size_t)kEmuSlices * N * 128 * 2 + (size_t)2 * kUpdStageBytes + 8 * 8 + 16 + sizeof(int) * (128 + 64);
+}
+
+template <class S>
+__global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* insts, const Io* iot, Io io0,
+                                                                const WorkItem* items, void* ws, int which,
+                                                                int* status) {
+  constexpr bool C = Tr<S>::C;
+  constexpr int RPE = C ? 2 : 1;
+  constexpr int TRg = kUmmaKT / RPE;  // rows per stored V tile
+  constexpr int UR = 4 * TRg;         // rows per 128-row MMA tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const Io io = get_io(iot, io0, it.inst);
+  const int k0 = (int)I.k0, k = (int)I.k;
+  const int kpe = (k + 7) / 8 * 8;
+  const int N = upd_umma_n(C, k);
+  const int bz = N * 128 * 2;  // one slice of B
+  unsigned char* Bz = smem_raw;
+  unsigned char* stages = Bz + kEmuSlices * bz;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + 2 * kUpdStageBytes);
+  const uint32_t b_full = smem_u32(bars), b_empty = b_full + 16, b_done = b_full + 32, b_free = b_full + 40,
+                 b_fin = b_full + 48;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  int* eV = reinterpret_cast<int*>(tslot + 4);
+  int* eZ = eV + 128;
+  const S* Zg = wsp<S>(ws, which ? I.oZ2 : I.oZ);
+  const int* eVg = reinterpret_cast<const int*>(wsp<S>(ws, I.oEv)) + (int64_t)it.idx * I.k0p;
+  const unsigned char* gvs =
+      reinterpret_cast<const unsigned char*>(wsp<S>(ws, I.oVs)) + (int64_t)it.idx * I.vs_tiles * kVsTileBytes;
+  const double* Bd = reinterpret_cast<const double*>(which ? io.Q : io.A);
+  double* Qd = reinterpret_cast<double*>(io.Q);
+  const int64_t ldb = (which ? io.ldq : io.lda) * RPE, ldq = io.ldq * RPE;
+  const int64_t r_begin = I.k0 + (int64_t)it.idx * I.rows4;
+  const int64_t r_end = min64(I.n, r_begin + I.rows4);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ntg = (int)((r_end - r_begin + TRg - 1) / TRg);  // stored tiles of this chunk
+  const int nut = (ntg + 3) / 4;                             // 128-row MMA tiles
+  const int nks = (k0 + 15) / 16;                            // 16-column stages per tile
+
+  for (int i = threadIdx.x; i < 128; i += kUpdThreads) eV[i] = i < k0 ? eVg[i] : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(b_full, 1);
+    mbar_init(b_full + 8, 1);
+    mbar_init(b_empty, 1);
+    mbar_init(b_empty + 8, 1);
+    mbar_init(b_done, 1);
+    mbar_init(b_free, 16);
+    mbar_init(b_fin, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const int ncols = gram_umma_cols(N);
+  if (warp == 16) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  // B = [Re Z' | Im Z'] (complex) or Z' (real), n x i, sliced per output column j.
+  auto zp = [&](int n, int i) -> double {
+    const bool im = C && n >= kpe;
+    const int j = im ? n - kpe : n;
+    if (i >= k0 || j >= k) return 0.0;
+    double b;
+    if constexpr (C) {
+      const z64 z = Zg[i + (int64_t)j * k0];
+      b = im ? z.y : z.x;
+    } else {
+      b = reinterpret_cast<const double*>(Zg)[i + (int64_t)j * k0];
+    }
+    return scale2(b, eV[i] - 1078);
+  };
+  for (int j = warp; j < (C ? kpe : N); j += kUpdWarps) {
+    int m = 0;
+    for (int i = lane; i < k0; i += 32) {
+      m = max(m, dexp(zp(j, i)));
+      if (C) m = max(m, dexp(zp(kpe + j, i)));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) eZ[j] = m;
+  }
+  __syncthreads();
+  for (int e2 = threadIdx.x; e2 < N * 64; e2 += kUpdThreads) {
+    const int n = e2 >> 6, i = 2 * (e2 & 63);
+    const int ez = eZ[(C && n >= kpe) ? n - kpe : n];
+    unsigned w[kEmuSlices];
+    emu_split2(zp(n, i), zp(n, i + 1), ez, ez, w);
+    const int off = ((n >> 3) * 16 + (i >> 3)) * 128 + (n & 7) * 16 + (i & 7) * 2;
+#pragma unroll
+    for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Bz + p * bz + off) = w[p];
+  }
+  fence_proxy_async();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 16) {
+    if (lane == 0) {
+      // A MN-major: LBO = 2048 (i-groups, along K), SBO = 128 (step groups, along M).
+      const uint32_t id = umma_idesc_bf16(128, N) | (1u << 15);
+      const uint64_t da = umma_sdesc(smem_u32(stages), 2048, 128);
+      const uint64_t db = umma_sdesc(smem_u32(Bz), 128, 16 * 128);
+      int sidx = 0;
+      for (int u = 0; u < nut && !*abort_flag; ++u) {
+        for (int ks = 0; ks < nks; ++ks, ++sidx) {
+          const int s = sidx & 1;
+          bool ok = mbar_wait(b_full + 8 * s, (sidx >> 1) & 1);
+          if (ok && ks == 0 && u > 0) ok = mbar_wait(b_free, (u - 1) & 1);
+          if (!ok) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll 1
+          for (int L = 0; L < kEmuLevels; ++L) {
+            const uint32_t dt = tmem + (uint32_t)(L * N);
+#pragma unroll 1
+            for (int p = 0; p <= L; ++p) {
+              const uint64_t ad = da + (uint64_t)((s * kUpdStageBytes + p * (kUpdStageBytes / kEmuSlices)) >> 4);
+              const uint64_t bd = db + (uint64_t)(((L - p) * bz + 2 * ks * 128) >> 4);
+              umma_bf16(dt, ad, bd, id, (ks == 0 && p == 0) ? 0u : 1u);
+            }
+          }
+          umma_commit(b_empty + 8 * s);
+          if (ks == nks - 1) umma_commit(b_done);
+        }
+      }
+      umma_commit(b_fin);
+      if (!mbar_wait(b_fin, 0)) *abort_flag = 1;
+    }
+    __syncwarp();
+  } else if (warp == 17) {
+    int sidx = 0;
+    for (int u = 0; u < nut && !*abort_flag; ++u) {
+      const int ntl = min(4, ntg - 4 * u);
+      for (int ks = 0; ks < nks; ++ks, ++sidx) {
+        const int s = sidx & 1;
+        bool ok = true;
+        if (lane == 0 && sidx >= 2) ok = mbar_wait(b_empty + 8 * s, ((sidx >> 1) - 1) & 1);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        if (lane == 0) mbar_arrive_tx(b_full + 8 * s, (uint32_t)(ntl * kEmuSlices * 2 * 512));
+        __syncwarp();
+        unsigned char* st = stages + s * kUpdStageBytes;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = lane + 32 * h;  // piece: slice p, i-group g, stored tile j
+          const int p = c >> 3, g = (c >> 2) & 1, j = c & 3;
+          if (j < ntl)
+            bulk_load(smem_u32(st + p * (kUpdStageBytes / kEmuSlices) + g * 2048 + j * 512),
+                      gvs + (int64_t)(4 * u + j) * kVsTileBytes + p * (kVsTileBytes / kEmuSlices) + (2 * ks + g) * 512,
+                      512u, b_full + 8 * s);
+        }
+      }
+    }
+  } else {
+    // Epilogue: warp w reads TMEM lanes 32 (w % 4).. (MMA rows) and output
+    // columns 8 (w / 4).. (complex: of both the Re Z' and the Im Z' blocks).
+    const int qd = warp & 3, j0 = (warp >> 2) * 8;
+    const bool act = j0 < (C ? kpe : N);
+    for (int u = 0; u < nut && !*abort_flag; ++u) {
+      if (!mbar_wait(b_done, u & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      long long h[16], l[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) h[c] = l[c] = 0;
+      if (act) {
+        const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + j0;
+#pragma unroll
+        for (int L = 0; L < kEmuLevels; ++L) {
+          uint32_t r[16];
+          tmem_ld4(tb + L * N, *reinterpret_cast<uint32_t(*)[4]>(r));
+          tmem_ld4(tb + L * N + 4, *reinterpret_cast<uint32_t(*)[4]>(r + 4));
+          if (C) {
+            tmem_ld4(tb + L * N + kpe, *reinterpret_cast<uint32_t(*)[4]>(r + 8));
+            tmem_ld4(tb + L * N + kpe + 4, *reinterpret_cast<uint32_t(*)[4]>(r + 12));
+          }
+          tmem_ld_wait();
+          const int sh = 21 - 7 * (L & 3);
+#pragma unroll
+          for (int c = 0; c < (C ? 16 : 8); ++c) {
+            const long long v = (long long)__float2int_rz(__uint_as_float(r[c])) << sh;
+            if (L < 4) h[c] += v;
+            else l[c] += v;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_free);
+      if (!act) continue;
+      const int m = qd * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int j = j0 + c;
+        long long hh = h[c], ll = l[c];
+        int64_t row;
+        int part = 0;
+        if constexpr (C) {
+          // Neighbour lane's Im-block sums: subtracted on the Re lane, added on the Im lane.
+          const long long xh = __shfl_xor_sync(0xffffffffu, h[8 + c], 1);
+          const long long xl = __shfl_xor_sync(0xffffffffu, l[8 + c], 1);
+          part = m & 1;
+          hh = part ? hh + xh : hh - xh;
+          ll = part ? ll + xl : ll - xl;
+          row = r_begin + (int64_t)u * UR + (m >> 1);
+        } else {
+          row = r_begin + (int64_t)u * UR + m;
+        }
+        if (row < r_end && j < k) {
+          const int sc = eZ[j] - 966;
+          const double v = scale2((double)hh, sc - 35) + scale2((double)ll, sc - 63);
+          Qd[(int64_t)j * ldq + row * RPE + part] = Bd[(int64_t)j * ldb + row * RPE + part] + v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicExch(status, 6);  // THO_ERR_TIMEOUT
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 16) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
 }  // namespace tho

@@ -81,7 +81,7 @@ cudaError_t backward_run(const PlanCore& pc, const BwdState& st, const BwdIo& io
   const dim3 blk(kThreads);
   Io fio{io.V, io.A, nullptr, nullptr, nullptr, io.ldv, io.lda, 0};
   // (W, T) recomputed: QR of V_{1:k0,:}, T, Wtop.
-  k_v1qr<double><<<1, blk, 0, s>>>(pc.d_insts, nullptr, fio, pc.ws);
+  k_v1qr<double><<<1, kV1Threads, 0, s>>>(pc.d_insts, nullptr, fio, pc.ws);
   // Split-n Grams V_2^T A_2, V_2^T Q_2, V_2^T dQ_2.
   Io ga{io.V, io.A, nullptr, nullptr, nullptr, io.ldv, io.lda, 0};
   Io gq{io.V, io.Q, nullptr, nullptr, nullptr, io.ldv, io.ldq, 0};

@@ -66,27 +66,44 @@ __device__ __forceinline__ double scale2(double x, int e) {
   return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(x, e);
 }
 
-// The 56-bit fixed-point magnitude of x relative to emax, as its top and bottom
-// 28 bits, and the sign (the integer emu_split slices).
+// The 56-bit fixed-point magnitude X of x relative to emax (the integer
+// emu_split slices), as its top and bottom 28 bits, and the sign.  With M the
+// 53-bit mantissa and sh = e - emax + 3 <= 3: top = M >> (28 - sh); bottom =
+// (M << sh) mod 2^28 for sh >= 0, (M >> -sh) mod 2^28 otherwise; computed on
+// the two 32-bit words of M with funnel shifts.
 __device__ __forceinline__ void emu_fixed56(double x, int emax, unsigned& h, unsigned& l, bool& neg) {
-  const long long bits = __double_as_longlong(x);
-  const int e = (int)((bits >> 52) & 0x7ff);
-  unsigned long long X = 0;
-  if (e != 0) {
-    const unsigned long long M = (bits & 0xfffffffffffffULL) | 0x10000000000000ULL;
-    const int sh = e - emax + 3;  // <= 3
-    X = sh >= 0 ? (M << sh) : (-sh >= 64 ? 0ULL : (M >> -sh));
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(bits >> 32), lw = (unsigned)bits;
+  const int e = (int)((hw >> 20) & 0x7ff);
+  const unsigned mh = (hw & 0xfffffu) | 0x100000u;
+  const int sh = e - emax + 3;
+  const int t = 28 - sh;  // >= 25
+  unsigned hh = t < 32 ? __funnelshift_r(lw, mh, t) : (t < 64 ? mh >> (t - 32) : 0u);
+  unsigned ll;
+  if (sh >= 0) {
+    ll = (lw << sh) & 0xfffffffu;
+  } else {
+    const int r = -sh;
+    ll = (r < 32 ? __funnelshift_r(lw, mh, r) : (r < 64 ? mh >> (r - 32) : 0u)) & 0xfffffffu;
   }
-  h = (unsigned)(X >> 28);
-  l = (unsigned)(X & 0xfffffffu);
-  neg = bits < 0;
+  h = e != 0 ? hh : 0u;
+  l = e != 0 ? ll : 0u;
+  neg = (hw >> 31) != 0;
+}
+
+// Packed bf16 subtraction (exact here: the operands and results are small integers).
+__device__ __forceinline__ unsigned bf16x2_sub(unsigned a, unsigned b) {
+  unsigned d;
+  asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
 }
 
 // The eight slices of two values (x0 with scale emax0, x1 with emax1) as packed
 // bf16 pairs: w[p] holds slice p of x0 in its low half and of x1 in its high
-// half.  A slice magnitude a <= 127 becomes a float by the exact magic-number
-// subtraction (2^23 + a) - 2^23; its top 16 bits are its bf16 pattern (exact:
-// a has at most 7 significant bits); the signs are OR-ed in.
+// half.  With the 7-bit slice magnitudes a0, a1 placed under the bf16 pattern
+// of 128 (0x4300: exponent 2^7, the magnitude as the 7-bit mantissa), one
+// packed subtraction of (128, 128) gives (a0, a1) exactly; the signs are
+// XOR-ed in.
 __device__ __forceinline__ void emu_split2(double x0, double x1, int emax0, int emax1,
                                            unsigned (&w)[kEmuSlices]) {
   unsigned h0, l0, h1, l1;
@@ -97,11 +114,10 @@ __device__ __forceinline__ void emu_split2(double x0, double x1, int emax0, int 
 #pragma unroll
   for (int p = 0; p < kEmuSlices; ++p) {
     const int sh = 21 - 7 * (p & 3);
-    const unsigned a0 = ((p < 4 ? h0 : l0) >> sh) & 127u;
-    const unsigned a1 = ((p < 4 ? h1 : l1) >> sh) & 127u;
-    const float f0 = __uint_as_float(0x4B000000u | a0) - 8388608.0f;
-    const float f1 = __uint_as_float(0x4B000000u | a1) - 8388608.0f;
-    w[p] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | sg;
+    const unsigned a = p < 4 ? h0 : l0, b = p < 4 ? h1 : l1;
+    const unsigned lo = ((a >> sh) & 0x7fu) | 0x43004300u;
+    const unsigned hi = (sh <= 16 ? (b << (16 - sh)) : (b >> (sh - 16))) & 0x7f0000u;
+    w[p] = bf16x2_sub(lo | hi, 0x43004300u) ^ sg;
   }
 }
 

@@ -178,8 +178,11 @@ __device__ __forceinline__ void make_reflector(double nrm2, S xj, double& beta, 
 // ------------------------------------------------------------------------------
 // a1, a2: QR of V_{1:k0,:}, T = I + R1^*, Wtop = P - V_{1:k0,:} with P = -Q1.
 // One CTA per instance; the k0 x k0 working copy lives in the workspace (L2).
+// One CTA of kV1Threads threads per instance: the steps of this small QR are
+// latency-bound, so every warp takes a column of each trailing update.
+constexpr int kV1Threads = 1024;
 template <class S>
-__global__ void __launch_bounds__(kThreads) k_v1qr(const Inst* insts, const Io* iot, Io io0, void* ws) {
+__global__ void __launch_bounds__(kV1Threads) k_v1qr(const Inst* insts, const Io* iot, Io io0, void* ws) {
   const int inst = blockIdx.x;
   const Inst& I = insts[inst];
   const int k0 = (int)I.k0;
@@ -194,9 +197,9 @@ __global__ void __launch_bounds__(kThreads) k_v1qr(const Inst* insts, const Io* 
   __shared__ double beta_s[kMaxK0];
   __shared__ S vdiag[kMaxK0];
   __shared__ S rdiag[kMaxK0];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kV1Threads / 32;
 
-  for (int e = threadIdx.x; e < k0 * k0; e += kThreads) {
+  for (int e = threadIdx.x; e < k0 * k0; e += kV1Threads) {
     int i = e % k0, j = e / k0;
     X[e] = V[i + (int64_t)j * io.ldv];
   }
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_v1qr(const Inst* insts, const Io* 
     __syncthreads();
   }
   // Q = H_0 ... H_{k0-1} I, applied right to left into Q1.
-  for (int e = threadIdx.x; e < k0 * k0; e += kThreads) Q1[e] = from_real<S>((e % k0) == (e / k0) ? 1.0 : 0.0);
+  for (int e = threadIdx.x; e < k0 * k0; e += kV1Threads) Q1[e] = from_real<S>((e % k0) == (e / k0) ? 1.0 : 0.0);
   __syncthreads();
   for (int j = k0 - 1; j >= 0; --j) {
     const double b = beta_s[j];
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_v1qr(const Inst* insts, const Io* 
     __syncthreads();
   }
   // Phase normalization D = diag(phase(R_jj)): Q1 <- Q1 D, R1 <- D^* R1.
-  for (int e = threadIdx.x; e < k0 * k0; e += kThreads) {
+  for (int e = threadIdx.x; e < k0 * k0; e += kV1Threads) {
     int i = e % k0, j = e / k0;
     S dj = phase(rdiag[j]);
     Q1[e] = mul(Q1[e], dj);
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) k_v1qr(const Inst* insts, const Io* 
     R1[e] = r;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < k0 * k0; e += kThreads) {
+  for (int e = threadIdx.x; e < k0 * k0; e += kV1Threads) {
     int i = e % k0, j = e / k0;
     // T = I + R1^* (lower triangular); Wtop = -Q1 - V_{1:k0,:}.
     S t = zero<S>();

@@ -157,7 +157,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   const dim3 blk(kThreads);
   if (pc.any_k0) {
     hk(kPhQrV1, 0, st);
-    k_v1qr<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws);
+    k_v1qr<S><<<pc.count, kV1Threads, 0, st>>>(insts, d_io, io0, ws);
     hk(kPhQrV1, 1, st);
     if (pc.tab.gram_n > 0) {
       hk(kPhGram, 0, st);

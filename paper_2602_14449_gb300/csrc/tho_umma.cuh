@@ -276,21 +276,23 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
             }
             bulk_store(gvs + (int64_t)t * kVsTileBytes, sb, (uint32_t)kVsTileBytes);
           }
-          // Level by level, so that consecutive MMAs accumulate into the
-          // same TMEM columns.  Descriptors advance by (byte offset >> 4) in
-          // their address field.
+          // The B slices q and q + 1 are contiguous and so are the level
+          // accumulators p + q and p + q + 1: one N = 2N MMA covers both pairs
+          // (20 MMAs per K step instead of 36; p = 0 touches every level first).
+          // Descriptors advance by (byte offset >> 4) in their address field.
+          const uint32_t id2 = umma_idesc_bf16(kUmmaM, 2 * N);
           const uint64_t d0 = umma_sdesc(sb, 128, (kUmmaKT / 8) * 128);
           const uint64_t db = d0 + (uint64_t)((kEmuSlices * abytes) >> 4);
-#pragma unroll 1
-          for (int L = 0; L < kEmuLevels; ++L) {
-            const uint32_t dt = tmem + (uint32_t)(L * N);
 #pragma unroll
-            for (int kk = 0; kk < kUmmaKT; kk += 16) {
+          for (int kk = 0; kk < kUmmaKT; kk += 16) {
 #pragma unroll 1
-              for (int p = 0; p <= L; ++p) {
-                const uint64_t ad = d0 + (uint64_t)((p * abytes + (kk / 8) * 128) >> 4);
-                const uint64_t bd = db + (uint64_t)(((L - p) * bbytes + (kk / 8) * 128) >> 4);
-                umma_bf16(dt, ad, bd, id, (first && kk == 0 && p == 0) ? 0u : 1u);
+            for (int p = 0; p < kEmuSlices; ++p) {
+              const uint64_t ad = d0 + (uint64_t)((p * abytes + (kk / 8) * 128) >> 4);
+              const uint32_t acc = (first && kk == 0 && p == 0) ? 0u : 1u;
+#pragma unroll 1
+              for (int q = 0; p + q < kEmuLevels; q += 2) {
+                const uint64_t bd = db + (uint64_t)((q * bbytes + (kk / 8) * 128) >> 4);
+                umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd, p + q + 1 < kEmuLevels ? id2 : id, acc);
               }
             }
           }
@@ -545,6 +547,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
     if (lane == 0) {
       // A MN-major: LBO = 2048 (i-groups, along K), SBO = 128 (step groups, along M).
       const uint32_t id = umma_idesc_bf16(128, N) | (1u << 15);
+      const uint32_t id2 = umma_idesc_bf16(128, 2 * N) | (1u << 15);
       const uint64_t da = umma_sdesc(smem_u32(stages), 2048, 128);
       const uint64_t db = umma_sdesc(smem_u32(Bz), 128, 16 * 128);
       int sidx = 0;
@@ -558,14 +561,16 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
             break;
           }
           tc_fence_after();
+          // Pairs (p, q), (p, q + 1) as one N = 2N MMA (B slices and level
+          // accumulators are contiguous), as in the Gram.
 #pragma unroll 1
-          for (int L = 0; L < kEmuLevels; ++L) {
-            const uint32_t dt = tmem + (uint32_t)(L * N);
+          for (int p = 0; p < kEmuSlices; ++p) {
+            const uint64_t ad = da + (uint64_t)((s * kUpdStageBytes + p * (kUpdStageBytes / kEmuSlices)) >> 4);
+            const uint32_t acc = (ks == 0 && p == 0) ? 0u : 1u;
 #pragma unroll 1
-            for (int p = 0; p <= L; ++p) {
-              const uint64_t ad = da + (uint64_t)((s * kUpdStageBytes + p * (kUpdStageBytes / kEmuSlices)) >> 4);
-              const uint64_t bd = db + (uint64_t)(((L - p) * bz + 2 * ks * 128) >> 4);
-              umma_bf16(dt, ad, bd, id, (ks == 0 && p == 0) ? 0u : 1u);
+            for (int q = 0; p + q < kEmuLevels; q += 2) {
+              const uint64_t bd = db + (uint64_t)((q * bz + 2 * ks * 128) >> 4);
+              umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd, p + q + 1 < kEmuLevels ? id2 : id, acc);
             }
           }
           umma_commit(b_empty + 8 * s);

@@ -271,6 +271,7 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
     I.oRn = take(nodes * kk);
     I.oRef = take((nodes - I.nb) * (kk + 2 * k));
     I.oF = take(nodes * kk);
+    I.oBeta = take(pc.prec == THO_PREC_FP64_EMU ? (int64_t)I.nb * k : 1);
   }
   pc.ws_elems = (size_t)off;
 

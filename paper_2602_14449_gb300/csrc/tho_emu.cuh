@@ -91,6 +91,12 @@ __device__ __forceinline__ void emu_fixed56(double x, int emax, unsigned& h, uns
   neg = (hw >> 31) != 0;
 }
 
+// xor shuffle of a scalar (double or complex double) within the lanes of mask.
+__device__ __forceinline__ double shfl_xor_s(double v, int o, unsigned mask) { return __shfl_xor_sync(mask, v, o); }
+__device__ __forceinline__ z64 shfl_xor_s(z64 v, int o, unsigned mask) {
+  return z64{__shfl_xor_sync(mask, v.x, o), __shfl_xor_sync(mask, v.y, o)};
+}
+
 // Packed bf16 subtraction (exact here: the operands and results are small integers).
 __device__ __forceinline__ unsigned bf16x2_sub(unsigned a, unsigned b) {
   unsigned d;
@@ -756,9 +762,20 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
 // embedding of F_b used by the rank-k0 update, which is sliced per column j.
 // The contraction (k columns, real-embedded) is at most 64 steps: one fold.
 // Shared: Qr [P][k+1] S | Fr [k][k] S | Zs [8][kpe][kEmuLd] | Vs [8][TM][kEmuLd] bf16 | eV | eZ.
+//
+// wy != 0: Q's rows hold the leaf's Householder vectors Y (v_j on the diagonal,
+// zero above) and the workspace its betas, instead of the explicit leaf Q.
+// With T the upper triangular factor of H_0 ... H_{k-1} = I - Y T Y^*,
+//   Qbar_b = [F_b; 0] - Y (T (Y_1^* F_b)),   Y_1 = rows 0..k-1 of Y,
+// formed per leaf as: G = Y^* Y on tensor cores (scales of Y's columns);
+// B = Y_1^* F_b (FP64); M = T B by back substitution with T^-1 = diag(1/beta)
+// + (strictly upper part of G), which holds for the forward product of the
+// reflectors (Puglisi); then the product above with F_b replaced by -M and
+// [F_b; 0] added in the epilogue.
+// Extra shared memory with wy: Gs (G), Ts (unused), Ms [k][k+1] S after Fr.
 template <class S, int MTM>
 __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
-                                                              const WorkItem* items, void* ws, int P) {
+                                                              const WorkItem* items, void* ws, int P, int wy) {
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
   constexpr int NW = kEmuThreads / 32;
@@ -772,9 +789,14 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
   const int MTt = max(1, min(MTM, NW / NT));
   const int TM = 16 * MTt;
   const int kz = RPE * k, kzp = (kz + 15) / 16 * 16;
+  const int ldf = k + 1;  // F_b, M: column-major, padded (conflict-free lane-parallel rows)
+  const int kk2 = (k * ldf + 1) / 2 * 2;
   S* Qr = reinterpret_cast<S*>(smem_raw);
   S* Fr = Qr + ((size_t)P * ldr + 1) / 2 * 2;
-  unsigned short* Zs = reinterpret_cast<unsigned short*>(Fr + (kk + 1) / 2 * 2);
+  S* Gs = Fr + kk2;
+  S* Ts = Gs + kk2;
+  S* Ms = Ts + kk2;
+  unsigned short* Zs = reinterpret_cast<unsigned short*>(Fr + (wy ? 4 : 1) * kk2);
   unsigned short* Vs = Zs + kEmuSlices * kpe * kEmuLd;
   int* eV = reinterpret_cast<int*>(Vs + kEmuSlices * TM * kEmuLd);
   int* eZ = eV + kMaxKP;
@@ -797,7 +819,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       const int r = e % rb, i = e / rb;
       Qr[r * ldr + i] = Qg[(lo + r) + (int64_t)i * ldq];
     }
-    for (int e = threadIdx.x; e < kk; e += kEmuThreads) Fr[e] = Fb[e];
+    for (int e = threadIdx.x; e < kk; e += kEmuThreads) Fr[(e % k) + (e / k) * ldf] = Fb[e];
     __syncthreads();
     for (int i = warp; i < k; i += NW) {
       int m = 0;
@@ -807,17 +829,117 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       if (lane == 0) eV[i] = m;
     }
     __syncthreads();
+    if (wy) {
+      // (1) G = Y^* Y over the leaf's rows, 64 real steps per chunk; Vs holds
+      // the slices of Y^T (rows = columns of Y), serving as both operands.
+      const int kr = (k + 15) / 16 * 16;
+      const bool gmine = warp < (kr / 16) * NT;
+      const int gmt = gmine ? warp / NT : 0, gnt = gmine ? warp % NT : 0;
+      const bool gimag = C && gnt * 8 >= kpe;
+      const int gjb0 = gimag ? gnt * 8 - kpe : gnt * 8;
+      float acc[kEmuLevels][4];
+      long long ghi[4] = {0, 0, 0, 0}, glo[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+      const int nq = rb * RPE;
+      int chunk = 0;
+      for (int q0 = 0; q0 < nq; q0 += kEmuKT, ++chunk) {
+        __syncthreads();  // the previous chunk's MMAs are done with Vs
+        for (int e2 = threadIdx.x; e2 < kr * (kEmuKT / 2); e2 += kEmuThreads) {
+          const int l = e2 / (kEmuKT / 2), q = 2 * (e2 % (kEmuKT / 2)), qa = q0 + q;
+          double x0 = 0.0, x1 = 0.0;
+          if (l < k) {
+            if (qa < nq) x0 = reinterpret_cast<const double*>(Qr + (qa / RPE) * ldr + l)[qa % RPE];
+            if (qa + 1 < nq) x1 = reinterpret_cast<const double*>(Qr + ((qa + 1) / RPE) * ldr + l)[(qa + 1) % RPE];
+          }
+          const int em = l < k ? eV[l] : 0;
+          unsigned w[kEmuSlices];
+          emu_split2(x0, x1, em, em, w);
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * kr + l) * kEmuLd + q) = w[p];
+        }
+        __syncthreads();
+        if (gmine) {
+          for (int ks = 0; ks < kEmuKT; ks += 16) {
+            unsigned bf[kEmuSlices][2];
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; qq += 2)
+              ld_bfrag2(Vs + (qq * kr) * kEmuLd, Vs + ((qq + 1) * kr) * kEmuLd, gjb0, ks, bf[qq], bf[qq + 1]);
+            if (gimag) {
+#pragma unroll
+              for (int qq = 0; qq < kEmuSlices; ++qq) {
+                bf[qq][0] = im_pair(bf[qq][0]);
+                bf[qq][1] = im_pair(bf[qq][1]);
+              }
+            }
+#pragma unroll
+            for (int p = 0; p < kEmuSlices; ++p) {
+              unsigned a[4];
+              ld_afrag(Vs + (p * kr) * kEmuLd, gmt * 16, ks, a);
+#pragma unroll
+              for (int qq = 0; qq < kEmuSlices; ++qq) {
+                if (p + qq > kEmuLevels - 1) continue;
+                mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+              }
+            }
+          }
+          if (chunk & 1) emu_fold(acc, ghi, glo);  // exact for 128 steps
+        }
+      }
+      if (gmine) {
+        emu_fold(acc, ghi, glo);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = gmt * 16 + g + (e >= 2 ? 8 : 0);
+          const int j = gjb0 + 2 * t4 + (e & 1);
+          if (i >= k || j >= k) continue;
+          const int sc = eV[i] + eV[j] - 2044;
+          const double v = scale2((double)ghi[e], sc - 35) + scale2((double)glo[e], sc - 63);
+          reinterpret_cast<double*>(Gs + i + j * k)[gimag ? 1 : 0] = v;
+        }
+      }
+      __syncthreads();
+      // (2) B = Y_1^* F_b into Ms (Y_1 lower triangular: Y(c, l) = 0 for c < l);
+      // a warp takes one row l (uniform loop length), lanes the columns j.
+      for (int e = threadIdx.x; e < kk; e += kEmuThreads) {
+        const int l = e / k, j = e % k;
+        S b = zero<S>();
+        for (int c = l; c < k; ++c) b = cmadd(b, Qr[c * ldr + l], Fr[c + j * ldf]);
+        Ms[l + j * ldf] = b;
+      }
+      __syncthreads();
+      // (3) M = T B without forming T: T^-1 = diag(1/beta) + (strictly upper part
+      // of G), so M solves that upper triangular system; right-looking back
+      // substitution: row i is final once scaled by beta_i, then it is removed
+      // from the rows above (one rank-1 update per step).
+      const S* btg = wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
+      for (int i = k - 1; i >= 0; --i) {
+        const double bi = real_(btg[i]);
+        if (threadIdx.x < k) Ms[i + threadIdx.x * ldf] = scale(Ms[i + threadIdx.x * ldf], bi);
+        __syncthreads();
+        for (int e = threadIdx.x; e < i * k; e += kEmuThreads) {
+          const int l = e / k, j = e % k;
+          Ms[l + j * ldf] = msub(Ms[l + j * ldf], Gs[l + i * k], Ms[i + j * ldf]);
+        }
+        __syncthreads();
+      }
+    }
+    // Second operand: F_b, or -M with the compact WY form.
+    const S* Zsrc = wy ? Ms : Fr;
+    const double zsg = wy ? -1.0 : 1.0;
     auto fp = [&](int q, int j) -> double {
       if (q >= kz || j >= k) return 0.0;
       const int i = q / RPE;
       double b;
       if constexpr (C) {
-        const z64 z = Fr[i + j * k];
+        const z64 z = Zsrc[i + j * ldf];
         b = (q & 1) ? -z.y : z.x;
       } else {
-        b = reinterpret_cast<const double*>(Fr)[i + j * k];
+        b = reinterpret_cast<const double*>(Zsrc)[i + j * ldf];
       }
-      return scale2(b, eV[i] - 1078);
+      return scale2(zsg * b, eV[i] - 1078);
     };
     for (int j = warp; j < kpe; j += NW) {
       int m = 0;
@@ -886,7 +1008,8 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
         const int j = jb0 + 2 * t4 + (e & 1);
         if (r < rb && j < k) {
           const int sc = eZ[j] - 966;
-          const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+          double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+          if (wy && r < k) v += reinterpret_cast<const double*>(Fr + r + j * ldf)[imag ? 1 : 0];  // [F_b; 0]
           reinterpret_cast<double*>(Qg + (lo + r) + (int64_t)j * ldq)[imag ? 1 : 0] = v;
         }
       }

@@ -368,7 +368,12 @@ __global__ void __launch_bounds__(kThreads) k_solve_z(const Inst* insts, const I
 // Shared memory: Lb (P x kp, ld P) | Zs (k0p x kp, ld k0p) | Vs (tile) | small.
 template <class S, class B>
 __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* iot, Io io0,
-                                                   const WorkItem* items, void* ws, int P, int from_q) {
+                                                   const WorkItem* items, void* ws, int P, int mode) {
+  // mode bit 0 (from_q): A'_b was formed by the emulated update and parked in
+  // Q's rows.  Bit 1 (wy): write the reflectors Y (Householder vectors, v_j on
+  // the diagonal, zero above) into Q's rows and the betas into the workspace
+  // instead of the explicit leaf Q (the emulated apply forms Qbar_b from them).
+  const int from_q = mode & 1, wy = mode & 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -519,6 +524,16 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
     }
   }
   __syncthreads();
+  if (wy) {
+    S* Q = reinterpret_cast<S*>(io.Q);
+    for (int e = threadIdx.x; e < rb * k; e += kThreads) {
+      const int r = e % rb, c = e / rb;
+      Q[(lo + r) + (int64_t)c * io.ldq] = cvt<S, B>(Yv(r, c));
+    }
+    S* bt = wsp<S>(ws, I.oBeta) + (int64_t)it.idx * k;
+    for (int c = threadIdx.x; c < k; c += kThreads) bt[c] = from_real<S>(beta_s[c]);
+    return;
+  }
   // Explicit Q_leaf = H_0 ... H_{k-1} [I; 0], in place, blocks from the last:
   // the block reflector on the formed columns, then the panel column by column.
   for (int J = ((k - 1) / kNB) * kNB; J >= 0; J -= kNB) {

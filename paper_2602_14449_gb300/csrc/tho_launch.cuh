@@ -41,11 +41,11 @@ template <class S>
 void launch_apply_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
                       void* ws, cudaStream_t st) {
   if (pc.upd_mt == 1)
-    k_apply_emu<S, 1><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P);
+    k_apply_emu<S, 1><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, 1);
   else if (pc.upd_mt == 2)
-    k_apply_emu<S, 2><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P);
+    k_apply_emu<S, 2><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, 1);
   else
-    k_apply_emu<S, 4><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P);
+    k_apply_emu<S, 4><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, 1);
 }
 
 template <class S, class B, bool EMU>
@@ -88,7 +88,8 @@ cudaError_t configure_impl(PlanCore& pc) {
       pc.smem_upd_umma = std::max(pc.smem_upd_umma, upd_umma_smem(upd_umma_n(pc.dtype == 1, (int)I.k)));
     // Emulated apply: staged leaf Q (P x (k+1)), F_b, slices of F' and of one row tile.
     const int kpm = (pc.kmax + 7) / 8 * 8;
-    pc.smem_apply_emu = (((size_t)pc.P * (pc.kmax + 1) + 1) / 2 * 2 + ((size_t)pc.kmax * pc.kmax + 1) / 2 * 2) * sizeof(S) +
+    // With the compact WY form (emulated mode): G / N, T and M after F_b.
+    pc.smem_apply_emu = (((size_t)pc.P * (pc.kmax + 1) + 1) / 2 * 2 + 4 * (((size_t)pc.kmax * (pc.kmax + 1) + 1) / 2 * 2)) * sizeof(S) +
                         (size_t)kEmuSlices * 2 * kEmuLd * (kpm + 16 * pc.upd_mt) + sizeof(int) * 2 * kMaxKP;
   }
   pc.smem_gram = std::max<size_t>((size_t)kTileRows * (pc.k0pmax + pc.kpmax), kRedElems) * b;
@@ -178,7 +179,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   }
   hk(kPhLeaf, 0, st);
   k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
-                                                         (EMU && pc.any_k0) ? 1 : 0);
+                                                         ((EMU && pc.any_k0) ? 1 : 0) | (EMU ? 2 : 0));
   hk(kPhLeaf, 1, st);
   hk(kPhTreeUp, 0, st);
   for (int l = 1; l <= pc.Lmax; ++l)

@@ -173,18 +173,20 @@ __device__ __forceinline__ void ldsm_x4(const unsigned short* p, unsigned& r0, u
                : "r"(a));
 }
 
-// A fragment (16 x 16 of a [row][k] tile, ld kEmuLd) at rows m0.., steps ks..
+// A fragment (16 x 16 of a [row][k] tile with row stride LD) at rows m0.., steps ks..
+template <int LD = kEmuLd>
 __device__ __forceinline__ void ld_afrag(const unsigned short* tile, int m0, int ks, unsigned (&a)[4]) {
   const int lane = threadIdx.x & 31, i = lane >> 3, r = lane & 7;
-  ldsm_x4(tile + (m0 + ((i & 1) ? 8 : 0) + r) * kEmuLd + ks + ((i & 2) ? 8 : 0), a[0], a[1], a[2], a[3]);
+  ldsm_x4(tile + (m0 + ((i & 1) ? 8 : 0) + r) * LD + ks + ((i & 2) ? 8 : 0), a[0], a[1], a[2], a[3]);
 }
 
-// B fragments of two slices (n 8 x k 16 of [n][k] tiles at t0 and t1, ld kEmuLd).
+// B fragments of two slices (n 8 x k 16 of [n][k] tiles at t0 and t1, row stride LD).
+template <int LD = kEmuLd>
 __device__ __forceinline__ void ld_bfrag2(const unsigned short* t0, const unsigned short* t1, int n0, int ks,
                                           unsigned (&b0)[2], unsigned (&b1)[2]) {
   const int lane = threadIdx.x & 31, i = lane >> 3, r = lane & 7;
   const unsigned short* t = (i & 2) ? t1 : t0;
-  ldsm_x4(t + (n0 + r) * kEmuLd + ks + ((i & 1) ? 8 : 0), b0[0], b0[1], b1[0], b1[1]);
+  ldsm_x4(t + (n0 + r) * LD + ks + ((i & 1) ? 8 : 0), b0[0], b0[1], b1[0], b1[1]);
 }
 
 constexpr int kEmuThreads = 512;   // 16 warps, one 16 x 8 output tile each
@@ -1015,6 +1017,346 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       }
     }
   }
+}
+
+// ------------------------------------------------------------------------------
+// a7 (leaf), emulated mode: blocked Householder QR of A'_b (parked in Q's rows by
+// the emulated update, or A when k0 = 0) in shared memory.  Panels of kNB
+// columns are factorized in FP64 (as k_leaf); the trailing update of each panel,
+//   W = Y_J^* C,   W <- T_J^* W,   C <- C - Y_J W,
+// runs its two products on bf16 tensor cores with the integer slices:
+//   W: A = Y_J^T (rows: the panel's columns), B = C^T, real-embedded rows as the
+//      contraction (32 steps per chunk, one fold per 128), column scales of Y_J
+//      and C, complex outputs as in the Gram (swapped pairs for Im W);
+//   C: A = rows of Y_J (contraction over the panel's columns, 16 real steps),
+//      B = W' with the scales of Y_J's columns moved in (as the rank-k0 update).
+// Output as k_leaf's compact-WY mode: R_b into the tree's leaf node, Y into Q's
+// rows, the betas into the workspace.
+// Shared: Lb [kp][P] S | vdiag, rdiag, beta, T (kNB x kNB), W (kNB x kp) | scales |
+// slices: step W: A [8][16][40], B [8][kpc][40]; step C: A [8][32][24], B [8][kpc][24].
+constexpr int kLeKT = 32;   // real contraction steps per chunk of the W product
+constexpr int kLeLdW = 40;  // row stride of the W-product slices (conflict-free ldmatrix)
+constexpr int kLeLdC = 24;  // row stride of the C-product slices (16 steps + pad)
+__host__ __device__ inline size_t leaf_emu_smem(int P, int kp, size_t elem) {
+  const size_t sw = (size_t)kEmuSlices * 2 * kLeLdW * (16 + 24);
+  const size_t sc = (size_t)kEmuSlices * 2 * kLeLdC * (32 + 24);
+  return (size_t)P * kp * elem + (size_t)kMaxKP * (2 * elem + 8) + (size_t)kNB * kNB * elem +
+         (size_t)kNB * kMaxKP * elem + sizeof(int) * (kNB + 2 * kMaxKP) + (sw > sc ? sw : sc) + 64;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, const Io* iot, Io io0,
+                                                         const WorkItem* items, void* ws, int P, int from_q) {
+  constexpr bool C = Tr<S>::C;
+  constexpr int RPE = C ? 2 : 1;
+  constexpr int NW = kThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const Io io = get_io(iot, io0, it.inst);
+  const int k = (int)I.k, kp = I.kp;
+  const int64_t lo = leaf_lo(I, it.idx);
+  const int rb = (int)(leaf_lo(I, it.idx + 1) - lo);
+  S* Lb = reinterpret_cast<S*>(smem_raw);
+  S* vdiag = Lb + (size_t)P * kp;
+  S* rdiag = vdiag + kMaxKP;
+  double* beta_s = reinterpret_cast<double*>(rdiag + kMaxKP);
+  S* T = reinterpret_cast<S*>(beta_s + kMaxKP);  // T(i, l) = T[i + l * kNB]
+  S* Wb = T + kNB * kNB;                          // W(l, c) = Wb[l + c * kNB]
+  int* eY = reinterpret_cast<int*>(Wb + kNB * kMaxKP);
+  int* eC = eY + kNB;
+  int* eZ = eC + kMaxKP;
+  unsigned short* Us = reinterpret_cast<unsigned short*>(
+      (reinterpret_cast<uintptr_t>(eZ + kMaxKP) + 15) & ~(uintptr_t)15);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+
+  const S* Asrc = from_q ? reinterpret_cast<const S*>(io.Q) : reinterpret_cast<const S*>(io.A);
+  const int64_t ldsrc = from_q ? io.ldq : io.lda;
+  for (int e = threadIdx.x; e < P * kp; e += kThreads) {
+    const int r = e % P, c = e / P;
+    Lb[e] = (r < rb && c < k) ? Asrc[(lo + r) + (int64_t)c * ldsrc] : zero<S>();
+  }
+  __syncthreads();
+  auto Yv = [&](int r, int l) -> S { return r == l ? vdiag[l] : (r > l ? Lb[r + l * P] : zero<S>()); };
+
+  for (int J = 0; J < k; J += kNB) {
+    const int jb = min(kNB, k - J);
+    // Panel factorization (FP64), column by column.
+    for (int j = J; j < J + jb; ++j) {
+      if (warp == 0) {
+        double sn = 0.0;
+        for (int i = j + lane; i < rb; i += 32) sn += abs2d(Lb[i + j * P]);
+        sn = warp_sum(sn);
+        if (lane == 0) {
+          double b;
+          S vj, rjj;
+          make_reflector<S>(sn, Lb[j + j * P], b, vj, rjj);
+          beta_s[j] = b;
+          vdiag[j] = vj;
+          rdiag[j] = rjj;
+        }
+      }
+      __syncthreads();
+      const double b = beta_s[j];
+      if (b != 0.0) {
+        for (int c = j + 1 + warp; c < J + jb; c += NW) {
+          S d = zero<S>();
+          for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
+          d = scale(warp_sum(d), b);
+          for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
+        }
+      }
+      __syncthreads();
+    }
+    const int c0 = J + jb, nc = k - c0;
+    if (nc <= 0) break;
+    // T of this panel (forward accumulation), FP64.
+    for (int pr = warp; pr < jb * jb; pr += NW) {
+      const int l = pr % jb, i = pr / jb;
+      if (l >= i) continue;
+      S d = zero<S>();
+      for (int r = J + i + lane; r < rb; r += 32) d = cmadd(d, Yv(r, J + l), Yv(r, J + i));
+      d = warp_sum(d);
+      if (lane == 0) Wb[l + i * kNB] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x < jb) {
+      const int l = threadIdx.x;
+      for (int i = 0; i < jb; ++i) T[l + i * kNB] = zero<S>();
+      T[l + l * kNB] = from_real<S>(beta_s[J + l]);
+      for (int i = l + 1; i < jb; ++i) {
+        S s2 = zero<S>();
+        for (int lp = l; lp < i; ++lp) s2 = madd(s2, T[l + lp * kNB], Wb[lp + i * kNB]);
+        T[l + i * kNB] = scale(s2, -beta_s[J + i]);
+      }
+    }
+    // Column scales over the panel's rows J..rb-1: Y_J's columns and C's columns.
+    for (int col = warp; col < jb + nc; col += NW) {
+      int m = 0;
+      for (int r = J + lane; r < rb; r += 32) {
+        const S v = col < jb ? Yv(r, J + col) : Lb[r + (c0 + col - jb) * P];
+        m = max(m, dexp(real_(v)));
+        if constexpr (C) m = max(m, dexp(v.y));
+      }
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) {
+        if (col < jb) eY[col] = m;
+        else eC[col - jb] = m;
+      }
+    }
+    __syncthreads();
+    const int kpc = (nc + 7) / 8 * 8;
+    const int NT = (C ? 2 : 1) * kpc / 8;
+    // ---- W = Y_J^* C on tensor cores
+    {
+      unsigned short* Aw = Us;                           // [8][16][kLeLdW]
+      unsigned short* Bw = Us + kEmuSlices * 16 * kLeLdW;  // [8][kpc][kLeLdW]
+      const bool mine = warp < NT;
+      const bool imag = C && warp * 8 >= kpc;
+      const int jb0 = imag ? warp * 8 - kpc : warp * 8;
+      float acc[kEmuLevels][4];
+      long long hi[4] = {0, 0, 0, 0}, lo4[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+      const int nq = (rb - J) * RPE;
+      int chunk = 0;
+      for (int q0 = 0; q0 < nq; q0 += kLeKT, ++chunk) {
+        // pairs: A rows l < 16 (l < jb real), B rows j < kpc (j < nc real); q pair in 0..30
+        const int npa = 16 * (kLeKT / 2), npb = kpc * (kLeKT / 2);
+        for (int e2 = threadIdx.x; e2 < npa + npb; e2 += kThreads) {
+          const bool isA = e2 < npa;
+          const int f = isA ? e2 : e2 - npa;
+          const int row = f / (kLeKT / 2), q = 2 * (f % (kLeKT / 2)), qa = q0 + q;
+          double x0 = 0.0, x1 = 0.0;
+          int em = 0;
+          if (isA ? row < jb : row < nc) {
+            const int col = isA ? J + row : c0 + row;
+            auto part = [&](int qq) -> double {
+              if (qq >= nq) return 0.0;
+              const int r = J + qq / RPE;
+              const S v = isA ? Yv(r, col) : Lb[r + col * P];
+              if constexpr (C) return (qq & 1) ? v.y : v.x;
+              else return v;
+            };
+            x0 = part(qa);
+            x1 = part(qa + 1);
+            em = isA ? eY[row] : eC[row];
+          }
+          unsigned w[kEmuSlices];
+          emu_split2(x0, x1, em, em, w);
+          unsigned short* dst = isA ? Aw + row * kLeLdW + q : Bw + row * kLeLdW + q;
+          const int pst = isA ? 16 * kLeLdW : kpc * kLeLdW;
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(dst + p * pst) = w[p];
+        }
+        __syncthreads();
+        if (mine) {
+#pragma unroll
+          for (int ks = 0; ks < kLeKT; ks += 16) {
+            unsigned bf[kEmuSlices][2];
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; qq += 2)
+              ld_bfrag2<kLeLdW>(Bw + (qq * kpc) * kLeLdW, Bw + ((qq + 1) * kpc) * kLeLdW, jb0, ks, bf[qq], bf[qq + 1]);
+            if (imag) {
+#pragma unroll
+              for (int qq = 0; qq < kEmuSlices; ++qq) {
+                bf[qq][0] = im_pair(bf[qq][0]);
+                bf[qq][1] = im_pair(bf[qq][1]);
+              }
+            }
+#pragma unroll
+            for (int p = 0; p < kEmuSlices; ++p) {
+              unsigned a[4];
+              ld_afrag<kLeLdW>(Aw + (p * 16) * kLeLdW, 0, ks, a);
+#pragma unroll
+              for (int qq = 0; qq < kEmuSlices; ++qq) {
+                if (p + qq > kEmuLevels - 1) continue;
+                mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+              }
+            }
+          }
+          if ((chunk & 3) == 3) emu_fold(acc, hi, lo4);  // exact for 128 steps
+        }
+        __syncthreads();
+      }
+      if (mine) {
+        emu_fold(acc, hi, lo4);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {  // rows g (< 8) of the 16-row tile
+          const int l = g, j = jb0 + 2 * t4 + e;
+          if (l >= jb || j >= nc) continue;
+          const int sc = eY[l] + eC[j] - 2044;
+          const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+          reinterpret_cast<double*>(Wb + l + j * kNB)[imag ? 1 : 0] = v;
+        }
+      }
+      __syncthreads();
+    }
+    // W <- T^* W (FP64): W(l) = sum_{l' <= l} conj(T(l', l)) W(l'), l descending.
+    for (int c = threadIdx.x; c < nc; c += kThreads) {
+      for (int l = jb - 1; l >= 0; --l) {
+        S s2 = zero<S>();
+        for (int lp = 0; lp <= l; ++lp) s2 = cmadd(s2, T[lp + l * kNB], Wb[lp + c * kNB]);
+        Wb[l + c * kNB] = s2;
+      }
+    }
+    __syncthreads();
+    // ---- C <- C - Y_J W on tensor cores.  W'(l, j) = 2^(eY_l - 1078) W(l, j), real-embedded
+    // along the contraction (complex: (Re W', -Im W') pairs; Im outputs swap).
+    {
+      unsigned short* Ac = Us;                           // [8][32][kLeLdC]
+      unsigned short* Bc = Us + kEmuSlices * 32 * kLeLdC;  // [8][kpc][kLeLdC]
+      auto wp = [&](int q, int j) -> double {  // W' entry at real contraction step q, column j
+        const int l = q / RPE;
+        if (l >= jb || j >= nc) return 0.0;
+        double b;
+        if constexpr (C) {
+          const z64 z = Wb[l + j * kNB];
+          b = (q & 1) ? -z.y : z.x;
+        } else {
+          b = Wb[l + j * kNB];
+        }
+        return scale2(b, eY[l] - 1078);
+      };
+      for (int j = warp; j < kpc; j += NW) {
+        int m = 0;
+        for (int q = lane; q < 16; q += 32) m = max(m, dexp(wp(q, j)));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) eZ[j] = m;
+      }
+      __syncthreads();
+      for (int e2 = threadIdx.x; e2 < kpc * 8; e2 += kThreads) {
+        const int j = e2 / 8, q = 2 * (e2 % 8);
+        unsigned w[kEmuSlices];
+        emu_split2(wp(q, j), wp(q + 1, j), eZ[j], eZ[j], w);
+#pragma unroll
+        for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Bc + (p * kpc + j) * kLeLdC + q) = w[p];
+      }
+      for (int rc = J; rc < rb; rc += 32) {
+        __syncthreads();  // Bc written; the previous chunk's MMAs are done with Ac
+        for (int e2 = threadIdx.x; e2 < 32 * 8; e2 += kThreads) {
+          const int r = e2 / 8, q = 2 * (e2 % 8), ra = rc + r;
+          double x0 = 0.0, x1 = 0.0;
+          if (ra < rb) {
+            auto part = [&](int qq) -> double {
+              const int l = qq / RPE;
+              if (l >= jb) return 0.0;
+              const S v = Yv(ra, J + l);
+              if constexpr (C) return (qq & 1) ? v.y : v.x;
+              else return v;
+            };
+            x0 = part(q);
+            x1 = part(q + 1);
+          }
+          const int l0 = q / RPE, l1 = (q + 1) / RPE;
+          unsigned w[kEmuSlices];
+          emu_split2(x0, x1, l0 < jb ? eY[l0] : 0, l1 < jb ? eY[l1] : 0, w);
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Ac + (p * 32 + r) * kLeLdC + q) = w[p];
+        }
+        __syncthreads();
+        for (int tile = warp; tile < 2 * NT; tile += NW) {
+          const int mt = tile / NT, nt = tile % NT;
+          const bool imag = C && nt * 8 >= kpc;
+          const int jb0 = imag ? nt * 8 - kpc : nt * 8;
+          float acc[kEmuLevels][4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+          unsigned bf[kEmuSlices][2];
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; qq += 2)
+            ld_bfrag2<kLeLdC>(Bc + (qq * kpc) * kLeLdC, Bc + ((qq + 1) * kpc) * kLeLdC, jb0, 0, bf[qq], bf[qq + 1]);
+          if (imag) {
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              bf[qq][0] = im_pair_update(bf[qq][0]);
+              bf[qq][1] = im_pair_update(bf[qq][1]);
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) {
+            unsigned a[4];
+            ld_afrag<kLeLdC>(Ac + (p * 32) * kLeLdC, mt * 16, 0, a);
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              if (p + qq > kEmuLevels - 1) continue;
+              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+            }
+          }
+          long long hi[4] = {0, 0, 0, 0}, lo4[4] = {0, 0, 0, 0};
+          emu_fold(acc, hi, lo4);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int ra = rc + mt * 16 + g + (e >= 2 ? 8 : 0);
+            const int j = jb0 + 2 * t4 + (e & 1);
+            if (ra >= rb || j >= nc) continue;
+            const int sc = eZ[j] - 966;
+            const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+            double* o = reinterpret_cast<double*>(Lb + ra + (c0 + j) * P) + (imag ? 1 : 0);
+            *o -= v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // R into the tree's leaf node, Y into Q's rows, the betas into the workspace.
+  S* Rn = wsp<S>(ws, I.oRn) + (I.lev_off[0] + it.idx) * (int64_t)(k * k);
+  for (int e = threadIdx.x; e < k * k; e += kThreads) {
+    const int i = e % k, c = e / k;
+    Rn[e] = i < c ? Lb[i + c * P] : (i == c ? rdiag[c] : zero<S>());
+  }
+  S* Q = reinterpret_cast<S*>(io.Q);
+  for (int e = threadIdx.x; e < rb * k; e += kThreads) {
+    const int r = e % rb, c = e / rb;
+    Q[(lo + r) + (int64_t)c * io.ldq] = Yv(r, c);
+  }
+  S* bt = wsp<S>(ws, I.oBeta) + (int64_t)it.idx * k;
+  for (int c = threadIdx.x; c < k; c += kThreads) bt[c] = from_real<S>(beta_s[c]);
 }
 
 }  // namespace tho

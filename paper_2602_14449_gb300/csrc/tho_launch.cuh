@@ -137,6 +137,8 @@ cudaError_t configure_impl(PlanCore& pc) {
   if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
+  pc.smem_leaf_emu = leaf_emu_smem(pc.P, pc.kpmax, sizeof(S));
+  if (EMU && (e = raise((const void*)k_leaf_emu<S>, pc.smem_leaf_emu)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
   int n = 0;
@@ -178,8 +180,15 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     hk(kPhUpdateA, 1, st);
   }
   hk(kPhLeaf, 0, st);
-  k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
-                                                         ((EMU && pc.any_k0) ? 1 : 0) | (EMU ? 2 : 0));
+  // Emulated mode: the leaf QR ends with the compact WY output.  Its trailing
+  // updates go to tensor cores when they are wide enough to pay for the
+  // slicing (complex, k >= 24: two CTAs per SM instead of three); else FP64.
+  if (EMU && pc.dtype == 1 && pc.kmax >= 24)  // dtype 1: complex128
+    k_leaf_emu<S><<<pc.tab.leaf_n, blk, pc.smem_leaf_emu, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
+                                                               pc.any_k0 ? 1 : 0);
+  else
+    k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
+                                                         EMU ? ((pc.any_k0 ? 1 : 0) | 2) : 0);
   hk(kPhLeaf, 1, st);
   hk(kPhTreeUp, 0, st);
   for (int l = 1; l <= pc.Lmax; ++l)

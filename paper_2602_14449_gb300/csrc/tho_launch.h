@@ -46,7 +46,7 @@ struct PlanCore {
   size_t smem_apply_emu = 0;
   size_t smem_gram_pipe = 0, smem_gram_umma = 0;
   bool gram_umma = false;  // emulated Gram on tcgen05 (when its stages fit)
-  size_t smem_upd_umma = 0;
+  size_t smem_upd_umma = 0, smem_leaf_emu = 0;
   bool upd_umma = false;   // emulated rank-k0 updates on tcgen05 (reading the V slices the Gram kept)
   bool gram_pipe = false;  // emulated Gram: pipelined variant (when its buffers fit)
   size_t smem_gram_emu = 0;  // emulated split-n Gram (THO_PREC_FP64_EMU)

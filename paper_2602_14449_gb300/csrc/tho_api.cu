@@ -65,6 +65,9 @@ void free_plan(tho_plan_s* p) {
   }
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->pc.side) cudaStreamDestroy(p->pc.side);
+  if (p->pc.ev_fork) cudaEventDestroy(p->pc.ev_fork);
+  if (p->pc.ev_join) cudaEventDestroy(p->pc.ev_join);
   if (p->io_ev) cudaEventDestroy(p->io_ev);
   if (p->h_io) cudaFreeHost(p->h_io);
   if (p->d_io) cudaFree(p->d_io);
@@ -207,7 +210,9 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   if (pc.P == 0) { free_plan(p); return THO_ERR_UNSUPPORTED; }
 
   // Per-instance partition and workspace layout.
-  const int64_t target_total = (count == 1 ? 2 : 8) * (int64_t)sms;
+  // Single problem: two chunks per SM less one, so that the SM running the
+  // small QR of V_{1:k0,:} beside the first Gram sweep takes one chunk fewer.
+  const int64_t target_total = count == 1 ? 2 * (int64_t)sms - 1 : 8 * (int64_t)sms;
   double msum = 0;
   for (int i = 0; i < count; ++i) msum += (double)(descs[i].n - descs[i].k0);
   int64_t off = 0;
@@ -332,6 +337,12 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
       free_plan(p);
       return THO_ERR_CUDA;
     }
+  }
+  if (pc.any_k0 && (cudaStreamCreateWithFlags(&p->pc.side, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&p->pc.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&p->pc.ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+    free_plan(p);
+    return THO_ERR_CUDA;
   }
   *out = p;
   return THO_OK;

@@ -159,9 +159,16 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   void* ws = pc.ws;
   const dim3 blk(kThreads);
   if (pc.any_k0) {
-    hk(kPhQrV1, 0, st);
-    k_v1qr<S><<<pc.count, kV1Threads, 0, st>>>(insts, d_io, io0, ws);
-    hk(kPhQrV1, 1, st);
+    // QR of V_{1:k0,:} on the side stream, overlapping the first Gram sweep.
+    cudaStream_t sq = pc.side ? pc.side : st;
+    if (pc.side) {
+      cudaEventRecord(pc.ev_fork, st);
+      cudaStreamWaitEvent(sq, pc.ev_fork, 0);
+    }
+    hk(kPhQrV1, 0, sq);
+    k_v1qr<S><<<pc.count, kV1Threads, 0, sq>>>(insts, d_io, io0, ws);
+    hk(kPhQrV1, 1, sq);
+    if (pc.side) cudaEventRecord(pc.ev_join, sq);
     if (pc.tab.gram_n > 0) {
       hk(kPhGram, 0, st);
       if (EMU)
@@ -170,6 +177,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
         k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
       hk(kPhGram, 1, st);
     }
+    if (pc.side) cudaStreamWaitEvent(st, pc.ev_join, 0);
     hk(kPhSolveZ, 0, st);
     k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
     hk(kPhSolveZ, 1, st);

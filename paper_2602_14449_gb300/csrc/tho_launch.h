@@ -26,6 +26,10 @@ struct Tables {
 };
 
 struct PlanCore {
+  // Side stream (and fork / join events) for the QR of V_{1:k0,:}, which the
+  // first Gram sweep does not need: the two overlap.  Null: one stream.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int count = 0;
   int dtype = 0, prec = 0;
   uint32_t flags = 0;

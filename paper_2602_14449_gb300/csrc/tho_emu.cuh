@@ -127,6 +127,51 @@ __device__ __forceinline__ void emu_split2(double x0, double x1, int emax0, int 
   }
 }
 
+// (hi 2^28 + lo) 2^(sc - 63) for the two exact int64 accumulators of a fold,
+// correctly rounded to nearest even with integer instructions only: the exact
+// 128-bit sum, its leading-zero count, the top 53 bits with round and sticky
+// bits, and the exponent placed in the bit pattern.  Outside the normal
+// exponent range it falls back to the FP64 scaling.
+__device__ __forceinline__ double emu_fx(long long hi, long long lo, int sc) {
+  unsigned long long xl = (unsigned long long)hi << 28;
+  unsigned long long xh = (unsigned long long)(hi >> 36);
+  const unsigned long long a = xl;
+  xl += (unsigned long long)lo;
+  xh += (unsigned long long)(lo >> 63) + (xl < a ? 1ull : 0ull);
+  const bool neg = (long long)xh < 0;
+  if (neg) {
+    xl = ~xl + 1ull;
+    xh = ~xh + (xl == 0 ? 1ull : 0ull);
+  }
+  if ((xh | xl) == 0) return 0.0;
+  const int lz = xh ? __clzll((long long)xh) : 64 + __clzll((long long)xl);
+  unsigned long long nh, nl;
+  if (lz >= 64) {
+    nh = xl << (lz - 64);
+    nl = 0;
+  } else if (lz == 0) {
+    nh = xh;
+    nl = xl;
+  } else {
+    nh = (xh << lz) | (xl >> (64 - lz));
+    nl = xl << lz;
+  }
+  unsigned long long mant = nh >> 11;
+  const bool rbit = (nh >> 10) & 1ull, sticky = (nh & 0x3ffull) != 0 || nl != 0;
+  int t = 127 - lz;
+  if (rbit && (sticky || (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++t;
+    }
+  }
+  const int E = t + (sc - 63) + 1023;
+  if (E <= 0 || E >= 2047) return emu_fx((long long)hi, (long long)lo, sc);
+  return __longlong_as_double((long long)(((unsigned long long)(neg ? 1 : 0) << 63) |
+                                          ((unsigned long long)E << 52) | (mant & 0xfffffffffffffull)));
+}
+
 __device__ __forceinline__ unsigned short bf16_bits(float v) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));  // exact: |v| <= 127 integer
 }
@@ -348,7 +393,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_gram_emu(const Inst* insts, 
         const int j = jb0 + 2 * t4 + (e & 1);
         if (i >= k0 || j >= k) continue;
         const int sc = eV[i] + eA[j] - 2044;
-        const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo[e], sc - 63);
+        const double v = emu_fx((long long)hi[e], (long long)lo[e], sc);
         double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
         if constexpr (C) o[imag ? 1 : 0] = v;
         else o[0] = v;
@@ -541,7 +586,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_gram_emu_pipe(const Inst* in
         const int j = jb0 + 2 * t4 + (e & 1);
         if (i >= k0 || j >= k) continue;
         const int sc = eV[i] + eA[j] - 2044;
-        const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo[e], sc - 63);
+        const double v = emu_fx((long long)hi[e], (long long)lo[e], sc);
         double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
         if constexpr (C) o[imag ? 1 : 0] = v;
         else o[0] = v;
@@ -743,7 +788,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
           const int j = jb0 + 2 * t4 + (e & 1);
           if (r < nr && j < k) {
             const int sc = eZ[j] - 966;
-            const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo[e], sc - 63);
+            const double v = emu_fx((long long)hi[e], (long long)lo[e], sc);
             const int64_t ob = (int64_t)j * ldb + (r0 + r) * RPE + (imag ? 1 : 0);
             const int64_t oq = (int64_t)j * ldq + (r0 + r) * RPE + (imag ? 1 : 0);
             Qd[oq] = Bd[ob] + v;
@@ -898,7 +943,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
           const int j = gjb0 + 2 * t4 + (e & 1);
           if (i >= k || j >= k) continue;
           const int sc = eV[i] + eV[j] - 2044;
-          const double v = scale2((double)ghi[e], sc - 35) + scale2((double)glo[e], sc - 63);
+          const double v = emu_fx((long long)ghi[e], (long long)glo[e], sc);
           reinterpret_cast<double*>(Gs + i + j * k)[gimag ? 1 : 0] = v;
         }
       }
@@ -1010,7 +1055,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
         const int j = jb0 + 2 * t4 + (e & 1);
         if (r < rb && j < k) {
           const int sc = eZ[j] - 966;
-          double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+          double v = emu_fx((long long)hi[e], (long long)lo4[e], sc);
           if (wy && r < k) v += reinterpret_cast<const double*>(Fr + r + j * ldf)[imag ? 1 : 0];  // [F_b; 0]
           reinterpret_cast<double*>(Qg + (lo + r) + (int64_t)j * ldq)[imag ? 1 : 0] = v;
         }
@@ -1228,7 +1273,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
           const int l = g, j = jb0 + 2 * t4 + e;
           if (l >= jb || j >= nc) continue;
           const int sc = eY[l] + eC[j] - 2044;
-          const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+          const double v = emu_fx((long long)hi[e], (long long)lo4[e], sc);
           reinterpret_cast<double*>(Wb + l + j * kNB)[imag ? 1 : 0] = v;
         }
       }
@@ -1335,7 +1380,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
             const int j = jb0 + 2 * t4 + (e & 1);
             if (ra >= rb || j >= nc) continue;
             const int sc = eZ[j] - 966;
-            const double v = scale2((double)hi[e], sc - 35) + scale2((double)lo4[e], sc - 63);
+            const double v = emu_fx((long long)hi[e], (long long)lo4[e], sc);
             double* o = reinterpret_cast<double*>(Lb + ra + (c0 + j) * P) + (imag ? 1 : 0);
             *o -= v;
           }

@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
       if (j >= k) continue;
       // value = (hi 2^28 + lo) 2^(sc - 63), as hi 2^(sc - 35) + lo 2^(sc - 63)
       const int sc = eV[i] + eA[j] - 2044;
-      const double v = scale2((double)hi[c], sc - 35) + scale2((double)lo[c], sc - 63);
+      const double v = emu_fx((long long)hi[c], (long long)lo[c], sc);
       double* o = reinterpret_cast<double*>(out + i + (int64_t)j * k0);
       if constexpr (C) o[imag ? 1 : 0] = v;
       else o[0] = v;
@@ -667,6 +667,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
         }
         if (row < r_end && j < k) {
           const int sc = eZ[j] - 966;
+          // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
           const double v = scale2((double)hh, sc - 35) + scale2((double)ll, sc - 63);
           Qd[(int64_t)j * ldq + row * RPE + part] = Bd[(int64_t)j * ldb + row * RPE + part] + v;
         }

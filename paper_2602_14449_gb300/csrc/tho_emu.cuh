@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
 // into the second operand, F'(q, j) = 2^(e_i - 1078) B(q, j) with B the real
 // embedding of F_b used by the rank-k0 update, which is sliced per column j.
 // The contraction (k columns, real-embedded) is at most 64 steps: one fold.
-// Shared: Qr [P][k+1] S | Fr [k][k] S | Zs [8][kpe][kEmuLd] | Vs [8][TM][kEmuLd] bf16 | eV | eZ.
+// Shared: Qr [P][k+1] S | Fr [k][k] S | Zs [8][kpe][kEmuLd] | Vs [8][max(TM, k16)][kEmuLd] bf16 | eV | eZ.
 //
 // wy != 0: Q's rows hold the leaf's Householder vectors Y (v_j on the diagonal,
 // zero above) and the workspace its betas, instead of the explicit leaf Q.
@@ -845,7 +845,10 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
   S* Ms = Ts + kk2;
   unsigned short* Zs = reinterpret_cast<unsigned short*>(Fr + (wy ? 4 : 1) * kk2);
   unsigned short* Vs = Zs + kEmuSlices * kpe * kEmuLd;
-  int* eV = reinterpret_cast<int*>(Vs + kEmuSlices * TM * kEmuLd);
+  // Vs holds one row tile (TM rows) or, with wy, the slices of Y^T (k rounded
+  // up to 16 rows).
+  const int vs_rows = max(TM, (k + 15) / 16 * 16);
+  int* eV = reinterpret_cast<int*>(Vs + kEmuSlices * vs_rows * kEmuLd);
   int* eZ = eV + kMaxKP;
   S* Qg = reinterpret_cast<S*>(io.Q);
   const int64_t ldq = io.ldq;
@@ -879,7 +882,17 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
     if (wy) {
       // (1) G = Y^* Y over the leaf's rows, 64 real steps per chunk; Vs holds
       // the slices of Y^T (rows = columns of Y), serving as both operands.
+      // The first chunk (rows < 64 / RPE >= k) also gives B = Y_1^* F_b on
+      // the same tiles, with the slices of F_b^T in Zs (free until the main
+      // product) and F_b's column scales in eZ.
       const int kr = (k + 15) / 16 * 16;
+      for (int j = warp; j < k; j += NW) {
+        int m = 0;
+        for (int q = lane; q < k * RPE; q += 32)
+          m = max(m, dexp(reinterpret_cast<const double*>(Fr + (q / RPE) + j * ldf)[q % RPE]));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) eZ[j] = m;
+      }
       const bool gmine = warp < (kr / 16) * NT;
       const int gmt = gmine ? warp / NT : 0, gnt = gmine ? warp % NT : 0;
       const bool gimag = C && gnt * 8 >= kpe;
@@ -907,7 +920,59 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * kr + l) * kEmuLd + q) = w[p];
         }
+        if (chunk == 0) {
+          for (int e2 = threadIdx.x; e2 < kpe * (kEmuKT / 2); e2 += kEmuThreads) {
+            const int j = e2 / (kEmuKT / 2), q = 2 * (e2 % (kEmuKT / 2));
+            double x0 = 0.0, x1 = 0.0;
+            if (j < k) {
+              if (q < k * RPE) x0 = reinterpret_cast<const double*>(Fr + (q / RPE) + j * ldf)[q % RPE];
+              if (q + 1 < k * RPE) x1 = reinterpret_cast<const double*>(Fr + ((q + 1) / RPE) + j * ldf)[(q + 1) % RPE];
+            }
+            const int em = j < k ? eZ[j] : 0;
+            unsigned w[kEmuSlices];
+            emu_split2(x0, x1, em, em, w);
+#pragma unroll
+            for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Zs + (p * kpe + j) * kEmuLd + q) = w[p];
+          }
+        }
         __syncthreads();
+        if (gmine && chunk == 0) {
+          // B = Y_1^* F_b (acc is still zero here; the fold clears it again).
+          const int kzf = (k * RPE + 15) / 16 * 16;
+          for (int ks = 0; ks < kzf; ks += 16) {
+            unsigned bf[kEmuSlices][2];
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; qq += 2)
+              ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, gjb0, ks, bf[qq], bf[qq + 1]);
+            if (gimag) {
+#pragma unroll
+              for (int qq = 0; qq < kEmuSlices; ++qq) {
+                bf[qq][0] = im_pair(bf[qq][0]);
+                bf[qq][1] = im_pair(bf[qq][1]);
+              }
+            }
+#pragma unroll
+            for (int p = 0; p < kEmuSlices; ++p) {
+              unsigned a[4];
+              ld_afrag(Vs + (p * kr) * kEmuLd, gmt * 16, ks, a);
+#pragma unroll
+              for (int qq = 0; qq < kEmuSlices; ++qq) {
+                if (p + qq > kEmuLevels - 1) continue;
+                mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+              }
+            }
+          }
+          long long bhi[4] = {0, 0, 0, 0}, blo[4] = {0, 0, 0, 0};
+          emu_fold(acc, bhi, blo);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int l = gmt * 16 + g + (e >= 2 ? 8 : 0);
+            const int j = gjb0 + 2 * t4 + (e & 1);
+            if (l >= k || j >= k) continue;
+            const double v = emu_fx((long long)bhi[e], (long long)blo[e], eV[l] + eZ[j] - 2044);
+            reinterpret_cast<double*>(Ms + l + j * ldf)[gimag ? 1 : 0] = v;
+          }
+        }
         if (gmine) {
           for (int ks = 0; ks < kEmuKT; ks += 16) {
             unsigned bf[kEmuSlices][2];
@@ -948,15 +1013,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
         }
       }
       __syncthreads();
-      // (2) B = Y_1^* F_b into Ms (Y_1 lower triangular: Y(c, l) = 0 for c < l);
-      // a warp takes one row l (uniform loop length), lanes the columns j.
-      for (int e = threadIdx.x; e < kk; e += kEmuThreads) {
-        const int l = e / k, j = e % k;
-        S b = zero<S>();
-        for (int c = l; c < k; ++c) b = cmadd(b, Qr[c * ldr + l], Fr[c + j * ldf]);
-        Ms[l + j * ldf] = b;
-      }
-      __syncthreads();
+      // (2) B = Y_1^* F_b is in Ms (first chunk above).
       // (3) M = T B without forming T: T^-1 = diag(1/beta) + (strictly upper part
       // of G), so M solves that upper triangular system; right-looking back
       // substitution: row i is final once scaled by beta_i, then it is removed
@@ -1078,12 +1135,12 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
 // Output as k_leaf's compact-WY mode: R_b into the tree's leaf node, Y into Q's
 // rows, the betas into the workspace.
 // Shared: Lb [kp][P] S | vdiag, rdiag, beta, T (kNB x kNB), W (kNB x kp) | scales |
-// slices: step W: A [8][16][40], B [8][kpc][40]; step C: A [8][32][24], B [8][kpc][24].
+// slices: step W: A [8][16][40], B [8][kpc + 8][40]; step C: A [8][32][24], B [8][kpc][24].
 constexpr int kLeKT = 32;   // real contraction steps per chunk of the W product
 constexpr int kLeLdW = 40;  // row stride of the W-product slices (conflict-free ldmatrix)
 constexpr int kLeLdC = 24;  // row stride of the C-product slices (16 steps + pad)
 __host__ __device__ inline size_t leaf_emu_smem(int P, int kp, size_t elem) {
-  const size_t sw = (size_t)kEmuSlices * 2 * kLeLdW * (16 + 24);
+  const size_t sw = (size_t)kEmuSlices * 2 * kLeLdW * (16 + kMaxKP);
   const size_t sc = (size_t)kEmuSlices * 2 * kLeLdC * (32 + 24);
   return (size_t)P * kp * elem + (size_t)kMaxKP * (2 * elem + 8) + (size_t)kNB * kNB * elem +
          (size_t)kNB * kMaxKP * elem + sizeof(int) * (kNB + 2 * kMaxKP) + (sw > sc ? sw : sc) + 64;
@@ -1155,26 +1212,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     }
     const int c0 = J + jb, nc = k - c0;
     if (nc <= 0) break;
-    // T of this panel (forward accumulation), FP64.
-    for (int pr = warp; pr < jb * jb; pr += NW) {
-      const int l = pr % jb, i = pr / jb;
-      if (l >= i) continue;
-      S d = zero<S>();
-      for (int r = J + i + lane; r < rb; r += 32) d = cmadd(d, Yv(r, J + l), Yv(r, J + i));
-      d = warp_sum(d);
-      if (lane == 0) Wb[l + i * kNB] = d;
-    }
-    __syncthreads();
-    if (threadIdx.x < jb) {
-      const int l = threadIdx.x;
-      for (int i = 0; i < jb; ++i) T[l + i * kNB] = zero<S>();
-      T[l + l * kNB] = from_real<S>(beta_s[J + l]);
-      for (int i = l + 1; i < jb; ++i) {
-        S s2 = zero<S>();
-        for (int lp = l; lp < i; ++lp) s2 = madd(s2, T[l + lp * kNB], Wb[lp + i * kNB]);
-        T[l + i * kNB] = scale(s2, -beta_s[J + i]);
-      }
-    }
     // Column scales over the panel's rows J..rb-1: Y_J's columns and C's columns.
     for (int col = warp; col < jb + nc; col += NW) {
       int m = 0;
@@ -1192,13 +1229,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     __syncthreads();
     const int kpc = (nc + 7) / 8 * 8;
     const int NT = (C ? 2 : 1) * kpc / 8;
-    // ---- W = Y_J^* C on tensor cores
+    // ---- [W | G] = Y_J^* [C | Y_J] on tensor cores: B rows 0..kpc-1 are C's
+    // columns, rows kpc..kpc+7 the panel's own columns, so the panel's Gram
+    // G = Y_J^* Y_J comes out of the same product (the FP64 alternative is one
+    // warp dot product per pair of columns).
     {
+      const int kpb = kpc + kNB, NTB = (C ? 2 : 1) * kpb / 8;
       unsigned short* Aw = Us;                           // [8][16][kLeLdW]
-      unsigned short* Bw = Us + kEmuSlices * 16 * kLeLdW;  // [8][kpc][kLeLdW]
-      const bool mine = warp < NT;
-      const bool imag = C && warp * 8 >= kpc;
-      const int jb0 = imag ? warp * 8 - kpc : warp * 8;
+      unsigned short* Bw = Us + kEmuSlices * 16 * kLeLdW;  // [8][kpb][kLeLdW]
+      const bool mine = warp < NTB;
+      const bool imag = C && warp * 8 >= kpb;
+      const int jb0 = imag ? warp * 8 - kpb : warp * 8;
       float acc[kEmuLevels][4];
       long long hi[4] = {0, 0, 0, 0}, lo4[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -1208,31 +1249,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
       const int nq = (rb - J) * RPE;
       int chunk = 0;
       for (int q0 = 0; q0 < nq; q0 += kLeKT, ++chunk) {
-        // pairs: A rows l < 16 (l < jb real), B rows j < kpc (j < nc real); q pair in 0..30
-        const int npa = 16 * (kLeKT / 2), npb = kpc * (kLeKT / 2);
+        // pairs: A rows l < 16 (l < jb real), B rows j < kpb (C column j < nc, or
+        // panel column j - kpc < jb); q pair in 0..30
+        const int npa = 16 * (kLeKT / 2), npb = kpb * (kLeKT / 2);
         for (int e2 = threadIdx.x; e2 < npa + npb; e2 += kThreads) {
           const bool isA = e2 < npa;
           const int f = isA ? e2 : e2 - npa;
           const int row = f / (kLeKT / 2), q = 2 * (f % (kLeKT / 2)), qa = q0 + q;
+          const int yl = isA ? row : row - kpc;  // panel column of a Y row, else < 0
           double x0 = 0.0, x1 = 0.0;
           int em = 0;
-          if (isA ? row < jb : row < nc) {
-            const int col = isA ? J + row : c0 + row;
+          if ((yl >= 0 && yl < jb) || (!isA && row < nc)) {
+            const bool isY = yl >= 0;
+            const int col = isY ? J + yl : c0 + row;
             auto part = [&](int qq) -> double {
               if (qq >= nq) return 0.0;
               const int r = J + qq / RPE;
-              const S v = isA ? Yv(r, col) : Lb[r + col * P];
+              const S v = isY ? Yv(r, col) : Lb[r + col * P];
               if constexpr (C) return (qq & 1) ? v.y : v.x;
               else return v;
             };
             x0 = part(qa);
             x1 = part(qa + 1);
-            em = isA ? eY[row] : eC[row];
+            em = isY ? eY[yl] : eC[row];
           }
           unsigned w[kEmuSlices];
           emu_split2(x0, x1, em, em, w);
           unsigned short* dst = isA ? Aw + row * kLeLdW + q : Bw + row * kLeLdW + q;
-          const int pst = isA ? 16 * kLeLdW : kpc * kLeLdW;
+          const int pst = isA ? 16 * kLeLdW : kpb * kLeLdW;
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(dst + p * pst) = w[p];
         }
@@ -1243,7 +1287,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
             unsigned bf[kEmuSlices][2];
 #pragma unroll
             for (int qq = 0; qq < kEmuSlices; qq += 2)
-              ld_bfrag2<kLeLdW>(Bw + (qq * kpc) * kLeLdW, Bw + ((qq + 1) * kpc) * kLeLdW, jb0, ks, bf[qq], bf[qq + 1]);
+              ld_bfrag2<kLeLdW>(Bw + (qq * kpb) * kLeLdW, Bw + ((qq + 1) * kpb) * kLeLdW, jb0, ks, bf[qq], bf[qq + 1]);
             if (imag) {
 #pragma unroll
               for (int qq = 0; qq < kEmuSlices; ++qq) {
@@ -1270,22 +1314,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
         emu_fold(acc, hi, lo4);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {  // rows g (< 8) of the 16-row tile
-          const int l = g, j = jb0 + 2 * t4 + e;
-          if (l >= jb || j >= nc) continue;
-          const int sc = eY[l] + eC[j] - 2044;
-          const double v = emu_fx((long long)hi[e], (long long)lo4[e], sc);
-          reinterpret_cast<double*>(Wb + l + j * kNB)[imag ? 1 : 0] = v;
+          const int l = g, j = jb0 + 2 * t4 + e, i = j - kpc;
+          if (l >= jb) continue;
+          if (j < nc) {
+            const double v = emu_fx((long long)hi[e], (long long)lo4[e], eY[l] + eC[j] - 2044);
+            reinterpret_cast<double*>(Wb + l + j * kNB)[imag ? 1 : 0] = v;
+          } else if (i > l && i < jb) {  // G(l, i), strictly upper part only
+            const double v = emu_fx((long long)hi[e], (long long)lo4[e], eY[l] + eY[i] - 2044);
+            reinterpret_cast<double*>(T + l + i * kNB)[imag ? 1 : 0] = v;
+          }
         }
       }
       __syncthreads();
     }
-    // W <- T^* W (FP64): W(l) = sum_{l' <= l} conj(T(l', l)) W(l'), l descending.
+    // W <- T^* W (FP64) without forming T.  T, the triangular factor of
+    // H_J ... H_{J+jb-1} = I - Y_J T Y_J^*, satisfies T^-1 = diag(1/beta) +
+    // (strictly upper part of G) (forward accumulation of the reflectors), so
+    //   (T^* W)(i) = beta_i (W(i) - sum_{l < i} conj(G(l, i)) (T^* W)(l)),
+    // which also holds for beta_i = 0.  Right-looking: row l is final once
+    // scaled, then removed from the rows below.  One thread per column of W.
     for (int c = threadIdx.x; c < nc; c += kThreads) {
-      for (int l = jb - 1; l >= 0; --l) {
-        S s2 = zero<S>();
-        for (int lp = 0; lp <= l; ++lp) s2 = cmadd(s2, T[lp + l * kNB], Wb[lp + c * kNB]);
-        Wb[l + c * kNB] = s2;
+      S x[kNB];
+#pragma unroll
+      for (int l = 0; l < kNB; ++l) x[l] = l < jb ? Wb[l + c * kNB] : zero<S>();
+#pragma unroll
+      for (int l = 0; l < kNB; ++l) {
+        if (l >= jb) break;
+        x[l] = scale(x[l], beta_s[J + l]);
+#pragma unroll
+        for (int i = l + 1; i < kNB; ++i)
+          if (i < jb) x[i] = msub(x[i], conj_(T[l + i * kNB]), x[l]);
       }
+#pragma unroll
+      for (int l = 0; l < kNB; ++l)
+        if (l < jb) Wb[l + c * kNB] = x[l];
     }
     __syncthreads();
     // ---- C <- C - Y_J W on tensor cores.  W'(l, j) = 2^(eY_l - 1078) W(l, j), real-embedded

@@ -159,6 +159,27 @@ __device__ __forceinline__ void update_tile(const B* X, const B* Y, int ldy, int
 // nrm2 = ||x||^2 (FP64) and x_j, returns beta = 2 / (v^* v) (0 for x = 0),
 // v_j = x_j + phase(x_j) ||x|| and the new diagonal -phase(x_j) ||x||.
 // (Reflector convention H = I - beta v v^*, v = x + phase(x_1)||x|| e_1.)
+//
+// |x_j| and phase(x_j): for a complex x_j of moderate size both come from one
+// reciprocal square root of |x_j|^2 (phase = x_j / |x_j| within a few ulps of
+// unit modulus, which changes H only at the rounding level); tiny or huge
+// |x_j| take the scaled hypot.  Each FP64 instruction of this serial step
+// costs a whole warp issue on the FP64 pipe, so the step is kept short.
+__device__ __forceinline__ void abs_phase(double x, double& ax, double& ph) {
+  ax = fabs(x);
+  ph = phase(x);
+}
+__device__ __forceinline__ void abs_phase(z64 x, double& ax, z64& ph) {
+  const double a2 = abs2d(x);
+  if (a2 >= 0x1p-1000 && a2 <= 0x1p+1000) {
+    const double ir = rsqrt(a2);
+    ax = a2 * ir;
+    ph = z64{x.x * ir, x.y * ir};
+  } else {
+    ax = absd(x);
+    ph = phase(x);
+  }
+}
 template <class S>
 __device__ __forceinline__ void make_reflector(double nrm2, S xj, double& beta, S& vj, S& rjj) {
   double alpha = sqrt(nrm2);
@@ -168,8 +189,9 @@ __device__ __forceinline__ void make_reflector(double nrm2, S xj, double& beta, 
     rjj = zero<S>();
     return;
   }
-  double ax = absd(xj);
-  S ph = phase(xj);
+  double ax;
+  S ph;
+  abs_phase(xj, ax, ph);
   vj = add(xj, scale(ph, alpha));
   rjj = scale(ph, -alpha);
   beta = 1.0 / (alpha * (alpha + ax));  // 2 / (2 alpha (alpha + |x_j|))

@@ -225,3 +225,36 @@ def test_emulated_full_size(tho, cid):
     Q, R, S = tho.orth(p.V, p.A, prec=tho.THO_PREC_FP64_EMU)
     assert loo(p.V, Q) < TOL_LOO
     assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_emulated_k0_zero(tho, dtype):
+    """k0 = 0 in the emulated mode: the leaf QR reads A itself (complex k = 32 takes
+    the tensor-core trailing updates) and the apply forms Q from the compact WY form."""
+    n, k = 5000, 32
+    p = inputs.random_problem(n, 0, k, dtype=dtype, seed=12)
+    A = p.A.cuda()
+    V = torch.zeros((n, 0), dtype=dtype, device="cuda")
+    Q, R, _ = tho.orth(V, A, prec=tho.THO_PREC_FP64_EMU)
+    Qo, Ro = oracle.householder_qr(p.A.numpy())
+    np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+    np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=TOL_Q * np.abs(Ro).max())
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_emulated_batched_matches_oracle(tho, dtype):
+    """Batched plans in the emulated mode (mixed k0 and k in one graph: tcgen05 Gram and
+    update per instance, one leaf kernel for all) against the oracle, per problem."""
+    probs = [inputs.random_problem(n, k0, k, dtype=dtype, seed=60 + i) for i, (n, k0, k) in enumerate(BATCH_SHAPES)]
+    pairs = [(p.V.cuda(), p.A.cuda()) for p in probs]
+    res = tho.orth_batched(pairs, prec=tho.THO_PREC_FP64_EMU)
+    torch.cuda.synchronize()
+    for p, (Q, R, S) in zip(probs, res):
+        Qo, Ro, So = oracle.two_stage(p.V.numpy(), p.A.numpy())
+        np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+        np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=TOL_Q * max(1, np.abs(Ro).max()))
+        np.testing.assert_allclose(S.cpu().numpy(), So, atol=TOL_Q * max(1, np.abs(So).max()))
+    res2 = tho.orth_batched(pairs, prec=tho.THO_PREC_FP64_EMU)
+    torch.cuda.synchronize()
+    for (Q, _, _), (Q2, _, _) in zip(res, res2):
+        assert torch.equal(Q, Q2)

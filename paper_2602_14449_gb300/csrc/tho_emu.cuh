@@ -819,7 +819,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
 // + (strictly upper part of G), which holds for the forward product of the
 // reflectors (Puglisi); then the product above with F_b replaced by -M and
 // [F_b; 0] added in the epilogue.
-// Extra shared memory with wy: Gs (G), Ts (unused), Ms [k][k+1] S after Fr.
+// Extra shared memory with wy: Gs (G), Ts (the betas), Ms [k][k+1] S after Fr.
 template <class S, int MTM>
 __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
                                                               const WorkItem* items, void* ws, int P, int wy) {
@@ -886,6 +886,9 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       // the same tiles, with the slices of F_b^T in Zs (free until the main
       // product) and F_b's column scales in eZ.
       const int kr = (k + 15) / 16 * 16;
+      double* bs = reinterpret_cast<double*>(Ts);  // the leaf's betas
+      const S* btg = wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
+      for (int i = threadIdx.x; i < k; i += kEmuThreads) bs[i] = real_(btg[i]);
       for (int j = warp; j < k; j += NW) {
         int m = 0;
         for (int q = lane; q < k * RPE; q += 32)
@@ -1009,20 +1012,18 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
           if (i >= k || j >= k) continue;
           const int sc = eV[i] + eV[j] - 2044;
           const double v = emu_fx((long long)ghi[e], (long long)glo[e], sc);
-          reinterpret_cast<double*>(Gs + i + j * k)[gimag ? 1 : 0] = v;
+          reinterpret_cast<double*>(Gs + i + j * k)[gimag ? 1 : 0] = v * bs[j];  // G(i, j) beta_j
         }
       }
       __syncthreads();
       // (2) B = Y_1^* F_b is in Ms (first chunk above).
       // (3) M = T B without forming T: T^-1 = diag(1/beta) + (strictly upper part
-      // of G), so M solves that upper triangular system; right-looking back
-      // substitution: row i is final once scaled by beta_i, then it is removed
-      // from the rows above (one rank-1 update per step).
-      const S* btg = wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
-      for (int i = k - 1; i >= 0; --i) {
-        const double bi = real_(btg[i]);
-        if (threadIdx.x < k) Ms[i + threadIdx.x * ldf] = scale(Ms[i + threadIdx.x * ldf], bi);
-        __syncthreads();
+      // of G), so M solves that upper triangular system.  With M = diag(beta) U
+      // and G' = G diag(beta) (scaled above), U(i) = B(i) - sum_{l > i} G'(i, l) U(l):
+      // right-looking back substitution, row i final after step i + 1, one
+      // rank-1 update and one barrier per step; the betas are applied when
+      // the second operand is sliced.  Valid for beta_i = 0 too.
+      for (int i = k - 1; i >= 1; --i) {
         for (int e = threadIdx.x; e < i * k; e += kEmuThreads) {
           const int l = e / k, j = e % k;
           Ms[l + j * ldf] = msub(Ms[l + j * ldf], Gs[l + i * k], Ms[i + j * ldf]);
@@ -1030,8 +1031,9 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
         __syncthreads();
       }
     }
-    // Second operand: F_b, or -M with the compact WY form.
+    // Second operand: F_b, or -M = -diag(beta) U with the compact WY form.
     const S* Zsrc = wy ? Ms : Fr;
+    const double* bsc = reinterpret_cast<const double*>(Ts);
     const double zsg = wy ? -1.0 : 1.0;
     auto fp = [&](int q, int j) -> double {
       if (q >= kz || j >= k) return 0.0;
@@ -1043,6 +1045,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       } else {
         b = reinterpret_cast<const double*>(Zsrc)[i + j * ldf];
       }
+      if (wy) b *= bsc[i];
       return scale2(zsg * b, eV[i] - 1078);
     };
     for (int j = warp; j < kpe; j += NW) {
@@ -1183,29 +1186,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
 
   for (int J = 0; J < k; J += kNB) {
     const int jb = min(kNB, k - J);
-    // Panel factorization (FP64), column by column.
-    for (int j = J; j < J + jb; ++j) {
-      if (warp == 0) {
-        double sn = 0.0;
-        for (int i = j + lane; i < rb; i += 32) sn += abs2d(Lb[i + j * P]);
-        sn = warp_sum(sn);
-        if (lane == 0) {
-          double b;
-          S vj, rjj;
-          make_reflector<S>(sn, Lb[j + j * P], b, vj, rjj);
-          beta_s[j] = b;
-          vdiag[j] = vj;
-          rdiag[j] = rjj;
-        }
+    // Panel factorization (FP64), column by column, one barrier per column:
+    // in step j warp 0 applies reflector j to column j + 1 and at once forms
+    // reflector j + 1 from it, while the other warps apply reflector j to
+    // columns j + 2.. of the panel (a one-column look-ahead).
+    auto reflector = [&](int j) {  // warp-wide; column j is final below row j - 1
+      double sn = 0.0;
+      for (int i = j + lane; i < rb; i += 32) sn += abs2d(Lb[i + j * P]);
+      sn = warp_sum(sn);
+      if (lane == 0) {
+        double b;
+        S vj, rjj;
+        make_reflector<S>(sn, Lb[j + j * P], b, vj, rjj);
+        beta_s[j] = b;
+        vdiag[j] = vj;
+        rdiag[j] = rjj;
       }
-      __syncthreads();
+    };
+    if (warp == 0) reflector(J);
+    __syncthreads();
+    for (int j = J; j < J + jb; ++j) {
       const double b = beta_s[j];
-      if (b != 0.0) {
-        for (int c = j + 1 + warp; c < J + jb; c += NW) {
+      for (int c = j + 1 + warp; c < J + jb; c += NW) {
+        if (b != 0.0) {
           S d = zero<S>();
           for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
           d = scale(warp_sum(d), b);
           for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
+        }
+        if (c == j + 1) {  // warp 0 only (c - j - 1 = warp)
+          __syncwarp();
+          reflector(c);
         }
       }
       __syncthreads();

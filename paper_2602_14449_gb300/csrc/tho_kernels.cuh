@@ -226,28 +226,35 @@ __global__ void __launch_bounds__(kV1Threads) k_v1qr(const Inst* insts, const Io
     X[e] = V[i + (int64_t)j * io.ldv];
   }
   __syncthreads();
-  for (int j = 0; j < k0; ++j) {
-    if (warp == 0) {
-      double s = 0.0;
-      for (int i = j + lane; i < k0; i += 32) s += abs2d(X[i + j * k0]);
-      s = warp_sum(s);
-      if (lane == 0) {
-        double b;
-        S vj, rjj;
-        make_reflector<S>(s, X[j + j * k0], b, vj, rjj);
-        beta_s[j] = b;
-        vdiag[j] = vj;
-        rdiag[j] = rjj;
-      }
+  // One barrier per column: in step j warp 0 first applies reflector j to
+  // column j + 1 and forms reflector j + 1 from it, then its other columns.
+  auto reflector = [&](int j) {  // warp-wide; column j is final below row j - 1
+    double s = 0.0;
+    for (int i = j + lane; i < k0; i += 32) s += abs2d(X[i + j * k0]);
+    s = warp_sum(s);
+    if (lane == 0) {
+      double b;
+      S vj, rjj;
+      make_reflector<S>(s, X[j + j * k0], b, vj, rjj);
+      beta_s[j] = b;
+      vdiag[j] = vj;
+      rdiag[j] = rjj;
     }
-    __syncthreads();
+  };
+  if (warp == 0) reflector(0);
+  __syncthreads();
+  for (int j = 0; j < k0; ++j) {
     const double b = beta_s[j];
-    if (b != 0.0) {
-      for (int c = j + 1 + warp; c < k0; c += nw) {
+    for (int c = j + 1 + warp; c < k0; c += nw) {
+      if (b != 0.0) {
         S d = zero<S>();
         for (int i = j + lane; i < k0; i += 32) d = cmadd(d, i == j ? vdiag[j] : X[i + j * k0], X[i + c * k0]);
         d = scale(warp_sum(d), b);
         for (int i = j + lane; i < k0; i += 32) X[i + c * k0] = msub(X[i + c * k0], i == j ? vdiag[j] : X[i + j * k0], d);
+      }
+      if (c == j + 1) {  // warp 0's first column
+        __syncwarp();
+        reflector(c);
       }
     }
     __syncthreads();
@@ -451,28 +458,36 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
   };
   for (int J = 0; J < k; J += kNB) {
     const int jb = min(kNB, k - J);
-    for (int j = J; j < J + jb; ++j) {
-      if (warp == 0) {
-        double sn = 0.0;
-        for (int i = j + lane; i < rb; i += 32) sn += abs2d(Lb[i + j * P]);
-        sn = warp_sum(sn);
-        if (lane == 0) {
-          double b;
-          S vj, rjj;
-          make_reflector<S>(sn, cvt<S, B>(Lb[j + j * P]), b, vj, rjj);
-          beta_s[j] = b;
-          vdiag[j] = cvt<B, S>(vj);
-          rdiag[j] = rjj;
-        }
+    // Column by column with one barrier per column: in step j warp 0 applies
+    // reflector j to column j + 1 and at once forms reflector j + 1 from it,
+    // while the other warps apply reflector j to columns j + 2.. of the block.
+    auto reflector = [&](int j) {  // warp-wide; column j is final below row j - 1
+      double sn = 0.0;
+      for (int i = j + lane; i < rb; i += 32) sn += abs2d(Lb[i + j * P]);
+      sn = warp_sum(sn);
+      if (lane == 0) {
+        double b;
+        S vj, rjj;
+        make_reflector<S>(sn, cvt<S, B>(Lb[j + j * P]), b, vj, rjj);
+        beta_s[j] = b;
+        vdiag[j] = cvt<B, S>(vj);
+        rdiag[j] = rjj;
       }
-      __syncthreads();
+    };
+    if (warp == 0) reflector(J);
+    __syncthreads();
+    for (int j = J; j < J + jb; ++j) {
       const double b = beta_s[j];
-      if (b != 0.0) {
-        for (int c = j + 1 + warp; c < J + jb; c += nw) {
+      for (int c = j + 1 + warp; c < J + jb; c += nw) {
+        if (b != 0.0) {
           B d = zero<B>();
           for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
           d = scale(warp_sum(d), b);
           for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
+        }
+        if (c == j + 1) {  // warp 0 only (c - j - 1 = warp)
+          __syncwarp();
+          reflector(c);
         }
       }
       __syncthreads();

@@ -184,6 +184,7 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
     free_plan(p);
     return THO_ERR_CUDA;
   }
+  pc.sms = sms;
   for (int i = 0; i < count; ++i) {
     pc.kmax = std::max<int>(pc.kmax, (int)descs[i].k);
     pc.k0max = std::max<int>(pc.k0max, (int)descs[i].k0);

@@ -147,6 +147,7 @@ cudaError_t configure_impl(PlanCore& pc) {
   pc.smem_leaf_emu = leaf_emu_smem(pc.P, pc.kpmax, sizeof(S));
   if (EMU && (e = raise((const void*)k_leaf_emu<S>, pc.smem_leaf_emu)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_down_w<S>, pc.smem_tree)) != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
   int n = 0;
   if (pc.any_k0) n += 3;  // v1qr, gram, solve_z
@@ -216,7 +217,10 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   hk(kPhTreeDown, 0, st);
   for (int l = pc.Lmax; l >= 1; --l)
     if (pc.tab.lev_n[l] > 0)
-      k_tree_down<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+      if (pc.tab.lev_n[l] >= kTreeDownWide * pc.sms)
+        k_tree_down_w<S><<<pc.tab.lev_n[l], 32, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+      else
+        k_tree_down<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   hk(kPhTreeDown, 1, st);
   hk(kPhApply, 0, st);
   if (EMU)  // Qbar_b = Q_leaf,b F_b on tensor cores

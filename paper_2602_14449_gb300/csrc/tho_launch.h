@@ -48,6 +48,7 @@ struct PlanCore {
   size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
   int upd_mt = 4;    // emulated update: 16-row tiles per warp column (max over problems)
   int apply_mt = 4;  // emulated apply: the same bound, lowered until its stage fits
+  int sms = 0;       // SMs of the plan's device
   size_t smem_apply_emu = 0;
   size_t smem_gram_pipe = 0, smem_gram_umma = 0;
   bool gram_umma = false;  // emulated Gram on tcgen05 (when its stages fit)

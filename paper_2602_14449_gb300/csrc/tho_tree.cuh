@@ -234,4 +234,91 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, c
   }
 }
 
+// a7 (tree, downward), the same product with one warp per node: lane c holds
+// column c of the bottom block (all k rows) in registers and the reflectors
+// are read from shared memory by broadcast.  Every lane works at every step
+// and no reduction is needed: about 30 % fewer FP64 instructions per node
+// than the four-row-group form, which keeps four warps per node and so the
+// levels with few nodes short.  Used for the levels with many nodes.
+constexpr int kTreeDownWide = 8;  // use this form at levels of >= 8 nodes per SM
+
+// Volatile shared-memory load: neither merged with an earlier load nor moved
+// ahead of the others, so the update loop re-reads the reflector entry by
+// entry instead of holding all of it in registers next to the column.
+__device__ __forceinline__ double lds_fresh(const double* p) {
+  double v;
+  asm volatile("ld.volatile.shared.f64 %0, [%1];" : "=d"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+__device__ __forceinline__ z64 lds_fresh(const z64* p) {
+  z64 v;
+  asm volatile("ld.volatile.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+
+// Step j of the downward product for one column (J = j, compile-time, so that
+// every index into the register array is static); recurses to step J - 1.
+template <class S, int J>
+__device__ __forceinline__ void tree_down_step(S (&eb)[kMaxKP], S et, const S* Rf, const S* Fi, S* Fa, int k,
+                                               int c) {
+  if constexpr (J >= 0) {
+    if (J < k) {
+      const int kk = k * k;
+      const S et_next = J > 0 ? Fi[(J - 1) + c * k] : zero<S>();
+      const double b = real_(Rf[kk + k + J]);
+      if (b != 0.0) {
+        const S vt = Rf[kk + J];
+        const S* u = Rf + J * k;
+        S d0 = cmadd(zero<S>(), vt, et), d1 = zero<S>();  // two chains
+#pragma unroll
+        for (int r = 0; r <= J; ++r) {
+          if (r & 1) d1 = cmadd(d1, u[r], eb[r]);
+          else d0 = cmadd(d0, u[r], eb[r]);
+        }
+        const S d = scale(add(d0, d1), b);
+        et = msub(et, vt, d);
+#pragma unroll
+        for (int r = 0; r <= J; ++r) eb[r] = msub(eb[r], lds_fresh(u + r), d);
+      }
+      Fa[J + c * k] = et;
+      et = et_next;
+    }
+    tree_down_step<S, J - 1>(eb, et, Rf, Fi, Fa, k, c);
+  }
+}
+
+template <class S>
+__global__ void __launch_bounds__(32) k_tree_down_w(const Inst* insts, const WorkItem* items, void* ws, int lev) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
+  const int k = (int)I.k, kk = k * k;
+  const int i = it.idx;
+  const int64_t node = I.lev_off[lev] + i;
+  const int64_t c0 = I.lev_off[lev - 1] + 2 * (int64_t)i;
+  const bool two = (2 * i + 1) < I.lev_cnt[lev - 1];
+  S* F = wsp<S>(ws, I.oF);
+  const S* Fi = F + node * kk;
+  if (!two) {
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) F[c0 * kk + e] = Fi[e];
+    return;
+  }
+  S* Rf = reinterpret_cast<S*>(smem_raw);  // k x k bottom parts | k tops | k betas
+  const S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
+  for (int e = threadIdx.x; e < kk + 2 * k; e += blockDim.x) Rf[e] = ref[e];
+  __syncwarp();
+  const int c = threadIdx.x;
+  if (c >= k) return;
+  S* Fa = F + c0 * kk;
+  S* Fb = Fa + kk;
+  S eb[kMaxKP];
+#pragma unroll
+  for (int r = 0; r < kMaxKP; ++r) eb[r] = zero<S>();
+  // The first step run is j = k - 1: its top entry is read here for every k.
+  tree_down_step<S, kMaxKP - 1>(eb, Fi[(k - 1) + c * k], Rf, Fi, Fa, k, c);
+#pragma unroll
+  for (int r = 0; r < kMaxKP; ++r)
+    if (r < k) Fb[r + c * k] = eb[r];
+}
+
 }  // namespace tho

@@ -74,14 +74,16 @@ REF_STEP_ROWS = {"c3": 16384, "c3-native": 16384, "c3-fp32": 16384, "c2": 32768,
 #   (2 k^2) and explicit leaf Q (2 k^2); apply: Q_leaf F (2 k^2) and V_2^* Qbar
 #   (2 k0 k); update_q: V_2 Z2 (2 k0 k).
 # With the products on tensor cores (precision 2) the leaf kernel keeps only
-# the QR and the explicit leaf Q in FP64 (4 k^2); A' moves to update_a.
+# the Householder QR of its leaves (compact WY form, no explicit leaf Q): over
+# nb leaves of the m trailing rows, 2 m k^2 - nb (2/3) k^3 flops (real count;
+# x4 complex); A' moves to update_a.
 PHASE_FLOPS_PER_ROW = {
     "gram": lambda k0, k: 2 * k0 * k,
     "leaf": lambda k0, k: 2 * k0 * k + 4 * k * k,
     "apply": lambda k0, k: 2 * k * k + 2 * k0 * k,
     "update_q": lambda k0, k: 2 * k0 * k,
 }
-LEAF_QR_FLOPS_PER_ROW = lambda k0, k: 4 * k * k
+LEAF_WY_QR_FLOPS = lambda m, k, nb: 2 * m * k * k - nb * (2.0 / 3.0) * k ** 3
 # bf16 tensor-core flops per trailing row of one emulated rank-k0 update (36
 # slice pairs of a real-embedded (rows x 2k0) times (2k0 x 2k) product; real: k0, k).
 EMU_UPDATE_MMA_FLOPS_PER_ROW = lambda k0, k, cplx: 2 * 36 * (2 * k0 if cplx else k0) * (2 * k if cplx else k)
@@ -202,10 +204,12 @@ _KERNEL_FILES = {
     "k_gram_emu": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh"),
     "k_update_emu": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh"),
     "k_apply_emu": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh"),
+    "k_leaf_emu": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh"),
     "k_gram_umma": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh", "tho_umma.cuh"),
     "k_update_umma": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_emu.cuh", "tho_umma.cuh"),
     "k_tree_up": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_tree.cuh"),
     "k_tree_down": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_tree.cuh"),
+    "k_tree_down_w": ("tho_scalar.cuh", "tho_plan.h", "tho_kernels.cuh", "tho_tree.cuh"),
 }
 
 
@@ -548,12 +552,15 @@ def run_gpu(args):
     m = n - k0
     kernel_of = {"gram": "k_gram", "leaf": "k_leaf", "apply": "k_apply_gram", "update_q": "k_update_q"}
     if prec == 2:
-        dom, flops_row = "leaf", LEAF_QR_FLOPS_PER_ROW(k0, k)
+        # Complex panels of k >= 24 take the leaf kernel with tensor-core trailing updates.
+        kernel_of["leaf"] = "k_leaf_emu" if (cplx and k >= 24) else "k_leaf"
+        dom = "leaf"
+        nb = -(-m // plan.leaf_rows)
+        flops_launch = LEAF_WY_QR_FLOPS(m, k, nb) * (4 if cplx else 1)
     else:
         dom = max(PHASE_FLOPS_PER_ROW, key=lambda ph: phases[ph][0])
-        flops_row = PHASE_FLOPS_PER_ROW[dom](k0, k)
+        flops_launch = PHASE_FLOPS_PER_ROW[dom](k0, k) * m * (4 if cplx else 1)
     dom_ms, dom_groups = phases[dom]
-    flops_launch = flops_row * m * (4 if cplx else 1)
     achieved = flops_launch / (dom_ms / dom_groups * 1e-3) / 1e12
     peak = FP32_PEAK_TFLOPS if prec == 1 else FP64_PEAK_TFLOPS
     tr_row = _traffic_for(kernel_of[dom] + ("@emu" if prec == 2 else ""))

@@ -110,6 +110,11 @@ size_t tho_plan_workspace_bytes(tho_plan_t plan);
 /* Number of kernel launches one tho_orth / tho_orth_batched call issues. */
 int32_t tho_plan_kernel_launches(tho_plan_t plan);
 
+/* Leaf height P of the plan's TSQR (Section 3.2: the Householder QR of the
+ * trailing block A'_2 is computed over row blocks of at most P rows, each
+ * leaf having between P/2 and P rows); 0 for NULL. */
+int32_t tho_plan_leaf_rows(tho_plan_t plan);
+
 /* Algorithm 1 (Section 3.1) with P = -Q_1 from the QR of V_{1:k0,:}
  * (Section 3.2, second choice), for a plan with count = 1.
  *   V  n x k0, ldv >= n (may be NULL when k0 = 0)

@@ -361,6 +361,7 @@ size_t tho_plan_workspace_bytes(tho_plan_t plan) {
 }
 
 int32_t tho_plan_kernel_launches(tho_plan_t plan) { return plan ? plan->pc.launches : 0; }
+int32_t tho_plan_leaf_rows(tho_plan_t plan) { return plan ? plan->pc.P : 0; }
 
 tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A, int64_t lda, void* Q,
                       int64_t ldq, void* R, void* S, void* stream) {

@@ -130,8 +130,7 @@ __device__ __forceinline__ void emu_split2(double x0, double x1, int emax0, int 
 // (hi 2^28 + lo) 2^(sc - 63) for the two exact int64 accumulators of a fold,
 // correctly rounded to nearest even with integer instructions only: the exact
 // 128-bit sum, its leading-zero count, the top 53 bits with round and sticky
-// bits, and the exponent placed in the bit pattern.  Outside the normal
-// exponent range it falls back to the FP64 scaling.
+// bits, and the exponent placed in the bit pattern.
 __device__ __forceinline__ double emu_fx(long long hi, long long lo, int sc) {
   unsigned long long xl = (unsigned long long)hi << 28;
   unsigned long long xh = (unsigned long long)(hi >> 36);
@@ -167,7 +166,10 @@ __device__ __forceinline__ double emu_fx(long long hi, long long lo, int sc) {
     }
   }
   const int E = t + (sc - 63) + 1023;
-  if (E <= 0 || E >= 2047) return emu_fx((long long)hi, (long long)lo, sc);
+  // Outside the normal range: infinity, or the subnormal mant 2^(E - 1075)
+  // (ldexp rounds the 53-bit mantissa once more).
+  if (E >= 2047) return __longlong_as_double((long long)(((unsigned long long)(neg ? 1 : 0) << 63) | 0x7ff0000000000000ull));
+  if (E <= 0) return ldexp(neg ? -(double)mant : (double)mant, E - 1075);
   return __longlong_as_double((long long)(((unsigned long long)(neg ? 1 : 0) << 63) |
                                           ((unsigned long long)E << 52) | (mant & 0xfffffffffffffull)));
 }
@@ -819,7 +821,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
 // + (strictly upper part of G), which holds for the forward product of the
 // reflectors (Puglisi); then the product above with F_b replaced by -M and
 // [F_b; 0] added in the epilogue.
-// Extra shared memory with wy: Gs (G), Ts (the betas), Ms [k][k+1] S after Fr.
+// Extra shared memory with wy: Gs (G'), Ts (betas, row scales of K), Ms [k][k+1] S after Fr.
 template <class S, int MTM>
 __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
                                                               const WorkItem* items, void* ws, int P, int wy) {
@@ -880,26 +882,20 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
     }
     __syncthreads();
     if (wy) {
-      // (1) G = Y^* Y over the leaf's rows, 64 real steps per chunk; Vs holds
-      // the slices of Y^T (rows = columns of Y), serving as both operands.
-      // The first chunk (rows < 64 / RPE >= k) also gives B = Y_1^* F_b on
-      // the same tiles, with the slices of F_b^T in Zs (free until the main
-      // product) and F_b's column scales in eZ.
+      // (1) G' = (Y^* Y) diag(beta) over the leaf's rows, 64 real steps per
+      // chunk; Vs holds the slices of Y^T (rows = columns of Y), serving as
+      // both operands.  Only the strictly upper part is used: tiles wholly
+      // below the diagonal are skipped.
       const int kr = (k + 15) / 16 * 16;
-      double* bs = reinterpret_cast<double*>(Ts);  // the leaf's betas
+      double* bs = reinterpret_cast<double*>(Ts);     // the leaf's betas
+      int* eK = reinterpret_cast<int*>(bs + k);       // row scales of K (Ts holds >= 12 k bytes)
       const S* btg = wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
       for (int i = threadIdx.x; i < k; i += kEmuThreads) bs[i] = real_(btg[i]);
-      for (int j = warp; j < k; j += NW) {
-        int m = 0;
-        for (int q = lane; q < k * RPE; q += 32)
-          m = max(m, dexp(reinterpret_cast<const double*>(Fr + (q / RPE) + j * ldf)[q % RPE]));
-        m = __reduce_max_sync(0xffffffffu, m);
-        if (lane == 0) eZ[j] = m;
-      }
       const bool gmine = warp < (kr / 16) * NT;
       const int gmt = gmine ? warp / NT : 0, gnt = gmine ? warp % NT : 0;
       const bool gimag = C && gnt * 8 >= kpe;
       const int gjb0 = gimag ? gnt * 8 - kpe : gnt * 8;
+      const bool gupper = gmine && gmt * 16 < gjb0 + 8;
       float acc[kEmuLevels][4];
       long long ghi[4] = {0, 0, 0, 0}, glo[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -923,60 +919,8 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * kr + l) * kEmuLd + q) = w[p];
         }
-        if (chunk == 0) {
-          for (int e2 = threadIdx.x; e2 < kpe * (kEmuKT / 2); e2 += kEmuThreads) {
-            const int j = e2 / (kEmuKT / 2), q = 2 * (e2 % (kEmuKT / 2));
-            double x0 = 0.0, x1 = 0.0;
-            if (j < k) {
-              if (q < k * RPE) x0 = reinterpret_cast<const double*>(Fr + (q / RPE) + j * ldf)[q % RPE];
-              if (q + 1 < k * RPE) x1 = reinterpret_cast<const double*>(Fr + ((q + 1) / RPE) + j * ldf)[(q + 1) % RPE];
-            }
-            const int em = j < k ? eZ[j] : 0;
-            unsigned w[kEmuSlices];
-            emu_split2(x0, x1, em, em, w);
-#pragma unroll
-            for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Zs + (p * kpe + j) * kEmuLd + q) = w[p];
-          }
-        }
         __syncthreads();
-        if (gmine && chunk == 0) {
-          // B = Y_1^* F_b (acc is still zero here; the fold clears it again).
-          const int kzf = (k * RPE + 15) / 16 * 16;
-          for (int ks = 0; ks < kzf; ks += 16) {
-            unsigned bf[kEmuSlices][2];
-#pragma unroll
-            for (int qq = 0; qq < kEmuSlices; qq += 2)
-              ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, gjb0, ks, bf[qq], bf[qq + 1]);
-            if (gimag) {
-#pragma unroll
-              for (int qq = 0; qq < kEmuSlices; ++qq) {
-                bf[qq][0] = im_pair(bf[qq][0]);
-                bf[qq][1] = im_pair(bf[qq][1]);
-              }
-            }
-#pragma unroll
-            for (int p = 0; p < kEmuSlices; ++p) {
-              unsigned a[4];
-              ld_afrag(Vs + (p * kr) * kEmuLd, gmt * 16, ks, a);
-#pragma unroll
-              for (int qq = 0; qq < kEmuSlices; ++qq) {
-                if (p + qq > kEmuLevels - 1) continue;
-                mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
-              }
-            }
-          }
-          long long bhi[4] = {0, 0, 0, 0}, blo[4] = {0, 0, 0, 0};
-          emu_fold(acc, bhi, blo);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int l = gmt * 16 + g + (e >= 2 ? 8 : 0);
-            const int j = gjb0 + 2 * t4 + (e & 1);
-            if (l >= k || j >= k) continue;
-            const double v = emu_fx((long long)bhi[e], (long long)blo[e], eV[l] + eZ[j] - 2044);
-            reinterpret_cast<double*>(Ms + l + j * ldf)[gimag ? 1 : 0] = v;
-          }
-        }
-        if (gmine) {
+        if (gupper) {
           for (int ks = 0; ks < kEmuKT; ks += 16) {
             unsigned bf[kEmuSlices][2];
 #pragma unroll
@@ -1003,37 +947,122 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
           if (chunk & 1) emu_fold(acc, ghi, glo);  // exact for 128 steps
         }
       }
-      if (gmine) {
+      if (gupper) {
         emu_fold(acc, ghi, glo);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int i = gmt * 16 + g + (e >= 2 ? 8 : 0);
           const int j = gjb0 + 2 * t4 + (e & 1);
-          if (i >= k || j >= k) continue;
+          if (i >= j || j >= k) continue;
           const int sc = eV[i] + eV[j] - 2044;
           const double v = emu_fx((long long)ghi[e], (long long)glo[e], sc);
           reinterpret_cast<double*>(Gs + i + j * k)[gimag ? 1 : 0] = v * bs[j];  // G(i, j) beta_j
         }
       }
+      // (2) K = T Y_1^* (upper triangular: T and Y_1^* are).  With T^-1 =
+      // diag(1/beta) + (strictly upper part of G) (forward accumulation of the
+      // reflectors; valid for beta_i = 0 too) and K = diag(beta) U, G' as above:
+      //   U(i) = Y_1^*(i) - sum_{l > i} G'(i, l) U(l),
+      // right-looking: after step i + 1 row i is final and step i removes it
+      // from the rows above, in the columns j >= i where it is nonzero.
+      for (int e = threadIdx.x; e < kk; e += kEmuThreads) {
+        const int l = e % k, j = e / k;
+        Ms[l + j * ldf] = j >= l ? conj_(Qr[j * ldr + l]) : zero<S>();  // Y_1^*(l, j) = conj(Y(j, l))
+      }
+      for (int j = warp; j < k; j += NW) {  // column scales of F_b
+        int m = 0;
+        for (int q = lane; q < k * RPE; q += 32)
+          m = max(m, dexp(reinterpret_cast<const double*>(Fr + (q / RPE) + j * ldf)[q % RPE]));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) eZ[j] = m;
+      }
       __syncthreads();
-      // (2) B = Y_1^* F_b is in Ms (first chunk above).
-      // (3) M = T B without forming T: T^-1 = diag(1/beta) + (strictly upper part
-      // of G), so M solves that upper triangular system.  With M = diag(beta) U
-      // and G' = G diag(beta) (scaled above), U(i) = B(i) - sum_{l > i} G'(i, l) U(l):
-      // right-looking back substitution, row i final after step i + 1, one
-      // rank-1 update and one barrier per step; the betas are applied when
-      // the second operand is sliced.  Valid for beta_i = 0 too.
       for (int i = k - 1; i >= 1; --i) {
-        for (int e = threadIdx.x; e < i * k; e += kEmuThreads) {
-          const int l = e / k, j = e % k;
+        const int w = k - i;
+        for (int e = threadIdx.x; e < i * w; e += kEmuThreads) {
+          const int l = e / w, j = i + e % w;
           Ms[l + j * ldf] = msub(Ms[l + j * ldf], Gs[l + i * k], Ms[i + j * ldf]);
         }
         __syncthreads();
       }
+      // (3) M = K F_b on tensor cores, contraction over K's columns (one
+      // chunk: RPE k <= 64 steps).  The emulated product forms A^* B, so A
+      // holds conj(K) = conj(diag(beta) U) (row scales eK), B = F_b^T (eZ).
+      for (int l = warp; l < k; l += NW) {  // over the values sliced below
+        int m = 0;
+        for (int q = lane; q < k * RPE; q += 32)
+          m = max(m, dexp(reinterpret_cast<const double*>(Ms + l + (q / RPE) * ldf)[q % RPE] * bs[l]));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) eK[l] = m;
+      }
+      __syncthreads();
+      for (int e2 = threadIdx.x; e2 < (kr + kpe) * (kEmuKT / 2); e2 += kEmuThreads) {
+        const bool isA = e2 < kr * (kEmuKT / 2);
+        const int f = isA ? e2 : e2 - kr * (kEmuKT / 2);
+        const int row = f / (kEmuKT / 2), q = 2 * (f % (kEmuKT / 2));
+        double x0 = 0.0, x1 = 0.0;
+        if (row < k) {
+          auto part = [&](int qq) -> double {
+            if (qq >= k * RPE) return 0.0;
+            const int r = qq / RPE;
+            if (isA) {
+              const double v = reinterpret_cast<const double*>(Ms + row + r * ldf)[qq % RPE] * bs[row];
+              return (qq % RPE) ? -v : v;  // conj(K)
+            }
+            return reinterpret_cast<const double*>(Fr + r + row * ldf)[qq % RPE];
+          };
+          x0 = part(q);
+          x1 = part(q + 1);
+        }
+        const int em = row < k ? (isA ? eK[row] : eZ[row]) : 0;
+        unsigned w[kEmuSlices];
+        emu_split2(x0, x1, em, em, w);
+        unsigned short* dst = isA ? Vs + (row * kEmuLd + q) : Zs + (row * kEmuLd + q);
+        const int pst = (isA ? kr : kpe) * kEmuLd;
+#pragma unroll
+        for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(dst + p * pst) = w[p];
+      }
+      __syncthreads();
+      if (gmine) {
+        const int kzf = (k * RPE + 15) / 16 * 16;
+        for (int ks = 0; ks < kzf; ks += 16) {
+          unsigned bf[kEmuSlices][2];
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; qq += 2)
+            ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, gjb0, ks, bf[qq], bf[qq + 1]);
+          if (gimag) {
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              bf[qq][0] = im_pair(bf[qq][0]);
+              bf[qq][1] = im_pair(bf[qq][1]);
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) {
+            unsigned a[4];
+            ld_afrag(Vs + (p * kr) * kEmuLd, gmt * 16, ks, a);
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              if (p + qq > kEmuLevels - 1) continue;
+              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+            }
+          }
+        }
+        long long bhi[4] = {0, 0, 0, 0}, blo[4] = {0, 0, 0, 0};
+        emu_fold(acc, bhi, blo);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int l = gmt * 16 + g + (e >= 2 ? 8 : 0);
+          const int j = gjb0 + 2 * t4 + (e & 1);
+          if (l >= k || j >= k) continue;
+          const double v = emu_fx((long long)bhi[e], (long long)blo[e], eK[l] + eZ[j] - 2044);
+          reinterpret_cast<double*>(Ms + l + j * ldf)[gimag ? 1 : 0] = v;
+        }
+      }
+      __syncthreads();
     }
-    // Second operand: F_b, or -M = -diag(beta) U with the compact WY form.
+    // Second operand: F_b, or -M with the compact WY form.
     const S* Zsrc = wy ? Ms : Fr;
-    const double* bsc = reinterpret_cast<const double*>(Ts);
     const double zsg = wy ? -1.0 : 1.0;
     auto fp = [&](int q, int j) -> double {
       if (q >= kz || j >= k) return 0.0;
@@ -1045,7 +1074,6 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       } else {
         b = reinterpret_cast<const double*>(Zsrc)[i + j * ldf];
       }
-      if (wy) b *= bsc[i];
       return scale2(zsg * b, eV[i] - 1078);
     };
     for (int j = warp; j < kpe; j += NW) {

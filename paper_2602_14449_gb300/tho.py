@@ -28,6 +28,7 @@ THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE = 0x1, 0x2
 THO_MAX_K0, THO_MAX_K = 128, 32
 
 EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",
+            "tho_plan_leaf_rows",
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
             "tho_orth_noalloc")
@@ -75,6 +76,8 @@ def load(path: str | None = None):
         lib.tho_plan_workspace_bytes.restype = ctypes.c_size_t
         lib.tho_plan_kernel_launches.argtypes = [vp]
         lib.tho_plan_kernel_launches.restype = ctypes.c_int32
+        lib.tho_plan_leaf_rows.argtypes = [vp]
+        lib.tho_plan_leaf_rows.restype = ctypes.c_int32
         lib.tho_orth.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp, vp]
         lib.tho_orth.restype = ctypes.c_int
         lib.tho_orth_batched.argtypes = [vp, ctypes.POINTER(Instance), i32, vp]
@@ -157,6 +160,10 @@ class Plan:
     @property
     def kernel_launches(self) -> int:
         return load().tho_plan_kernel_launches(self.handle)
+
+    @property
+    def leaf_rows(self) -> int:
+        return load().tho_plan_leaf_rows(self.handle)
 
     def status(self) -> int:
         return load().tho_plan_status(self.handle)

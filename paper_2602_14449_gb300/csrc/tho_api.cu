@@ -192,6 +192,9 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   }
   pc.kpmax = (int)round_up(pc.kmax, tho::kBJ);
   pc.k0pmax = (int)round_up(pc.k0max, tho::kBI);
+  // Complex emulated plans with k >= 24 factor their leaves with tensor-core
+  // trailing updates (k_leaf_emu), which also writes G' for the apply.
+  pc.leaf_tc = pc.prec == THO_PREC_FP64_EMU && cplx && pc.kmax >= 24;
   // Leaf height: the largest of 256/128/64 rows whose panel fits in shared memory.
   pc.P = 0;
   // Emulated mode forms A' outside the leaf kernel: no Z / V staging there.
@@ -278,6 +281,7 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
     I.oRef = take((nodes - I.nb) * (kk + 2 * k));
     I.oF = take(nodes * kk);
     I.oBeta = take(pc.prec == THO_PREC_FP64_EMU ? (int64_t)I.nb * k : 1);
+    I.oGw = take(pc.leaf_tc ? (int64_t)I.nb * kk : 1);
   }
   pc.ws_elems = (size_t)off;
 

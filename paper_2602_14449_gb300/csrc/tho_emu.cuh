@@ -812,15 +812,16 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
 // The contraction (k columns, real-embedded) is at most 64 steps: one fold.
 // Shared: Qr [P][k+1] S | Fr [k][k] S | Zs [8][kpe][kEmuLd] | Vs [8][max(TM, k16)][kEmuLd] bf16 | eV | eZ.
 //
-// wy != 0: Q's rows hold the leaf's Householder vectors Y (v_j on the diagonal,
-// zero above) and the workspace its betas, instead of the explicit leaf Q.
-// With T the upper triangular factor of H_0 ... H_{k-1} = I - Y T Y^*,
-//   Qbar_b = [F_b; 0] - Y (T (Y_1^* F_b)),   Y_1 = rows 0..k-1 of Y,
-// formed per leaf as: G = Y^* Y on tensor cores (scales of Y's columns);
-// B = Y_1^* F_b (FP64); M = T B by back substitution with T^-1 = diag(1/beta)
-// + (strictly upper part of G), which holds for the forward product of the
-// reflectors (Puglisi); then the product above with F_b replaced by -M and
-// [F_b; 0] added in the epilogue.
+// wy != 0 (bit 0): Q's rows hold the leaf's Householder vectors Y (v_j on the
+// diagonal, zero above) and the workspace its betas, instead of the explicit
+// leaf Q.  With T the upper triangular factor of H_0 ... H_{k-1} = I - Y T Y^*,
+//   Qbar_b = [F_b; 0] - Y (K F_b),   K = T Y_1^*,   Y_1 = rows 0..k-1 of Y,
+// formed per leaf as: G' = (Y^* Y) diag(beta) on tensor cores, or read from
+// the workspace when the leaf kernel wrote it (bit 1); K by back substitution
+// with T^-1 = diag(1/beta) + (strictly upper part of Y^* Y), which holds for
+// the forward product of the reflectors (Puglisi); M = K F_b on tensor cores;
+// then the product above with F_b replaced by -M and [F_b; 0] added in the
+// epilogue.
 // Extra shared memory with wy: Gs (G'), Ts (betas, row scales of K), Ms [k][k+1] S after Fr.
 template <class S, int MTM>
 __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
@@ -832,6 +833,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
   const Io io = get_io(iot, io0, it.inst);
+  const bool gpre = (wy & 2) != 0;  // G' = (Y^* Y) diag(beta) written by the leaf kernel
   const int k = (int)I.k, kk = k * k, ldr = k + 1;
   const int kpe = (k + 7) / 8 * 8;
   const int NT = (C ? 2 * kpe : kpe) / 8;
@@ -902,7 +904,12 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       for (int e = 0; e < 4; ++e)
 #pragma unroll
         for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
-      const int nq = rb * RPE;
+      const int nq = gpre ? 0 : rb * RPE;  // G' from the leaf kernel: no Gram here
+      if (gpre) {
+        const S* gw = wsp<S>(ws, I.oGw) + (int64_t)lb * kk;
+        for (int e = threadIdx.x; e < kk; e += kEmuThreads)
+          if (e % k < e / k) Gs[e] = gw[e];
+      }
       int chunk = 0;
       for (int q0 = 0; q0 < nq; q0 += kEmuKT, ++chunk) {
         __syncthreads();  // the previous chunk's MMAs are done with Vs
@@ -947,7 +954,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
           if (chunk & 1) emu_fold(acc, ghi, glo);  // exact for 128 steps
         }
       }
-      if (gupper) {
+      if (gupper && !gpre) {
         emu_fold(acc, ghi, glo);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -1180,6 +1187,8 @@ __host__ __device__ inline size_t leaf_emu_smem(int P, int kp, size_t elem) {
 template <class S>
 __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, const Io* iot, Io io0,
                                                          const WorkItem* items, void* ws, int P, int from_q) {
+  // Besides R, Y and the betas, the leaf writes G' = (Y^* Y) diag(beta) (its
+  // strictly upper part) for the apply, from the same tensor-core products.
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
   constexpr int NW = kThreads / 32;
@@ -1249,31 +1258,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
       }
       __syncthreads();
     }
-    const int c0 = J + jb, nc = k - c0;
-    if (nc <= 0) break;
-    // Column scales over the panel's rows J..rb-1: Y_J's columns and C's columns.
-    for (int col = warp; col < jb + nc; col += NW) {
+    const int c0 = J + jb, nc = max(0, k - c0);
+    int* eP = eZ;  // scales of the earlier panels' columns (eZ is free until the C product)
+    // Column scales over the panel's rows J..rb-1: Y_J's columns, C's columns
+    // and the earlier panels' columns (their rows from J down).
+    for (int col = warp; col < jb + nc + J; col += NW) {
       int m = 0;
       for (int r = J + lane; r < rb; r += 32) {
-        const S v = col < jb ? Yv(r, J + col) : Lb[r + (c0 + col - jb) * P];
+        const S v = col < jb ? Yv(r, J + col) : (col < jb + nc ? Lb[r + (c0 + col - jb) * P] : Lb[r + (col - jb - nc) * P]);
         m = max(m, dexp(real_(v)));
         if constexpr (C) m = max(m, dexp(v.y));
       }
       m = __reduce_max_sync(0xffffffffu, m);
       if (lane == 0) {
         if (col < jb) eY[col] = m;
-        else eC[col - jb] = m;
+        else if (col < jb + nc) eC[col - jb] = m;
+        else eP[col - jb - nc] = m;
       }
     }
     __syncthreads();
     const int kpc = (nc + 7) / 8 * 8;
     const int NT = (C ? 2 : 1) * kpc / 8;
-    // ---- [W | G] = Y_J^* [C | Y_J] on tensor cores: B rows 0..kpc-1 are C's
-    // columns, rows kpc..kpc+7 the panel's own columns, so the panel's Gram
-    // G = Y_J^* Y_J comes out of the same product (the FP64 alternative is one
-    // warp dot product per pair of columns).
+    // ---- [W | G_JJ | G_<J] = Y_J^* [C | Y_J | Y_<J] on tensor cores: B rows
+    // 0..kpc-1 are C's columns, rows kpc..kpc+7 the panel's own columns (the
+    // panel Gram that defines T_J, without FP64 dot products) and rows
+    // kpc+8.. the earlier panels' columns (the blocks of the leaf's Gram above
+    // this panel; Y_J is zero above row J, so rows J.. suffice).  kpb <= 32.
     {
-      const int kpb = kpc + kNB, NTB = (C ? 2 : 1) * kpb / 8;
+      const int kpb = kpc + kNB + J, NTB = (C ? 2 : 1) * kpb / 8;
       unsigned short* Aw = Us;                           // [8][16][kLeLdW]
       unsigned short* Bw = Us + kEmuSlices * 16 * kLeLdW;  // [8][kpb][kLeLdW]
       const bool mine = warp < NTB;
@@ -1288,19 +1300,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
       const int nq = (rb - J) * RPE;
       int chunk = 0;
       for (int q0 = 0; q0 < nq; q0 += kLeKT, ++chunk) {
-        // pairs: A rows l < 16 (l < jb real), B rows j < kpb (C column j < nc, or
-        // panel column j - kpc < jb); q pair in 0..30
+        // pairs: A rows l < 16 (l < jb real), B rows j < kpb (C column j < nc,
+        // panel column j - kpc < jb, or earlier column j - kpc - 8 < J); q pair in 0..30
         const int npa = 16 * (kLeKT / 2), npb = kpb * (kLeKT / 2);
         for (int e2 = threadIdx.x; e2 < npa + npb; e2 += kThreads) {
           const bool isA = e2 < npa;
           const int f = isA ? e2 : e2 - npa;
           const int row = f / (kLeKT / 2), q = 2 * (f % (kLeKT / 2)), qa = q0 + q;
           const int yl = isA ? row : row - kpc;  // panel column of a Y row, else < 0
+          const int pl = isA ? -1 : row - kpc - kNB;  // earlier column, else < 0
           double x0 = 0.0, x1 = 0.0;
           int em = 0;
-          if ((yl >= 0 && yl < jb) || (!isA && row < nc)) {
-            const bool isY = yl >= 0;
-            const int col = isY ? J + yl : c0 + row;
+          if ((yl >= 0 && yl < jb) || (!isA && row < nc) || pl >= 0) {
+            const bool isY = yl >= 0 && yl < kNB;
+            const int col = pl >= 0 ? pl : (isY ? J + yl : c0 + row);
             auto part = [&](int qq) -> double {
               if (qq >= nq) return 0.0;
               const int r = J + qq / RPE;
@@ -1310,7 +1323,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
             };
             x0 = part(qa);
             x1 = part(qa + 1);
-            em = isY ? eY[yl] : eC[row];
+            em = pl >= 0 ? eP[pl] : (isY ? eY[yl] : eC[row]);
           }
           unsigned w[kEmuSlices];
           emu_split2(x0, x1, em, em, w);
@@ -1352,20 +1365,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
       if (mine) {
         emu_fold(acc, hi, lo4);
 #pragma unroll
+        double* gw = reinterpret_cast<double*>(wsp<S>(ws, I.oGw) + (int64_t)it.idx * k * k);
         for (int e = 0; e < 2; ++e) {  // rows g (< 8) of the 16-row tile
-          const int l = g, j = jb0 + 2 * t4 + e, i = j - kpc;
+          const int l = g, j = jb0 + 2 * t4 + e, i = j - kpc, pi = j - kpc - kNB;
           if (l >= jb) continue;
           if (j < nc) {
             const double v = emu_fx((long long)hi[e], (long long)lo4[e], eY[l] + eC[j] - 2044);
             reinterpret_cast<double*>(Wb + l + j * kNB)[imag ? 1 : 0] = v;
-          } else if (i > l && i < jb) {  // G(l, i), strictly upper part only
+          } else if (i > l && i < jb) {  // G(J+l, J+i), strictly upper part only
             const double v = emu_fx((long long)hi[e], (long long)lo4[e], eY[l] + eY[i] - 2044);
             reinterpret_cast<double*>(T + l + i * kNB)[imag ? 1 : 0] = v;
+            gw[RPE * ((J + l) + (int64_t)(J + i) * k) + (imag ? 1 : 0)] = v * beta_s[J + i];
+          } else if (pi >= 0 && pi < J) {  // G(pi, J+l) = conj(Y_{J+l}^* Y_pi)
+            const double v = emu_fx((long long)hi[e], (long long)lo4[e], eY[l] + eP[pi] - 2044);
+            gw[RPE * (pi + (int64_t)(J + l) * k) + (imag ? 1 : 0)] = (imag ? -v : v) * beta_s[J + l];
           }
         }
       }
       __syncthreads();
     }
+    if (nc == 0) continue;  // last panel: only the Gram blocks were needed
     // W <- T^* W (FP64) without forming T.  T, the triangular factor of
     // H_J ... H_{J+jb-1} = I - Y_J T Y_J^*, satisfies T^-1 = diag(1/beta) +
     // (strictly upper part of G) (forward accumulation of the reflectors), so

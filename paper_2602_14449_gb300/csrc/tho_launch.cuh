@@ -40,12 +40,13 @@ void launch_gram_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, cons
 template <class S>
 void launch_apply_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
                       void* ws, cudaStream_t st) {
+  const int wy = 1 | (pc.leaf_tc ? 2 : 0);  // compact WY form; G' from the leaf kernel
   if (pc.apply_mt == 1)
-    k_apply_emu<S, 1><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, 1);
+    k_apply_emu<S, 1><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, wy);
   else if (pc.apply_mt == 2)
-    k_apply_emu<S, 2><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, 1);
+    k_apply_emu<S, 2><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, wy);
   else
-    k_apply_emu<S, 4><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, 1);
+    k_apply_emu<S, 4><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, wy);
 }
 
 template <class S, class B, bool EMU>
@@ -199,7 +200,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   // Emulated mode: the leaf QR ends with the compact WY output.  Its trailing
   // updates go to tensor cores when they are wide enough to pay for the
   // slicing (complex, k >= 24: two CTAs per SM instead of three); else FP64.
-  if (EMU && pc.dtype == 1 && pc.kmax >= 24)  // dtype 1: complex128
+  if (EMU && pc.leaf_tc)
     k_leaf_emu<S><<<pc.tab.leaf_n, blk, pc.smem_leaf_emu, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
                                                                pc.any_k0 ? 1 : 0);
   else

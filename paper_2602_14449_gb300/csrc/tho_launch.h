@@ -49,6 +49,7 @@ struct PlanCore {
   int upd_mt = 4;    // emulated update: 16-row tiles per warp column (max over problems)
   int apply_mt = 4;  // emulated apply: the same bound, lowered until its stage fits
   int sms = 0;       // SMs of the plan's device
+  bool leaf_tc = false;  // emulated complex plan with k >= 24: k_leaf_emu (writes G' for the apply)
   size_t smem_apply_emu = 0;
   size_t smem_gram_pipe = 0, smem_gram_umma = 0;
   bool gram_umma = false;  // emulated Gram on tcgen05 (when its stages fit)

@@ -44,6 +44,7 @@ struct Inst {
   int64_t rows1, rows4;  // rows per chunk of sweeps 1 and 3b (multiples of kTileRows)
   int64_t oX, oQ1, oR1, oT, oWt, oZ, oZ2, oG1, oG3, oRn, oRef, oF;
   int64_t oBeta;  // emulated mode: leaf reflector betas (nb x k)
+  int64_t oGw;    // emulated mode, tensor-core leaf: per leaf G' = (Y^* Y) diag(beta), strictly upper (nb x k x k)
   int64_t oEv;  // emulated products: column exponents of V per sweep-1 chunk (g1 x k0p ints)
   int64_t oVs;       // emulated products: bf16 slices of V, kVsTileBytes per row tile (g1 x vs_tiles tiles)
   int64_t vs_tiles;  // row tiles of kUmmaKT real steps per sweep-1 chunk

@@ -101,24 +101,43 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
     }
     __syncthreads();
     if (own && c > j) {
+      // The top entry (v_j at row j of R_a) rides in the last row group's
+      // unused slot when j mod 4 != 3 (row group 3 has no row <= j there), so
+      // no separate FP64 instruction is issued for it; then only that lane
+      // holds the updated top entry.
+      const bool fold = (j % kTreeRG) != kTreeRG - 1;
+      const bool top = fold && g == kTreeRG - 1;
       const double b = bsh[buf];
       if (b != 0.0) {
         const S vj = vsh[buf];
-        S d = (g == 0) ? cmadd(zero<S>(), vj, xt) : zero<S>();
+        S d = zero<S>();
+        if (!fold) d = (g == 0) ? cmadd(zero<S>(), vj, xt) : zero<S>();
 #pragma unroll
         for (int q = 0; q <= j / kTreeRG; ++q) {
           const int r = g + kTreeRG * q;
-          if (r <= j) d = cmadd(d, ush[buf][r], xb[q]);
+          if (q < j / kTreeRG) {
+            d = cmadd(d, ush[buf][r], xb[q]);  // r <= j in every lane
+          } else {
+            const bool act = r <= j;
+            d = cmadd(d, act ? ush[buf][r] : (top ? vj : zero<S>()), act ? xb[q] : (top ? xt : zero<S>()));
+          }
         }
         d = scale(tree_sum4(d, m4), b);
-        xt = msub(xt, vj, d);
+        if (!fold) xt = msub(xt, vj, d);
 #pragma unroll
         for (int q = 0; q <= j / kTreeRG; ++q) {
           const int r = g + kTreeRG * q;
-          if (r <= j) xb[q] = msub(xb[q], ush[buf][r], d);
+          if (q < j / kTreeRG) {
+            xb[q] = msub(xb[q], ush[buf][r], d);
+          } else {
+            const bool act = r <= j;
+            const S y = msub(act ? xb[q] : xt, act ? ush[buf][r] : vj, d);
+            if (act) xb[q] = y;
+            else if (top) xt = y;
+          }
         }
       }
-      if (g == 0) Rdst[j + c * k] = xt;  // entry (j, c) of the node's R is final
+      if (g == (fold ? kTreeRG - 1 : 0)) Rdst[j + c * k] = xt;  // entry (j, c) of the node's R is final
     }
     xt = xt_next;
   }

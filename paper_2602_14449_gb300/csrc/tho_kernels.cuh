@@ -476,16 +476,22 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
     };
     if (warp == 0) reflector(J);
     __syncthreads();
+    // Column slots: warp 0 takes column j + 1 (the serial chain); warp 4, which
+    // shares warp 0's SM sub-partition and so its FP64 pipe, takes none; the
+    // other six warps take columns j + 2.. (at most six: kNB = 8).
+    static_assert(kThreads == 256 && kNB <= 8, "the column slots assume 8 warps and panels of <= 8 columns");
+    const int slot = warp == 0 ? 0 : (warp < 4 ? warp : (warp > 4 ? warp - 1 : -1));
     for (int j = J; j < J + jb; ++j) {
       const double b = beta_s[j];
-      for (int c = j + 1 + warp; c < J + jb; c += nw) {
+      const int c = j + 1 + slot;
+      if (slot >= 0 && c < J + jb) {
         if (b != 0.0) {
           B d = zero<B>();
           for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
           d = scale(warp_sum(d), b);
           for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
         }
-        if (c == j + 1) {  // warp 0 only (c - j - 1 = warp)
+        if (slot == 0) {
           __syncwarp();
           reflector(c);
         }

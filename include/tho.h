@@ -126,6 +126,24 @@ int32_t tho_plan_leaf_rows(tho_plan_t plan);
 tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A, int64_t lda,
                       void* Q, int64_t ldq, void* R, void* S, void* stream);
 
+/* tho_orth for operands in HOST memory (page-locked for full copy bandwidth),
+ * count = 1 plans; same shapes, layouts and outputs.  The plan stages the
+ * problem in one of two device buffer sets used alternately (allocated on the
+ * first call: 2 x (n k0 + 2 n k + k^2 + k0 k) elements): the input copy runs on
+ * the plan's input copy stream, the computation on `stream`, the output copy
+ * on the plan's output copy stream.  So consecutive calls overlap the input
+ * copy of one problem and the output copy of the one before last with the
+ * computation of the previous one.  Asynchronous: V and A must stay unchanged
+ * until the call's input copy has completed, and Q, R, S are complete once
+ * `stream` has passed a later tho_orth_host_wait(plan, stream).  R and S may
+ * be NULL.  Errors: ARG, ALIGN, NOMEM, CUDA. */
+tho_status_t tho_orth_host(tho_plan_t plan, const void* hV, int64_t ldv, const void* hA, int64_t lda,
+                           void* hQ, int64_t ldq, void* hR, void* hS, void* stream);
+
+/* Make `stream` wait for the output copies of every tho_orth_host call issued
+ * on this plan so far.  Errors: ARG, CUDA. */
+tho_status_t tho_orth_host_wait(tho_plan_t plan, void* stream);
+
 /* Pointers of one batched problem (same meaning as in tho_orth). */
 typedef struct {
   const void* V;

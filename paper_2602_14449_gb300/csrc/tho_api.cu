@@ -35,6 +35,13 @@ struct tho_plan_s {
   size_t ev_used = 0;            // pairs recorded since the last read
   // reverse mode (allocated on the first tho_orth_backward call)
   tho::BwdState* bwd = nullptr;
+  // host-buffer path (allocated on the first tho_orth_host call): two device
+  // staging sets used alternately, copy streams for each direction, and per
+  // set the events "inputs copied", "computed" and "outputs copied".
+  void* hs_buf[2] = {nullptr, nullptr};
+  cudaStream_t hs_in = nullptr, hs_out = nullptr;
+  cudaEvent_t hs_ev_in[2] = {nullptr, nullptr}, hs_ev_comp[2] = {nullptr, nullptr}, hs_ev_out[2] = {nullptr, nullptr};
+  int hs_next = 0;
 };
 
 namespace {
@@ -63,6 +70,14 @@ void free_plan(tho_plan_s* p) {
     tho::backward_free(*p->bwd);
     delete p->bwd;
   }
+  for (int b = 0; b < 2; ++b) {
+    if (p->hs_buf[b]) cudaFree(p->hs_buf[b]);
+    if (p->hs_ev_in[b]) cudaEventDestroy(p->hs_ev_in[b]);
+    if (p->hs_ev_comp[b]) cudaEventDestroy(p->hs_ev_comp[b]);
+    if (p->hs_ev_out[b]) cudaEventDestroy(p->hs_ev_out[b]);
+  }
+  if (p->hs_in) cudaStreamDestroy(p->hs_in);
+  if (p->hs_out) cudaStreamDestroy(p->hs_out);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->pc.side) cudaStreamDestroy(p->pc.side);
@@ -381,6 +396,83 @@ tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A
   }
   if (plan->L->run(plan->pc, nullptr, io0, reinterpret_cast<cudaStream_t>(stream), hook) != cudaSuccess)
     return THO_ERR_CUDA;
+  return THO_OK;
+}
+
+tho_status_t tho_orth_host(tho_plan_t plan, const void* hV, int64_t ldv, const void* hA, int64_t lda, void* hQ,
+                           int64_t ldq, void* hR, void* hS, void* stream) {
+  if (!plan || plan->pc.count != 1) return THO_ERR_ARG;
+  const Inst& I = plan->pc.h_insts[0];
+  const size_t el = plan->L->elem;
+  tho_status_t s = check_io(I, el, hV, ldv, hA, lda, hQ, ldq, hR, hS);
+  if (s != THO_OK) return s;
+  const int64_t n = I.n, k0 = I.k0, k = I.k;
+  // Staging set: V (n x k0), A (n x k), Q (n x k), R (k x k), S (k0 x k), each
+  // column-major with leading dimension n (R: k, S: k0), 256-byte aligned.
+  const size_t szV = (size_t)(n * k0) * el, szA = (size_t)(n * k) * el, szR = (size_t)(k * k) * el;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t oA = al(szV), oQ = oA + al(szA), oR = oQ + al(szA), oS = oR + al(szR);
+  const size_t total = oS + al((size_t)(k0 * k) * el);
+  if (!plan->hs_buf[0]) {
+    for (int b = 0; b < 2; ++b) {
+      if (cudaMalloc(&plan->hs_buf[b], total) != cudaSuccess) return THO_ERR_NOMEM;
+      if (cudaEventCreateWithFlags(&plan->hs_ev_in[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&plan->hs_ev_comp[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&plan->hs_ev_out[b], cudaEventDisableTiming) != cudaSuccess)
+        return THO_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&plan->hs_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&plan->hs_out, cudaStreamNonBlocking) != cudaSuccess)
+      return THO_ERR_CUDA;
+  }
+  const int b = plan->hs_next;
+  plan->hs_next ^= 1;
+  char* base = static_cast<char*>(plan->hs_buf[b]);
+  void *dV = base, *dA = base + oA, *dQ = base + oQ, *dR = base + oR, *dS = base + oS;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  bool ok = true;
+  auto chk = [&ok](cudaError_t e) { ok = ok && e == cudaSuccess; };
+  // A column-major matrix with leading dimension ld: one linear copy when the
+  // columns are contiguous (ld = n), else one copy per column.
+  auto copy_cm = [&](void* dst, int64_t ldd, const void* src, int64_t lds, int64_t cols, cudaMemcpyKind kind,
+                     cudaStream_t cs) {
+    if (cols <= 0) return;
+    if (ldd == n && lds == n) {
+      chk(cudaMemcpyAsync(dst, src, (size_t)(n * cols) * el, kind, cs));
+      return;
+    }
+    for (int64_t c = 0; c < cols; ++c)
+      chk(cudaMemcpyAsync(static_cast<char*>(dst) + (size_t)(c * ldd) * el,
+                          static_cast<const char*>(src) + (size_t)(c * lds) * el, (size_t)n * el, kind, cs));
+  };
+  // Inputs: into set b once the computation that last read it is done.
+  chk(cudaStreamWaitEvent(plan->hs_in, plan->hs_ev_comp[b], 0));
+  copy_cm(dV, n, hV, ldv, k0, cudaMemcpyHostToDevice, plan->hs_in);
+  copy_cm(dA, n, hA, lda, k, cudaMemcpyHostToDevice, plan->hs_in);
+  chk(cudaEventRecord(plan->hs_ev_in[b], plan->hs_in));
+  if (!ok) return THO_ERR_CUDA;
+  // Computation on the caller's stream once the inputs are in and set b's
+  // previous outputs have left.
+  chk(cudaStreamWaitEvent(st, plan->hs_ev_in[b], 0));
+  chk(cudaStreamWaitEvent(st, plan->hs_ev_out[b], 0));
+  if (!ok) return THO_ERR_CUDA;
+  s = tho_orth(plan, k0 > 0 ? dV : nullptr, n, dA, n, dQ, n, dR, dS, stream);
+  if (s != THO_OK) return s;
+  chk(cudaEventRecord(plan->hs_ev_comp[b], st));
+  // Outputs on the second copy stream.
+  chk(cudaStreamWaitEvent(plan->hs_out, plan->hs_ev_comp[b], 0));
+  copy_cm(hQ, ldq, dQ, n, k, cudaMemcpyDeviceToHost, plan->hs_out);
+  if (hR) chk(cudaMemcpyAsync(hR, dR, szR, cudaMemcpyDeviceToHost, plan->hs_out));
+  if (hS && k0 > 0) chk(cudaMemcpyAsync(hS, dS, (size_t)(k0 * k) * el, cudaMemcpyDeviceToHost, plan->hs_out));
+  chk(cudaEventRecord(plan->hs_ev_out[b], plan->hs_out));
+  return ok ? THO_OK : THO_ERR_CUDA;
+}
+
+tho_status_t tho_orth_host_wait(tho_plan_t plan, void* stream) {
+  if (!plan) return THO_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (int b = 0; b < 2; ++b)
+    if (plan->hs_ev_out[b] && cudaStreamWaitEvent(st, plan->hs_ev_out[b], 0) != cudaSuccess) return THO_ERR_CUDA;
   return THO_OK;
 }
 

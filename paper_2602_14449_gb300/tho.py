@@ -28,7 +28,7 @@ THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE = 0x1, 0x2
 THO_MAX_K0, THO_MAX_K = 128, 32
 
 EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",
-            "tho_plan_leaf_rows",
+            "tho_plan_leaf_rows", "tho_orth_host", "tho_orth_host_wait",
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
             "tho_orth_noalloc")
@@ -80,6 +80,10 @@ def load(path: str | None = None):
         lib.tho_plan_leaf_rows.restype = ctypes.c_int32
         lib.tho_orth.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp, vp]
         lib.tho_orth.restype = ctypes.c_int
+        lib.tho_orth_host.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp, vp]
+        lib.tho_orth_host.restype = ctypes.c_int
+        lib.tho_orth_host_wait.argtypes = [vp, vp]
+        lib.tho_orth_host_wait.restype = ctypes.c_int
         lib.tho_orth_batched.argtypes = [vp, ctypes.POINTER(Instance), i32, vp]
         lib.tho_orth_batched.restype = ctypes.c_int
         lib.tho_orth_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp]
@@ -112,11 +116,11 @@ def colmajor(x: torch.Tensor) -> torch.Tensor:
     return x.t().contiguous().t()
 
 
-def _ld(x: torch.Tensor, name: str) -> int:
+def _ld(x: torch.Tensor, name: str, host: bool = False) -> int:
     if x.dim() != 2:
         raise ValueError(f"{name} must be 2-D")
-    if not x.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.is_cuda == host:
+        raise ValueError(f"{name} must be a {'host (CPU)' if host else 'CUDA'} tensor")
     rows, cols = x.shape
     if cols > 1 and x.stride(0) != 1:
         raise ValueError(f"{name} must be column-major (stride (1, ld)); use tho.colmajor()")
@@ -245,6 +249,41 @@ def orth(V: torch.Tensor, A: torch.Tensor, prec: int = THO_PREC_FP64, want_R: bo
     _check(load().tho_orth(p.handle, _ptr(V) if k0 > 0 else None, ldv, _ptr(A), lda, _ptr(Q), ldq,
                            _ptr(R), _ptr(S), ctypes.c_void_p(st)), "tho_orth")
     return Q, R, S
+
+
+def orth_host(V: torch.Tensor, A: torch.Tensor, Q: torch.Tensor, R: torch.Tensor | None = None,
+              S: torch.Tensor | None = None, prec: int = THO_PREC_FP64, plan: Plan | None = None):
+    """tho_orth_host: Algorithm 1 with V, A and the outputs Q, R, S in host memory.
+
+    V (n x k0), A (n x k) and Q (n x k) are column-major CPU tensors (pinned for
+    full copy bandwidth); R (k x k) and S (k0 x k) are optional outputs with
+    ld = k and k0.  Asynchronous on the current torch stream: the inputs must
+    not change until their copy is done, and the outputs are complete after
+    orth_host_wait(plan) and a synchronization of that stream.  Consecutive
+    calls overlap their copies with the previous computation.
+    """
+    n, k = A.shape
+    k0 = V.shape[1] if V is not None else 0
+    flags = THO_FLAG_ALLOW_K0_ZERO if k0 == 0 else 0
+    for x, nm in ((R, "R"), (S, "S")):
+        if x is not None and x.is_cuda:
+            raise ValueError(f"{nm} must be a host (CPU) tensor")
+    for x, nm, ld in ((R, "R", k), (S, "S", k0)):
+        if x is not None and (x.stride(0) != 1 or (x.shape[1] > 1 and x.stride(1) != ld)):
+            raise ValueError(f"{nm} must be column-major with ld = {ld}")
+    p = plan or get_plan([(n, k0, k)], A.dtype, prec, flags)
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().tho_orth_host(p.handle, _ptr(V) if k0 > 0 else None, _ld(V, "V", True) if k0 > 0 else n,
+                                _ptr(A), _ld(A, "A", True), _ptr(Q), _ld(Q, "Q", True), _ptr(R), _ptr(S),
+                                ctypes.c_void_p(st)),
+           "tho_orth_host")
+    return Q, R, S
+
+
+def orth_host_wait(plan: Plan):
+    """Make the current torch stream wait for every orth_host output copy of ``plan``."""
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().tho_orth_host_wait(plan.handle, ctypes.c_void_p(st)), "tho_orth_host_wait")
 
 
 def orth_batched(pairs, prec: int = THO_PREC_FP64, plan: Plan | None = None, outs=None):

@@ -258,3 +258,50 @@ def test_emulated_batched_matches_oracle(tho, dtype):
     torch.cuda.synchronize()
     for (Q, _, _), (Q2, _, _) in zip(res, res2):
         assert torch.equal(Q, Q2)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("prec_name", ["THO_PREC_FP64", "THO_PREC_FP64_EMU"])
+def test_orth_host_matches_device(tho, dtype, prec_name):
+    """tho_orth_host: five different problems back to back through the two
+    staging sets (copies overlapping the previous computation), pinned and
+    pageable host buffers, each bitwise equal to tho_orth on the device."""
+    prec = getattr(tho, prec_name)
+    n, k0, k = 6000, 24, 12
+    plan = tho.Plan([(n, k0, k)], dtype, prec, 0)
+    probs = [inputs.random_problem(n, k0, k, dtype=dtype, seed=80 + i) for i in range(5)]
+    outs = []
+    for i, p in enumerate(probs):
+        pin = i % 2 == 0
+        hV = p.V.clone().pin_memory() if pin else p.V.clone()
+        hA = p.A.clone().pin_memory() if pin else p.A.clone()
+        hQ = torch.empty_strided((n, k), (1, n), dtype=dtype)
+        hR = torch.empty_strided((k, k), (1, k), dtype=dtype)
+        hS = torch.empty_strided((k0, k), (1, k0), dtype=dtype)
+        if pin:
+            hQ, hR, hS = hQ.pin_memory(), hR.pin_memory(), hS.pin_memory()
+        tho.orth_host(hV, hA, hQ, hR, hS, prec=prec, plan=plan)
+        outs.append((hV, hA, hQ, hR, hS))
+    tho.orth_host_wait(plan)
+    torch.cuda.synchronize()
+    for p, (_, _, hQ, hR, hS) in zip(probs, outs):
+        Q, R, S = tho.orth(p.V.cuda(), p.A.cuda(), prec=prec, plan=plan)
+        torch.cuda.synchronize()
+        assert torch.equal(hQ, Q.cpu()) and torch.equal(hR, R.cpu()) and torch.equal(hS, S.cpu())
+    Qo, _, _ = oracle.two_stage(probs[-1].V.numpy(), probs[-1].A.numpy())
+    np.testing.assert_allclose(outs[-1][2].numpy(), Qo, atol=TOL_Q)
+
+
+def test_orth_host_k0_zero(tho):
+    """tho_orth_host with k0 = 0 (V absent): the Householder QR of A."""
+    n, k = 3000, 8
+    p = inputs.random_problem(n, 0, k, dtype=torch.float64, seed=7)
+    plan = tho.Plan([(n, 0, k)], torch.float64, tho.THO_PREC_FP64, tho.THO_FLAG_ALLOW_K0_ZERO)
+    hQ = torch.empty_strided((n, k), (1, n), dtype=torch.float64)
+    hR = torch.empty_strided((k, k), (1, k), dtype=torch.float64)
+    tho.orth_host(None, p.A.clone(), hQ, hR, None, plan=plan)
+    tho.orth_host_wait(plan)
+    torch.cuda.synchronize()
+    Qo, Ro = oracle.householder_qr(p.A.numpy())
+    np.testing.assert_allclose(hQ.numpy(), Qo, atol=TOL_Q)
+    np.testing.assert_allclose(hR.numpy(), Ro, atol=TOL_Q * np.abs(Ro).max())

@@ -433,17 +433,23 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
 // Warps 0..15 build B, then fold and write each 128-row tile; warp 16 issues
 // the MMAs (and owns TMEM); warp 17 issues the bulk copies.
 // Shared: Bz [8][N x 128] bf16 | stages [2][8][2 i-groups][4 tiles][4 step groups][128 B] |
-// mbarriers full[2], empty[2], done, free, fin | TMEM slot, abort | eV | eZ.
+// mbarriers full[kUpdStages], empty[kUpdStages], done, free, fin | TMEM slot, abort | eV | eZ.
 constexpr int kUpdWarps = 18;
 constexpr int kUpdThreads = 32 * kUpdWarps;
 constexpr int kUpdStageBytes = kEmuSlices * 2 * 4 * 512;
+// Three stages in flight: the V-slice loads (a 32 KB stage per 16 columns, at
+// close to the HBM rate the MMAs consume them) take longer than one stage of
+// MMAs, so two stages left the issuer waiting on the loads.
+constexpr int kUpdStages = 3;
+constexpr int kUpdBars = 2 * kUpdStages + 3;
 
 __host__ __device__ inline int upd_umma_n(bool cplx, int k) {
   const int kpe = (k + 7) / 8 * 8;
   return cplx ? 2 * kpe : (k + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t upd_umma_smem(int N) {
-  return (size_t)kEmuSlices * N * 128 * 2 + (size_t)2 * kUpdStageBytes + 8 * 8 + 16 + sizeof(int) * (128 + 64);
+  return (size_t)kEmuSlices * N * 128 * 2 + (size_t)kUpdStages * kUpdStageBytes + 8 * kUpdBars + 16 +
+         sizeof(int) * (128 + 64);
 }
 
 template <class S>
@@ -464,10 +470,10 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
   const int bz = N * 128 * 2;  // one slice of B
   unsigned char* Bz = smem_raw;
   unsigned char* stages = Bz + kEmuSlices * bz;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + 2 * kUpdStageBytes);
-  const uint32_t b_full = smem_u32(bars), b_empty = b_full + 16, b_done = b_full + 32, b_free = b_full + 40,
-                 b_fin = b_full + 48;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + kUpdStages * kUpdStageBytes);
+  const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * kUpdStages, b_done = b_empty + 8 * kUpdStages,
+                 b_free = b_done + 8, b_fin = b_free + 8;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kUpdBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   int* eV = reinterpret_cast<int*>(tslot + 4);
   int* eZ = eV + 128;
@@ -487,10 +493,10 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
 
   for (int i = threadIdx.x; i < 128; i += kUpdThreads) eV[i] = i < k0 ? eVg[i] : 0;
   if (threadIdx.x == 0) {
-    mbar_init(b_full, 1);
-    mbar_init(b_full + 8, 1);
-    mbar_init(b_empty, 1);
-    mbar_init(b_empty + 8, 1);
+    for (int i = 0; i < kUpdStages; ++i) {
+      mbar_init(b_full + 8 * i, 1);
+      mbar_init(b_empty + 8 * i, 1);
+    }
     mbar_init(b_done, 1);
     mbar_init(b_free, 16);
     mbar_init(b_fin, 1);
@@ -553,8 +559,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
       int sidx = 0;
       for (int u = 0; u < nut && !*abort_flag; ++u) {
         for (int ks = 0; ks < nks; ++ks, ++sidx) {
-          const int s = sidx & 1;
-          bool ok = mbar_wait(b_full + 8 * s, (sidx >> 1) & 1);
+          const int s = sidx % kUpdStages;
+          bool ok = mbar_wait(b_full + 8 * s, (sidx / kUpdStages) & 1);
           if (ok && ks == 0 && u > 0) ok = mbar_wait(b_free, (u - 1) & 1);
           if (!ok) {
             *abort_flag = 1;
@@ -586,9 +592,9 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
     for (int u = 0; u < nut && !*abort_flag; ++u) {
       const int ntl = min(4, ntg - 4 * u);
       for (int ks = 0; ks < nks; ++ks, ++sidx) {
-        const int s = sidx & 1;
+        const int s = sidx % kUpdStages;
         bool ok = true;
-        if (lane == 0 && sidx >= 2) ok = mbar_wait(b_empty + 8 * s, ((sidx >> 1) - 1) & 1);
+        if (lane == 0 && sidx >= kUpdStages) ok = mbar_wait(b_empty + 8 * s, ((sidx / kUpdStages) - 1) & 1);
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (!ok) {
           *abort_flag = 1;
@@ -614,6 +620,18 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
     const int qd = warp & 3, j0 = (warp >> 2) * 8;
     const bool act = j0 < (C ? kpe : N);
     for (int u = 0; u < nut && !*abort_flag; ++u) {
+      // While tile u's MMAs run, pull its base entries (A or Q) toward L1 so
+      // that the loads after the fold do not wait on HBM.
+      if (act) {
+        const int m = qd * 32 + lane;
+        const int64_t row = r_begin + (int64_t)u * UR + (C ? (m >> 1) : m);
+        if (row < r_end) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (j0 + c < k)
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(Bd + (int64_t)(j0 + c) * ldb + row * RPE + (C ? (m & 1) : 0)));
+        }
+      }
       if (!mbar_wait(b_done, u & 1)) {
         *abort_flag = 1;
         break;

@@ -620,18 +620,6 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
     const int qd = warp & 3, j0 = (warp >> 2) * 8;
     const bool act = j0 < (C ? kpe : N);
     for (int u = 0; u < nut && !*abort_flag; ++u) {
-      // While tile u's MMAs run, pull its base entries (A or Q) toward L1 so
-      // that the loads after the fold do not wait on HBM.
-      if (act) {
-        const int m = qd * 32 + lane;
-        const int64_t row = r_begin + (int64_t)u * UR + (C ? (m >> 1) : m);
-        if (row < r_end) {
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (j0 + c < k)
-              asm volatile("prefetch.global.L1 [%0];" ::"l"(Bd + (int64_t)(j0 + c) * ldb + row * RPE + (C ? (m & 1) : 0)));
-        }
-      }
       if (!mbar_wait(b_done, u & 1)) {
         *abort_flag = 1;
         break;

@@ -869,11 +869,28 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
     const int rb = (int)(leaf_lo(I, lb + 1) - lo);
     const S* Fb = Fg + (I.lev_off[0] + lb) * (int64_t)kk;
     __syncthreads();  // the previous leaf is done with every buffer
-    for (int e = threadIdx.x; e < k * rb; e += kEmuThreads) {
-      const int r = e % rb, i = e / rb;
-      Qr[r * ldr + i] = Qg[(lo + r) + (int64_t)i * ldq];
+    // Loads in groups of 8 per thread ahead of their stores: one memory round
+    // trip per group instead of one per element (in-order issue would make
+    // each store wait for its load before the next load issues).
+    for (int e0 = threadIdx.x; e0 < k * rb; e0 += 8 * kEmuThreads) {
+      S v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kEmuThreads;
+        v[u] = e < k * rb ? Qg[(lo + e % rb) + (int64_t)(e / rb) * ldq] : zero<S>();
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kEmuThreads;
+        if (e < k * rb) Qr[(e % rb) * ldr + e / rb] = v[u];
+      }
     }
-    for (int e = threadIdx.x; e < kk; e += kEmuThreads) Fr[(e % k) + (e / k) * ldf] = Fb[e];
+    for (int e0 = threadIdx.x; e0 < kk; e0 += 2 * kEmuThreads) {
+      const int e1 = e0 + kEmuThreads;
+      const S a = Fb[e0], b = e1 < kk ? Fb[e1] : zero<S>();
+      Fr[(e0 % k) + (e0 / k) * ldf] = a;
+      if (e1 < kk) Fr[(e1 % k) + (e1 / k) * ldf] = b;
+    }
     __syncthreads();
     for (int i = warp; i < k; i += NW) {
       int m = 0;
@@ -1214,9 +1231,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
 
   const S* Asrc = from_q ? reinterpret_cast<const S*>(io.Q) : reinterpret_cast<const S*>(io.A);
   const int64_t ldsrc = from_q ? io.ldq : io.lda;
-  for (int e = threadIdx.x; e < P * kp; e += kThreads) {
-    const int r = e % P, c = e / P;
-    Lb[e] = (r < rb && c < k) ? Asrc[(lo + r) + (int64_t)c * ldsrc] : zero<S>();
+  // Loads in groups of 8 per thread ahead of their stores (one round trip per group).
+  for (int e0 = threadIdx.x; e0 < P * kp; e0 += 8 * kThreads) {
+    S v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kThreads, r = e % P, c = e / P;
+      v[u] = (e < P * kp && r < rb && c < k) ? Asrc[(lo + r) + (int64_t)c * ldsrc] : zero<S>();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < P * kp) Lb[e] = v[u];
+    }
   }
   __syncthreads();
   auto Yv = [&](int r, int l) -> S { return r == l ? vdiag[l] : (r > l ? Lb[r + l * P] : zero<S>()); };

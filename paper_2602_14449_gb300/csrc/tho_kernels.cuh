@@ -430,9 +430,19 @@ __global__ void __launch_bounds__(kThreads) k_leaf(const Inst* insts, const Io* 
   // from_q: A'_b was already formed (emulated update) and parked in Q's rows.
   const S* Asrc = from_q ? reinterpret_cast<const S*>(io.Q) : A;
   const int64_t ldsrc = from_q ? io.ldq : io.lda;
-  for (int e = threadIdx.x; e < P * kp; e += kThreads) {
-    int r = e % P, c = e / P;
-    Lb[e] = (r < rb && c < k) ? cvt<B, S>(Asrc[(lo + r) + (int64_t)c * ldsrc]) : zero<B>();
+  // Loads in groups of 4 per thread ahead of their stores (one round trip per group).
+  for (int e0 = threadIdx.x; e0 < P * kp; e0 += 4 * kThreads) {
+    S v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * kThreads, r = e % P, c = e / P;
+      v[u] = (e < P * kp && r < rb && c < k) ? Asrc[(lo + r) + (int64_t)c * ldsrc] : zero<S>();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < P * kp) Lb[e] = cvt<B, S>(v[u]);
+    }
   }
   __syncthreads();
   if (k0 > 0 && !from_q) {

@@ -208,7 +208,20 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, c
   }
   S* Rf = reinterpret_cast<S*>(smem_raw);  // k x k bottom parts | k tops | k betas
   const S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
-  for (int e = threadIdx.x; e < kk + 2 * k; e += blockDim.x) Rf[e] = ref[e];
+  // Loads in groups of 8 per thread ahead of their stores (one round trip per group).
+  for (int e0 = threadIdx.x; e0 < kk + 2 * k; e0 += 8 * (int)blockDim.x) {
+    S v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = e < kk + 2 * k ? ref[e] : zero<S>();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < kk + 2 * k) Rf[e] = v[u];
+    }
+  }
   __syncthreads();
   const int c = threadIdx.x / kTreeRG, g = threadIdx.x % kTreeRG;
   if (c >= k) return;
@@ -324,7 +337,20 @@ __global__ void __launch_bounds__(32) k_tree_down_w(const Inst* insts, const Wor
   }
   S* Rf = reinterpret_cast<S*>(smem_raw);  // k x k bottom parts | k tops | k betas
   const S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
-  for (int e = threadIdx.x; e < kk + 2 * k; e += blockDim.x) Rf[e] = ref[e];
+  // Loads in groups of 8 per thread ahead of their stores (one round trip per group).
+  for (int e0 = threadIdx.x; e0 < kk + 2 * k; e0 += 8 * (int)blockDim.x) {
+    S v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = e < kk + 2 * k ? ref[e] : zero<S>();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < kk + 2 * k) Rf[e] = v[u];
+    }
+  }
   __syncwarp();
   const int c = threadIdx.x;
   if (c >= k) return;

@@ -169,7 +169,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
   for (int col = warp + (which ? k0 : 0); col < k0 + k; col += kUmmaThreads / 32) {
     const double* src = col < k0 ? Vd + (int64_t)col * ldv : Ad + (int64_t)(col - k0) * lda;
     int m = 0;
-    for (int64_t q = r_begin * RPE + lane; q < r_end * RPE; q += 32) m = max(m, dexp(src[q]));
+    int64_t q = r_begin * RPE + lane;
+    const int64_t qe = r_end * RPE;
+    for (; q + 7 * 32 < qe; q += 8 * 32) {  // eight loads in flight per lane
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = src[q + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) m = max(m, dexp(v[u]));
+    }
+    for (; q < qe; q += 32) m = max(m, dexp(src[q]));
     m = __reduce_max_sync(0xffffffffu, m);
     if (lane == 0) {
       if (col < k0) {

@@ -136,7 +136,9 @@ tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A
  * computation of the previous one.  Asynchronous: V and A must stay unchanged
  * until the call's input copy has completed, and Q, R, S are complete once
  * `stream` has passed a later tho_orth_host_wait(plan, stream).  R and S may
- * be NULL.  Errors: ARG, ALIGN, NOMEM, CUDA. */
+ * be NULL.  Calls on one plan share its workspace: issue them on one stream.
+ * A failed staging allocation leaves the plan as it was.
+ * Errors: ARG, ALIGN, NOMEM, CUDA. */
 tho_status_t tho_orth_host(tho_plan_t plan, const void* hV, int64_t ldv, const void* hA, int64_t lda,
                            void* hQ, int64_t ldq, void* hR, void* hS, void* stream);
 

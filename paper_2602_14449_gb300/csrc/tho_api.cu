@@ -413,17 +413,39 @@ tho_status_t tho_orth_host(tho_plan_t plan, const void* hV, int64_t ldv, const v
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t oA = al(szV), oQ = oA + al(szA), oR = oQ + al(szA), oS = oR + al(szR);
   const size_t total = oS + al((size_t)(k0 * k) * el);
-  if (!plan->hs_buf[0]) {
+  if (!plan->hs_out) {  // all or nothing: hs_out is created last
+    auto undo = [plan]() {
+      for (int b = 0; b < 2; ++b) {
+        if (plan->hs_buf[b]) cudaFree(plan->hs_buf[b]);
+        if (plan->hs_ev_in[b]) cudaEventDestroy(plan->hs_ev_in[b]);
+        if (plan->hs_ev_comp[b]) cudaEventDestroy(plan->hs_ev_comp[b]);
+        if (plan->hs_ev_out[b]) cudaEventDestroy(plan->hs_ev_out[b]);
+        plan->hs_buf[b] = nullptr;
+        plan->hs_ev_in[b] = plan->hs_ev_comp[b] = plan->hs_ev_out[b] = nullptr;
+      }
+      if (plan->hs_in) cudaStreamDestroy(plan->hs_in);
+      plan->hs_in = nullptr;
+    };
     for (int b = 0; b < 2; ++b) {
-      if (cudaMalloc(&plan->hs_buf[b], total) != cudaSuccess) return THO_ERR_NOMEM;
+      if (cudaMalloc(&plan->hs_buf[b], total) != cudaSuccess) {
+        plan->hs_buf[b] = nullptr;
+        cudaGetLastError();
+        undo();
+        return THO_ERR_NOMEM;
+      }
       if (cudaEventCreateWithFlags(&plan->hs_ev_in[b], cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&plan->hs_ev_comp[b], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&plan->hs_ev_out[b], cudaEventDisableTiming) != cudaSuccess)
+          cudaEventCreateWithFlags(&plan->hs_ev_out[b], cudaEventDisableTiming) != cudaSuccess) {
+        undo();
         return THO_ERR_CUDA;
+      }
     }
     if (cudaStreamCreateWithFlags(&plan->hs_in, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&plan->hs_out, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&plan->hs_out, cudaStreamNonBlocking) != cudaSuccess) {
+      plan->hs_out = nullptr;
+      undo();
       return THO_ERR_CUDA;
+    }
   }
   const int b = plan->hs_next;
   plan->hs_next ^= 1;

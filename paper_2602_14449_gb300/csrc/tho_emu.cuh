@@ -1190,13 +1190,14 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
 // Output as k_leaf's compact-WY mode: R_b into the tree's leaf node, Y into Q's
 // rows, the betas into the workspace.
 // Shared: Lb [kp][P] S | vdiag, rdiag, beta, T (kNB x kNB), W (kNB x kp) | scales |
-// slices: step W: A [8][16][40], B [8][kpc + 8][40]; step C: A [8][32][24], B [8][kpc][24].
+// slices: step W: A [8][16][40], B [8][kpc + 8 + J][40]; step C: A [8][64][24], B [8][kpc][24].
 constexpr int kLeKT = 32;   // real contraction steps per chunk of the W product
 constexpr int kLeLdW = 40;  // row stride of the W-product slices (conflict-free ldmatrix)
 constexpr int kLeLdC = 24;  // row stride of the C-product slices (16 steps + pad)
+constexpr int kLeRC = 64;   // rows per chunk of the C product (4 m-tiles: 2-3 output tiles per warp)
 __host__ __device__ inline size_t leaf_emu_smem(int P, int kp, size_t elem) {
   const size_t sw = (size_t)kEmuSlices * 2 * kLeLdW * (16 + kMaxKP);
-  const size_t sc = (size_t)kEmuSlices * 2 * kLeLdC * (32 + 24);
+  const size_t sc = (size_t)kEmuSlices * 2 * kLeLdC * (kLeRC + 24);
   return (size_t)P * kp * elem + (size_t)kMaxKP * (2 * elem + 8) + (size_t)kNB * kNB * elem +
          (size_t)kNB * kMaxKP * elem + sizeof(int) * (kNB + 2 * kMaxKP) + (sw > sc ? sw : sc) + 64;
 }
@@ -1444,8 +1445,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     // ---- C <- C - Y_J W on tensor cores.  W'(l, j) = 2^(eY_l - 1078) W(l, j), real-embedded
     // along the contraction (complex: (Re W', -Im W') pairs; Im outputs swap).
     {
-      unsigned short* Ac = Us;                           // [8][32][kLeLdC]
-      unsigned short* Bc = Us + kEmuSlices * 32 * kLeLdC;  // [8][kpc][kLeLdC]
+      unsigned short* Ac = Us;                                // [8][kLeRC][kLeLdC]
+      unsigned short* Bc = Us + kEmuSlices * kLeRC * kLeLdC;  // [8][kpc][kLeLdC]
       auto wp = [&](int q, int j) -> double {  // W' entry at real contraction step q, column j
         const int l = q / RPE;
         if (l >= jb || j >= nc) return 0.0;
@@ -1472,9 +1473,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
 #pragma unroll
         for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Bc + (p * kpc + j) * kLeLdC + q) = w[p];
       }
-      for (int rc = J; rc < rb; rc += 32) {
+      for (int rc = J; rc < rb; rc += kLeRC) {
         __syncthreads();  // Bc written; the previous chunk's MMAs are done with Ac
-        for (int e2 = threadIdx.x; e2 < 32 * 8; e2 += kThreads) {
+        for (int e2 = threadIdx.x; e2 < kLeRC * 8; e2 += kThreads) {
           const int r = e2 / 8, q = 2 * (e2 % 8), ra = rc + r;
           double x0 = 0.0, x1 = 0.0;
           if (ra < rb) {
@@ -1492,10 +1493,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
           unsigned w[kEmuSlices];
           emu_split2(x0, x1, l0 < jb ? eY[l0] : 0, l1 < jb ? eY[l1] : 0, w);
 #pragma unroll
-          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Ac + (p * 32 + r) * kLeLdC + q) = w[p];
+          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Ac + (p * kLeRC + r) * kLeLdC + q) = w[p];
         }
         __syncthreads();
-        for (int tile = warp; tile < 2 * NT; tile += NW) {
+        for (int tile = warp; tile < (kLeRC / 16) * NT; tile += NW) {
           const int mt = tile / NT, nt = tile % NT;
           const bool imag = C && nt * 8 >= kpc;
           const int jb0 = imag ? nt * 8 - kpc : nt * 8;
@@ -1518,7 +1519,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) {
             unsigned a[4];
-            ld_afrag<kLeLdC>(Ac + (p * 32) * kLeLdC, mt * 16, 0, a);
+            ld_afrag<kLeLdC>(Ac + (p * kLeRC) * kLeLdC, mt * 16, 0, a);
 #pragma unroll
             for (int qq = 0; qq < kEmuSlices; ++qq) {
               if (p + qq > kEmuLevels - 1) continue;

@@ -59,7 +59,7 @@ typedef enum {
   THO_ERR_TIMEOUT = 6,     /* a bounded device-side wait of a tcgen05 kernel ran   *
                             * out (results invalid); latched like NONFINITE        */
   THO_ERR_NONFINITE = 7,   /* device check found NaN/Inf (THO_FLAG_CHECK_FINITE)   */
-  THO_ERR_UNSUPPORTED = 8  /* shape or mode beyond what this build implements      */
+  THO_ERR_UNSUPPORTED = 8  /* shape or mode beyond what the library implements    */
 } tho_status_t;
 
 typedef enum { THO_F64 = 0, THO_C128 = 1 } tho_dtype_t;

@@ -170,7 +170,7 @@ const char* tho_status_string(tho_status_t s) {
     case THO_ERR_CUDA: return "CUDA runtime error";
     case THO_ERR_TIMEOUT: return "device wait timed out";
     case THO_ERR_NONFINITE: return "non-finite value detected on the device";
-    case THO_ERR_UNSUPPORTED: return "shape or mode not supported by this build";
+    case THO_ERR_UNSUPPORTED: return "shape or mode not supported by the library";
   }
   return "unknown status";
 }

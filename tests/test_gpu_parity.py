@@ -184,21 +184,24 @@ def test_batched_matches_oracle(tho, dtype):
         assert torch.equal(Q, Q2)
 
 
-def test_batched_c4_workload(tho):
-    """The 256-problem batched workload (n log-uniform in [16384, 262144]): every
-    problem meets LOO and residual <= 1e-13 and matches the looped tho_orth."""
+@pytest.mark.parametrize("prec_name", ["THO_PREC_FP64", "THO_PREC_FP64_EMU"])
+def test_batched_c4_workload(tho, prec_name):
+    """The 256-problem batched workload (n log-uniform in [16384, 262144]), in
+    both FP64-accurate modes: every problem meets LOO and residual <= 1e-13 and
+    matches the looped tho_orth."""
     from gpu_metrics import loo, resid_fro
+    prec = getattr(tho, prec_name)
     shapes = inputs.batched_shapes()
     probs = inputs.batched_problems(shapes, device="cuda")
     pairs = [(p.V, p.A) for p in probs]
-    res = tho.orth_batched(pairs)
+    res = tho.orth_batched(pairs, prec=prec)
     torch.cuda.synchronize()
     worst = 0.0
     for i, (p, (Q, R, S)) in enumerate(zip(probs, res)):
         assert loo(p.V, Q) < TOL_LOO, i
         assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO, i
         if i % 16 == 0:
-            Ql, _, _ = tho.orth(p.V, p.A)
+            Ql, _, _ = tho.orth(p.V, p.A, prec=prec)
             worst = max(worst, float((Ql - Q).abs().max()))
     assert worst < TOL_Q
 

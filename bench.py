@@ -64,6 +64,9 @@ WORKLOADS = {
     "c4": (4, 0, 0, 0, "float64", 0,
            "batched: 256 real problems, n log-uniform in [16384, 262144], k0 in {8..128}, k in {4..32}, "
            "one graph replay vs 256 looped tho_orth calls"),
+    "blocks": (6, 1 << 20, 0, 16, "float64", 2,
+               "Algorithm 3 (block Householder-QR): real n=2^20, eight blocks of 16 columns, block-Krylov input "
+               "A_{i+1} = D A_i (cond > 1e12); FP64-accurate products on bf16 tensor cores"),
     "c4-emu": (4, 0, 0, 0, "float64", 2,
                "batched: the 256 real problems of c4 with FP64-accurate products on bf16 tensor cores, "
                "one graph replay vs 256 looped tho_orth calls"),
@@ -266,7 +269,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if ws > 1 and rank != 0:
         return 0
-    if args.workload in ("c4", "c4-emu", "c5"):
+    if args.workload in ("c4", "c4-emu", "c5", "blocks"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-problem "
                           "workloads c1, c2, c3"}), flush=True)
         return 0
@@ -297,6 +300,72 @@ def run_reference(args):
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_blocks(args):
+    """Algorithm 3: tho_orth_blocks over eight blocks of 16 columns (k0 = 0, 16,
+    ..., 112 in its eight Algorithm 1 steps) on a block-Krylov matrix."""
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2602_14449_gb300 import inputs, tho
+    tho.load()
+    _, n, _, k, _, prec, desc = WORKLOADS["blocks"]
+    if args.rows:
+        n = args.rows
+    nb = 8
+    g = torch.Generator().manual_seed(1449 + 6)
+    d = torch.exp(torch.linspace(0.0, 4.0, n, dtype=torch.float64))
+    blocks = [torch.randn(n, k, generator=g, dtype=torch.float64)]
+    for _ in range(nb - 1):
+        blocks.append(d[:, None] * blocks[-1])
+    A = inputs.colmajor(torch.cat(blocks, dim=1)).to(dev)
+    del blocks
+    K = k * nb
+    blk = tho.Blocks(n, [k] * nb, torch.float64, prec)
+    Q = torch.empty_strided((n, K), (1, n), dtype=torch.float64, device=dev)
+    R = torch.empty_strided((K, K), (1, K), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        blk.orth(A, Q, R)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev.index)).split(",")[0] if ws == 1 else str(local)
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        blk.orth(A, Q, R)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+    B = sum(b_alg(n, i * k, k, False) for i in range(nb))
+    F = sum(f_alg(n, i * k, k, False) for i in range(nb))
+    I = torch.eye(K, dtype=torch.float64, device=dev)
+    check = {"loo": float(torch.linalg.matrix_norm(Q.T @ Q - I, ord=2)),
+             "resid_fro": float(torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A))}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": B * ws / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (fp64-accurate; products on bf16 tensor cores)", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "blocks": [k] * nb, "B_alg": B, "F_alg": F,
+                       "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "tflops": F / (ms * 1e-3) / 1e12, "clocks": clocks, "check": check,
+            "gpu_launches": blk.kernel_launches * args.steps,
+        }
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -712,6 +781,8 @@ def main():
         return run_reference(args)
     if args.workload in ("c4", "c4-emu"):
         return run_batched(args)
+    if args.workload == "blocks":
+        return run_blocks(args)
     if args.workload == "c5":
         return run_adjoint(args)
     return run_gpu(args)

@@ -239,6 +239,29 @@ tho_status_t tho_orth_noalloc(const tho_desc_t* desc, const void* V, int64_t ldv
  * Returns THO_OK or the first device-detected error (THO_ERR_NONFINITE). */
 tho_status_t tho_plan_status(tho_plan_t plan);
 
+/* Block Householder-QR (Algorithm 3, Section 5): the QR factorization
+ * A = Q R of A = [A_1, ..., A_p], A_i of kb[i] columns, the blocks taken in
+ * order as in block Krylov methods.  Step 1 is the Householder QR of A_1 (the
+ * k0 = 0 case of Algorithm 1); step i >= 2 is Algorithm 1 with
+ * V = [Q_1, ..., Q_{i-1}] (k0 = kb[0] + ... + kb[i-2]) and A = A_i, giving Q_i,
+ * the diagonal block R_ii and the block above it, R_{1:i-1, i} = S.
+ *   n      rows, K = kb[0] + ... + kb[p-1] <= n
+ *   kb[i]  1 <= kb[i] <= THO_MAX_K, and K - kb[p-1] <= THO_MAX_K0
+ *   A      n x K, lda >= n (device, column-major)
+ *   Q      n x K, ldq >= n, output; must not overlap A
+ *   R      K x K, ld = K, output: upper block triangular, zero below the
+ *          diagonal blocks (diag(R) real >= 0)
+ * The block plan owns one tho_plan per step and small device buffers.
+ * Asynchronous on `stream`.  Errors: ARG, SHAPE, UNSUPPORTED, NOMEM, ALIGN, CUDA. */
+typedef struct tho_blocks_s* tho_blocks_t;
+tho_status_t tho_blocks_plan(int64_t n, const int32_t* kb, int32_t p, int32_t dtype, int32_t prec,
+                             tho_blocks_t* out);
+tho_status_t tho_blocks_destroy(tho_blocks_t blocks);
+tho_status_t tho_orth_blocks(tho_blocks_t blocks, const void* A, int64_t lda, void* Q, int64_t ldq, void* R,
+                             void* stream);
+/* Kernel launches one tho_orth_blocks call issues (the steps' plans summed); 0 for NULL. */
+int32_t tho_blocks_kernel_launches(tho_blocks_t blocks);
+
 /* Static English description of a status code. */
 const char* tho_status_string(tho_status_t status);
 

@@ -19,6 +19,9 @@ Every function here is pinned in ``tests/test_oracle.py``:
   * ``householder_qr`` — LAPACK QR after phase normalization.
   * ``bcgs``           — Table 1 first row (loss of orthogonality ~ 1) and the
                          three-projection rows (~ u) on the worked example.
+  * ``block_hhqr``     — Algorithm 3: the unique QR with real nonnegative
+                         diag(R) of a full-rank A by LAPACK (phase-normalized),
+                         for several block splittings; Q^* Q = I, A = Q R.
 """
 from __future__ import annotations
 
@@ -127,6 +130,32 @@ def householder_qr(X):
     fn = _load().oracle_householder_qr_c128 if dt == np.complex128 else _load().oracle_householder_qr_f64
     if fn(m, k, _ptr(X), m, _ptr(Q), m, _ptr(R)) != 0:
         raise ValueError("householder_qr needs m >= k >= 1")
+    return Q, R
+
+
+def block_hhqr(A, kb):
+    """Algorithm 3 (Block Householder-QR, Section 5): the QR factorization of
+    A = [A_1, ..., A_p] (block widths kb) taking the blocks in order.  Step 1
+    is the Householder QR of A_1; step i >= 2 is Algorithm 1 with
+    V = [Q_1, ..., Q_{i-1}] and A = A_i, whose Q, R and S give Q_i, the
+    diagonal block R_ii and the block above it, R_{1:i-1, i}.  Returns (Q, R)."""
+    dt = _dtype_of(A)
+    A = _fortran(A, dt)
+    n, K = A.shape
+    if sum(kb) != K:
+        raise ValueError("block widths must add up to the columns of A")
+    Q = np.zeros((n, K), dtype=dt, order="F")
+    R = np.zeros((K, K), dtype=dt, order="F")
+    o = 0
+    for i, k in enumerate(kb):
+        if i == 0:
+            Qi, Rii = householder_qr(A[:, :k])
+        else:
+            Qi, Rii, S = two_stage(Q[:, :o], A[:, o:o + k])
+            R[:o, o:o + k] = S
+        Q[:, o:o + k] = Qi
+        R[o:o + k, o:o + k] = Rii
+        o += k
     return Q, R
 
 

@@ -575,4 +575,104 @@ tho_status_t tho_plan_status(tho_plan_t plan) {
   return (tho_status_t)h;
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 3 (Block Householder-QR): one Algorithm 1 plan per block.
+}  // extern "C"
+
+struct tho_blocks_s {
+  int64_t n = 0;
+  int p = 0, K = 0;
+  size_t elem = 0;
+  std::vector<int> kb, off;  // block widths and first columns
+  std::vector<tho_plan_t> plans;
+  void* tmp = nullptr;  // R_ii (kb x kb) then S_i (k0 x kb) of the current step
+};
+
+extern "C" {
+
+tho_status_t tho_blocks_destroy(tho_blocks_t b) {
+  if (!b) return THO_OK;
+  for (tho_plan_t pl : b->plans) tho_plan_destroy(pl);
+  if (b->tmp) cudaFree(b->tmp);
+  delete b;
+  return THO_OK;
+}
+
+tho_status_t tho_blocks_plan(int64_t n, const int32_t* kb, int32_t p, int32_t dtype, int32_t prec,
+                             tho_blocks_t* out) {
+  if (!kb || !out || p < 1) return THO_ERR_ARG;
+  *out = nullptr;
+  int64_t K = 0;
+  for (int i = 0; i < p; ++i) {
+    if (kb[i] < 1 || kb[i] > THO_MAX_K) return THO_ERR_UNSUPPORTED;
+    if (K > THO_MAX_K0) return THO_ERR_UNSUPPORTED;  // k0 of step i
+    K += kb[i];
+  }
+  if (K > n) return THO_ERR_SHAPE;
+  tho_blocks_s* b = new (std::nothrow) tho_blocks_s();
+  if (!b) return THO_ERR_NOMEM;
+  b->n = n;
+  b->p = p;
+  b->K = (int)K;
+  b->elem = dtype == THO_C128 ? 16 : 8;
+  int maxk = 0, o = 0;
+  for (int i = 0; i < p; ++i) {
+    b->kb.push_back(kb[i]);
+    b->off.push_back(o);
+    tho_desc_t d{n, o, kb[i], dtype, prec, i == 0 ? (uint32_t)THO_FLAG_ALLOW_K0_ZERO : 0u};
+    tho_plan_t pl = nullptr;
+    tho_status_t s = tho_plan(&d, 1, &pl);
+    if (s != THO_OK) {
+      tho_blocks_destroy(b);
+      return s;
+    }
+    b->plans.push_back(pl);
+    o += kb[i];
+    maxk = std::max(maxk, (int)kb[i]);
+  }
+  const size_t bytes = (size_t)(maxk * maxk + (K - kb[p - 1]) * maxk + 1) * b->elem;
+  if (cudaMalloc(&b->tmp, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    tho_blocks_destroy(b);
+    return THO_ERR_NOMEM;
+  }
+  *out = b;
+  return THO_OK;
+}
+
+int32_t tho_blocks_kernel_launches(tho_blocks_t b) {
+  if (!b) return 0;
+  int32_t n = 0;
+  for (tho_plan_t pl : b->plans) n += tho_plan_kernel_launches(pl);
+  return n;
+}
+
+tho_status_t tho_orth_blocks(tho_blocks_t b, const void* A, int64_t lda, void* Q, int64_t ldq, void* R,
+                             void* stream) {
+  if (!b || !A || !Q || !R || lda < b->n || ldq < b->n) return THO_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t el = b->elem;
+  const int64_t K = b->K;
+  if (cudaMemsetAsync(R, 0, (size_t)(K * K) * el, st) != cudaSuccess) return THO_ERR_CUDA;
+  char* Rb = static_cast<char*>(R);
+  for (int i = 0; i < b->p; ++i) {
+    const int64_t k0 = b->off[i], k = b->kb[i];
+    char* Rt = static_cast<char*>(b->tmp);
+    char* St = Rt + (size_t)(k * k) * el;
+    const void* Ai = static_cast<const char*>(A) + (size_t)(k0 * lda) * el;
+    void* Qi = static_cast<char*>(Q) + (size_t)(k0 * ldq) * el;
+    tho_status_t s = tho_orth(b->plans[i], k0 > 0 ? Q : nullptr, ldq, Ai, lda, Qi, ldq, Rt, k0 > 0 ? St : nullptr,
+                              stream);
+    if (s != THO_OK) return s;
+    // R_ii at rows/columns k0.., and R_{1:i-1, i} = S above it.
+    if (cudaMemcpy2DAsync(Rb + (size_t)(k0 + k0 * K) * el, (size_t)K * el, Rt, (size_t)k * el, (size_t)k * el,
+                          (size_t)k, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return THO_ERR_CUDA;
+    if (k0 > 0 && cudaMemcpy2DAsync(Rb + (size_t)(k0 * K) * el, (size_t)K * el, St, (size_t)k0 * el,
+                                    (size_t)k0 * el, (size_t)k, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return THO_ERR_CUDA;
+  }
+  return THO_OK;
+}
+
 }  // extern "C"

@@ -29,6 +29,7 @@ THO_MAX_K0, THO_MAX_K = 128, 32
 
 EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",
             "tho_plan_leaf_rows", "tho_orth_host", "tho_orth_host_wait",
+            "tho_blocks_plan", "tho_blocks_destroy", "tho_orth_blocks", "tho_blocks_kernel_launches",
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
             "tho_orth_noalloc")
@@ -84,6 +85,14 @@ def load(path: str | None = None):
         lib.tho_orth_host.restype = ctypes.c_int
         lib.tho_orth_host_wait.argtypes = [vp, vp]
         lib.tho_orth_host_wait.restype = ctypes.c_int
+        lib.tho_blocks_plan.argtypes = [i64, ctypes.POINTER(i32), i32, i32, i32, ctypes.POINTER(vp)]
+        lib.tho_blocks_plan.restype = ctypes.c_int
+        lib.tho_blocks_destroy.argtypes = [vp]
+        lib.tho_blocks_destroy.restype = ctypes.c_int
+        lib.tho_orth_blocks.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+        lib.tho_orth_blocks.restype = ctypes.c_int
+        lib.tho_blocks_kernel_launches.argtypes = [vp]
+        lib.tho_blocks_kernel_launches.restype = ctypes.c_int32
         lib.tho_orth_batched.argtypes = [vp, ctypes.POINTER(Instance), i32, vp]
         lib.tho_orth_batched.restype = ctypes.c_int
         lib.tho_orth_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp]
@@ -284,6 +293,51 @@ def orth_host_wait(plan: Plan):
     """Make the current torch stream wait for every orth_host output copy of ``plan``."""
     st = torch.cuda.current_stream().cuda_stream
     _check(load().tho_orth_host_wait(plan.handle, ctypes.c_void_p(st)), "tho_orth_host_wait")
+
+
+class Blocks:
+    """tho_blocks_t: Block Householder-QR (Algorithm 3) of n x K matrices whose
+    columns come in blocks of widths ``kb`` (one Algorithm 1 plan per block)."""
+
+    def __init__(self, n: int, kb, dtype: torch.dtype, prec: int = THO_PREC_FP64):
+        lib = load()
+        self.n, self.kb, self.dtype, self.prec = n, list(kb), dtype, prec
+        self.K = sum(self.kb)
+        arr = (ctypes.c_int32 * len(self.kb))(*self.kb)
+        h = ctypes.c_void_p()
+        _check(lib.tho_blocks_plan(n, arr, len(self.kb), _dtype_code(dtype), prec, ctypes.byref(h)), "tho_blocks_plan")
+        self.handle = h
+
+    @property
+    def kernel_launches(self) -> int:
+        return load().tho_blocks_kernel_launches(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.tho_blocks_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def orth(self, A: torch.Tensor, Q: torch.Tensor | None = None, R: torch.Tensor | None = None):
+        """Q (n x K) and R (K x K, upper block triangular) with A = Q R, on the current stream."""
+        n, K = A.shape
+        if n != self.n or K != self.K or A.dtype != self.dtype:
+            raise ValueError("A does not match the block plan")
+        if Q is None:
+            Q = _empty_cm(n, K, A.dtype, A.device)
+        if R is None:
+            R = _empty_cm(K, K, A.dtype, A.device)
+        if R.stride(0) != 1 or (K > 1 and R.stride(1) != K):
+            raise ValueError("R must be column-major with ld = K")
+        st = torch.cuda.current_stream().cuda_stream
+        _check(load().tho_orth_blocks(self.handle, _ptr(A), _ld(A, "A"), _ptr(Q), _ld(Q, "Q"), _ptr(R),
+                                      ctypes.c_void_p(st)), "tho_orth_blocks")
+        return Q, R
 
 
 def orth_batched(pairs, prec: int = THO_PREC_FP64, plan: Plan | None = None, outs=None):

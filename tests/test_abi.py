@@ -94,3 +94,20 @@ def test_binding_fails_loudly_without_library(tmp_path):
             tho_mod.load(str(tmp_path / "missing.so"))
     finally:
         tho_mod._lib = saved
+
+
+def test_block_plan_argument_errors(lib):
+    """tho_blocks_plan rejects bad block lists before touching the device."""
+    h = ctypes.c_void_p()
+
+    def plan(n, kb):
+        arr = (ctypes.c_int32 * len(kb))(*kb)
+        return lib.tho_blocks_plan(n, arr, len(kb), tho.THO_F64, tho.THO_PREC_FP64, ctypes.byref(h))
+
+    assert lib.tho_blocks_plan(100, None, 1, 0, 0, ctypes.byref(h)) == tho.THO_ERR_ARG
+    assert plan(100, []) == tho.THO_ERR_ARG
+    assert plan(1000, [8, 33]) == tho.THO_ERR_UNSUPPORTED      # a block wider than THO_MAX_K
+    assert plan(1000, [0, 8]) == tho.THO_ERR_UNSUPPORTED
+    assert plan(1000, [64, 65, 8]) == tho.THO_ERR_UNSUPPORTED  # the last step's k0 = 129 > THO_MAX_K0
+    assert plan(20, [16, 16]) == tho.THO_ERR_SHAPE             # K > n
+    assert lib.tho_blocks_destroy(None) == tho.THO_OK

@@ -308,3 +308,40 @@ def test_orth_host_k0_zero(tho):
     Qo, Ro = oracle.householder_qr(p.A.numpy())
     np.testing.assert_allclose(hQ.numpy(), Qo, atol=TOL_Q)
     np.testing.assert_allclose(hR.numpy(), Ro, atol=TOL_Q * np.abs(Ro).max())
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("prec_name", ["THO_PREC_FP64", "THO_PREC_FP64_EMU"])
+@pytest.mark.parametrize("kb", [[4, 7, 16, 3], [32, 32, 32, 32, 32]])
+def test_blocks_match_oracle(tho, dtype, prec_name, kb):
+    """Algorithm 3 (tho_orth_blocks): ragged block widths, and five blocks of 32
+    (the last step at k0 = THO_MAX_K0), against the oracle's Algorithm 3."""
+    n = 3000
+    p = inputs.random_problem(n, 0, sum(kb), dtype=dtype, seed=90 + len(kb))
+    blk = tho.Blocks(n, kb, dtype, getattr(tho, prec_name))
+    Q, R = blk.orth(p.A.cuda())
+    torch.cuda.synchronize()
+    Qo, Ro = oracle.block_hhqr(p.A.numpy(), kb)
+    np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+    np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=TOL_Q * np.abs(Ro).max())
+
+
+@pytest.mark.parametrize("prec_name", ["THO_PREC_FP64", "THO_PREC_FP64_EMU"])
+def test_blocks_ill_conditioned_krylov(tho, prec_name):
+    """Block Krylov-style A (A_{i+1} = D A_i, cond far beyond 1e10) at n = 2^18,
+    eight blocks of 16: orthogonality and residual at the rounding level."""
+    n, k, nb = 1 << 18, 16, 8
+    g = torch.Generator().manual_seed(5)
+    d = torch.exp(torch.linspace(0.0, 4.0, n, dtype=torch.float64))
+    blocks = [torch.randn(n, k, generator=g, dtype=torch.float64)]
+    for _ in range(nb - 1):
+        blocks.append(d[:, None] * blocks[-1])
+    A = inputs.colmajor(torch.cat(blocks, dim=1)).cuda()
+    blk = tho.Blocks(n, [k] * nb, torch.float64, getattr(tho, prec_name))
+    Q, R = blk.orth(A)
+    torch.cuda.synchronize()
+    K = k * nb
+    I = torch.eye(K, dtype=torch.float64, device="cuda")
+    assert float(torch.linalg.matrix_norm(Q.T @ Q - I, ord=2)) < TOL_LOO
+    assert float(torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)) < TOL_LOO
+    assert float(torch.tril(R, -1).abs().max()) == 0.0

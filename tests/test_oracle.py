@@ -253,3 +253,36 @@ def test_householder_qr_rank_deficient_columns():
 def test_oracle_rejects_bad_shapes():
     with pytest.raises(ValueError):
         oracle.two_stage(np.zeros((4, 3)), np.zeros((4, 2)))  # k0 + k > n
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("kb", [[5], [3, 4], [4, 7, 1, 6], [1, 1, 1, 1, 1, 1]])
+def test_block_hhqr_is_the_unique_qr(dtype, kb):
+    """Algorithm 3 on a full-rank A: the unique QR with real nonnegative diag(R)
+    (LAPACK, phase-normalized), whatever the block splitting."""
+    p = inputs.random_problem(300, 0, sum(kb), dtype=dtype, seed=31 + len(kb))
+    A = _np(p.A)
+    Q, R = oracle.block_hhqr(A, kb)
+    Qc, Rc = qf(A)
+    np.testing.assert_allclose(Q, Qc, atol=1e-13)
+    np.testing.assert_allclose(R, Rc, atol=1e-12)
+    assert np.abs(np.tril(R, -1)).max() == 0.0
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(sum(kb)), atol=1e-14)
+    np.testing.assert_allclose(Q @ R, A, atol=1e-13 * np.abs(A).max())
+
+
+def test_block_hhqr_ill_conditioned_krylov():
+    """Block Krylov-style blocks A_{i+1} = D A_i (spread spectrum D): the whole
+    matrix is ill-conditioned, and Algorithm 3 keeps orthogonality at the
+    rounding level (the stability of Section 5's example)."""
+    rng = np.random.default_rng(7)
+    n, k, p = 400, 4, 6
+    d = np.exp(np.linspace(0.0, 6.0, n))
+    blocks = [rng.standard_normal((n, k))]
+    for _ in range(p - 1):
+        blocks.append(d[:, None] * blocks[-1])
+    A = np.hstack(blocks)
+    assert np.linalg.cond(A) > 1e8
+    Q, R = oracle.block_hhqr(A, [k] * p)
+    assert np.linalg.norm(Q.T @ Q - np.eye(k * p), 2) < 1e-14
+    assert np.linalg.norm(A - Q @ R, "fro") / np.linalg.norm(A, "fro") < 1e-14

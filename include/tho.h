@@ -82,6 +82,11 @@ typedef enum { THO_PREC_FP64 = 0, THO_PREC_FP32_BULK = 1, THO_PREC_FP64_EMU = 2 
 #define THO_FLAG_ALLOW_K0_ZERO 0x1u /* k0 = 0: plain Householder QR of A        */
 #define THO_FLAG_CHECK_FINITE 0x2u  /* latch THO_ERR_NONFINITE if G, R or Z2    */
                                     /* contain NaN/Inf (read via tho_plan_status) */
+/* The first choice of P (Section 3.2): P diagonal, determined on the fly by the
+ * modified LU factorization of P - V_{1:k0,:} (Algorithm 2), T = (P - V_1)^* P
+ * applied through the L and U factors.  Without it: the second choice,
+ * P = -Q_1 from the QR of V_{1:k0,:}.  Not for tho_orth_backward. */
+#define THO_FLAG_P_MLU 0x4u
 
 /* One orthogonalization problem: V is n x k0, A is n x k. */
 typedef struct {

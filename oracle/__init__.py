@@ -19,6 +19,13 @@ Every function here is pinned in ``tests/test_oracle.py``:
   * ``householder_qr`` — LAPACK QR after phase normalization.
   * ``bcgs``           — Table 1 first row (loss of orthogonality ~ 1) and the
                          three-projection rows (~ u) on the worked example.
+  * ``modified_lu``, ``two_stage_mlu`` — Algorithm 2 and Algorithm 1 with the
+                         first choice of P: P - V_1 = L U with |U_ii| >= 1,
+                         T = (P - V_1)^* P; Q, R, S equal the closed form
+                         (they do not depend on P) and the second choice's.
+  * ``two_stage_polar`` — Algorithm 1 with the third choice of P: V_1 = Q2 M,
+                         T = I + M Hermitian positive definite with
+                         kappa_2(T) <= 2; Q, R, S equal the closed form.
   * ``block_hhqr``     — Algorithm 3: the unique QR with real nonnegative
                          diag(R) of a full-rank A by LAPACK (phase-normalized),
                          for several block splittings; Q^* Q = I, A = Q R.
@@ -131,6 +138,103 @@ def householder_qr(X):
     if fn(m, k, _ptr(X), m, _ptr(Q), m, _ptr(R)) != 0:
         raise ValueError("householder_qr needs m >= k >= 1")
     return Q, R
+
+
+def modified_lu(Z):
+    """Algorithm 2 (modified LU factorization): for Z (k x k, ||Z||_2 <= 1),
+    a diagonal unitary P and the LU factorization P - Z = L U (L unit lower,
+    U upper triangular) with P's entries chosen on the fly, P_ii = -sign(Z_ii)
+    (sign(mu) = 1 if Re mu >= 0 else -1), so that |U_ii| >= 1 without pivoting.
+    Plain loops in the algorithm's order.  Returns (P, L, U)."""
+    Z = np.array(Z, dtype=np.result_type(Z, np.float64), copy=True)
+    k = Z.shape[0]
+    P = np.eye(k, dtype=Z.dtype)
+    L = np.eye(k, dtype=Z.dtype)
+    U = np.zeros((k, k), dtype=Z.dtype)
+    for i in range(k):
+        P[i, i] = -1.0 if Z[i, i].real >= 0 else 1.0
+        U[i, i] = P[i, i] - Z[i, i]
+        for j in range(i + 1, k):
+            U[i, j] = -Z[i, j]
+        for r in range(i + 1, k):
+            L[r, i] = -Z[r, i] / U[i, i]
+        for r in range(i + 1, k):
+            for j in range(i + 1, k):
+                Z[r, j] = Z[r, j] + L[r, i] * U[i, j]
+    return P, L, U
+
+
+def _tri(M, B, lower):
+    """Substitution with the triangular M (plain loops, no explicit inverse)."""
+    n = M.shape[0]
+    X = np.zeros(B.shape, dtype=np.result_type(M, B))
+    order = range(n) if lower else range(n - 1, -1, -1)
+    for i in order:
+        acc = B[i].astype(X.dtype)
+        for j in (range(i) if lower else range(i + 1, n)):
+            acc = acc - M[i, j] * X[j]
+        X[i] = acc / M[i, i]
+    return X
+
+
+def two_stage_mlu(V, A):
+    """Algorithm 1 with the first choice of P (Section 3.2): P diagonal from the
+    modified LU factorization of P - V_{1:k0,:} (Algorithm 2), T = I - V_1^* P
+    = (P - V_1)^* P = U^* L^* P, so T^{-*} G = U^{-1} L^{-1} (P G) and
+    T^{-1} G_2 = P^* L^{-*} U^{-*} G_2 by triangular substitution.  The trailing
+    QR is the oracle's Householder QR.  Returns (Q, R, S, aux) with aux the
+    dict of P, L, U, T, Wtop, G, Z, Z2."""
+    dt = _dtype_of(V, A)
+    V = np.asarray(V, dtype=dt)
+    A = np.asarray(A, dtype=dt)
+    n, k = A.shape
+    k0 = V.shape[1]
+    V1, V2 = V[:k0], V[k0:]
+    P, L, U = modified_lu(V1)
+    Wtop = P - V1                      # W = [P; 0] - V
+    T = np.eye(k0) - V1.conj().T @ P
+    G = Wtop.conj().T @ A[:k0] - V2.conj().T @ A[k0:]
+    Z = _tri(U, _tri(L, P @ G, lower=True), lower=False)       # T^{-*} G
+    A1 = A[:k0] - Wtop @ Z                                       # A <- A - W T^{-*} W^* A
+    A2 = A[k0:] + V2 @ Z
+    S = P.conj().T @ A1
+    Qb, R = householder_qr(A2)
+    G2 = -V2.conj().T @ Qb                                       # W^* [0; Qbar]
+    Z2 = P.conj().T @ _tri(L.conj().T, _tri(U.conj().T, G2, lower=True), lower=False)  # T^{-1} G2
+    Q = np.vstack([-Wtop @ Z2, Qb + V2 @ Z2])
+    return Q, R, S, {"P": P, "L": L, "U": U, "T": T, "Wtop": Wtop, "G": G, "Z": Z, "Z2": Z2}
+
+
+def two_stage_polar(V, A):
+    """Algorithm 1 with the third choice of P (Section 3.2): the polar
+    decomposition V_{1:k0,:} = Q2 M (from the SVD, a library step: V_1 = X S Y^*,
+    Q2 = X Y^*, M = Y S Y^*), P = -Q2, so T = I - V_1^* P = I + M is Hermitian
+    positive definite with kappa_2(T) <= 2; T^{-*} = T^{-1} is applied through
+    its Cholesky factor T = C C^* by triangular substitution.  Returns
+    (Q, R, S, aux) with aux the dict of P, M, T, C, Wtop, G, Z, Z2."""
+    dt = _dtype_of(V, A)
+    V = np.asarray(V, dtype=dt)
+    A = np.asarray(A, dtype=dt)
+    n, k = A.shape
+    k0 = V.shape[1]
+    V1, V2 = V[:k0], V[k0:]
+    X, sv, Yh = np.linalg.svd(V1)
+    Q2 = X @ Yh
+    M = Yh.conj().T @ np.diag(sv) @ Yh
+    P = -Q2
+    Wtop = P - V1
+    T = np.eye(k0) - V1.conj().T @ P
+    C = np.linalg.cholesky(0.5 * (T + T.conj().T))
+    solve = lambda B: _tri(C.conj().T, _tri(C, B, lower=True), lower=False)  # T^{-1} B
+    G = Wtop.conj().T @ A[:k0] - V2.conj().T @ A[k0:]
+    Z = solve(G)                                                  # T^{-*} = T^{-1}
+    A1 = A[:k0] - Wtop @ Z
+    A2 = A[k0:] + V2 @ Z
+    S = P.conj().T @ A1
+    Qb, R = householder_qr(A2)
+    Z2 = solve(-V2.conj().T @ Qb)
+    Q = np.vstack([-Wtop @ Z2, Qb + V2 @ Z2])
+    return Q, R, S, {"P": P, "M": M, "T": T, "C": C, "Wtop": Wtop, "G": G, "Z": Z, "Z2": Z2}
 
 
 def block_hhqr(A, kb):

@@ -55,7 +55,7 @@ tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
   if (d.dtype != d0.dtype || d.prec != d0.prec || d.flags != d0.flags) return THO_ERR_ARG;
   if (d.dtype != THO_F64 && d.dtype != THO_C128) return THO_ERR_ARG;
   if (d.prec != THO_PREC_FP64 && d.prec != THO_PREC_FP32_BULK && d.prec != THO_PREC_FP64_EMU) return THO_ERR_ARG;
-  if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE)) return THO_ERR_ARG;
+  if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE | THO_FLAG_P_MLU)) return THO_ERR_ARG;
   if (d.k < 1 || d.k0 < 0 || d.n < 1) return THO_ERR_SHAPE;
   if (d.k0 == 0 && !(d.flags & THO_FLAG_ALLOW_K0_ZERO)) return THO_ERR_SHAPE;
   if (d.k0 + d.k > d.n) return THO_ERR_SHAPE;
@@ -541,7 +541,8 @@ tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, cons
                                int64_t lddv, void* dA, int64_t ldda, void* stream) {
   if (!plan || plan->pc.count != 1) return THO_ERR_ARG;
   const Inst& I = plan->pc.h_insts[0];
-  if (plan->pc.dtype != THO_F64 || plan->pc.prec != THO_PREC_FP64 || I.k0 < 1) return THO_ERR_UNSUPPORTED;
+  if (plan->pc.dtype != THO_F64 || plan->pc.prec != THO_PREC_FP64 || I.k0 < 1 || (plan->pc.flags & THO_FLAG_P_MLU))
+    return THO_ERR_UNSUPPORTED;
   if (!V || !A || !Q || !dQ || !dV || !dA) return THO_ERR_ARG;
   if (ldv < I.n || lda < I.n || ldq < I.n || lddq < I.n || lddv < I.n || ldda < I.n) return THO_ERR_ARG;
   for (const void* p : {V, A, Q, dQ, (const void*)dV, (const void*)dA})

@@ -204,7 +204,8 @@ __device__ __forceinline__ void make_reflector(double nrm2, S xj, double& beta, 
 // latency-bound, so every warp takes a column of each trailing update.
 constexpr int kV1Threads = 1024;
 template <class S>
-__global__ void __launch_bounds__(kV1Threads) k_v1qr(const Inst* insts, const Io* iot, Io io0, void* ws) {
+__global__ void __launch_bounds__(kV1Threads) k_v1qr(const Inst* insts, const Io* iot, Io io0, void* ws,
+                                                     uint32_t flags = 0) {
   const int inst = blockIdx.x;
   const Inst& I = insts[inst];
   const int k0 = (int)I.k0;
@@ -226,6 +227,47 @@ __global__ void __launch_bounds__(kV1Threads) k_v1qr(const Inst* insts, const Io
     X[e] = V[i + (int64_t)j * io.ldv];
   }
   __syncthreads();
+  if (flags & 0x4u) {  // THO_FLAG_P_MLU
+    // First choice of P: the modified LU factorization of P - V_1 (Algorithm
+    // 2), P_ii = -sign(Z_ii) chosen at step i (sign = 1 for Re >= 0), so that
+    // |U_ii| >= 1 and no pivoting is needed; X holds the running Z.  Stored:
+    // Q1 = -P (so that Wtop = -Q1 - V_1 = P - V_1 and S = -Q1^* A'_1 as for the
+    // second choice), T = L (unit lower), R1 = U (upper).
+    __shared__ double psh[kMaxK0];
+    for (int e = threadIdx.x; e < k0 * k0; e += kV1Threads) {
+      R1[e] = zero<S>();
+      T[e] = from_real<S>((e % k0) == (e / k0) ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int i = 0; i < k0; ++i) {
+      if (threadIdx.x == 0) {
+        const double pi = real_(X[i + i * k0]) >= 0.0 ? -1.0 : 1.0;
+        psh[i] = pi;
+        R1[i + i * k0] = sub(from_real<S>(pi), X[i + i * k0]);
+      }
+      __syncthreads();
+      const S u = R1[i + i * k0];
+      const S uinv = scale(conj_(u), 1.0 / abs2d(u));  // |u| >= 1
+      const int w = k0 - 1 - i;
+      for (int e = threadIdx.x; e < 2 * w; e += kV1Threads) {
+        const int c = i + 1 + (e % w);
+        if (e < w) R1[i + c * k0] = neg(X[i + c * k0]);          // U(i, c) = -Z(i, c)
+        else T[c + i * k0] = neg(mul(X[c + i * k0], uinv));      // L(c, i) = -Z(c, i) / U(i, i)
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < w * w; e += kV1Threads) {
+        const int r = i + 1 + (e % w), c = i + 1 + (e / w);
+        X[r + c * k0] = madd(X[r + c * k0], T[r + i * k0], R1[i + c * k0]);  // Z += L U
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < k0 * k0; e += kV1Threads) {
+      const int i = e % k0, j = e / k0;
+      Q1[e] = from_real<S>(i == j ? -psh[i] : 0.0);
+      Wt[e] = sub(i == j ? from_real<S>(psh[i]) : zero<S>(), V[i + (int64_t)j * io.ldv]);
+    }
+    return;
+  }
   // One barrier per column: in step j warp 0 first applies reflector j to
   // column j + 1 and forms reflector j + 1 from it, then its other columns.
   auto reflector = [&](int j) {  // warp-wide; column j is final below row j - 1
@@ -359,8 +401,32 @@ __global__ void __launch_bounds__(kThreads) k_solve_z(const Inst* insts, const I
     if ((flags & 0x2u) && !finite_(g[i])) atomicExch(status, 7);
   }
   __syncthreads();
-  // Back substitution with U = T^*: U(i, l) = conj(T(l, i)), one warp.
-  if (threadIdx.x < 32) {
+  if (flags & 0x4u) {
+    // First choice: T^* = P^* L U, so Z = U^{-1} L^{-1} (P g), P = -Q1 (real +-1
+    // on the diagonal); L (unit lower) in T's slot, U in R1's.  One warp.
+    const S* U = wsp<S>(ws, I.oR1);
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int i = 0; i < k0; ++i) {  // x = L^{-1} (P g), into z
+        S s = zero<S>();
+        for (int l = lane; l < i; l += 32) s = madd(s, T[i + l * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) z[i] = sub(scale(g[i], -real_(Q1[i + i * k0])), s);
+        __syncwarp();
+      }
+      for (int i = k0 - 1; i >= 0; --i) {  // z = U^{-1} x
+        S s = zero<S>();
+        for (int l = i + 1 + lane; l < k0; l += 32) s = madd(s, U[i + l * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) {
+          const S u = U[i + i * k0];
+          z[i] = mul(sub(z[i], s), scale(conj_(u), 1.0 / abs2d(u)));
+        }
+        __syncwarp();
+      }
+    }
+  } else if (threadIdx.x < 32) {
+    // Back substitution with U = T^*: U(i, l) = conj(T(l, i)), one warp.
     const int lane = threadIdx.x;
     for (int i = k0 - 1; i >= 0; --i) {
       S s = zero<S>();
@@ -732,7 +798,33 @@ __global__ void __launch_bounds__(kThreads) k_solve_z2(const Inst* insts, const 
     g[i] = neg(s);
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (flags & 0x4u) {
+    // First choice: T = U^* L^* P, so Z2 = P^* L^{-*} U^{-*} g2.  One warp.
+    const S* U = wsp<S>(ws, I.oR1);
+    const S* Q1 = wsp<S>(ws, I.oQ1);
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int i = 0; i < k0; ++i) {  // y = U^{-*} g2: U^*(i, l) = conj(U(l, i)), l <= i
+        S s = zero<S>();
+        for (int l = lane; l < i; l += 32) s = cmadd(s, U[l + i * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) {
+          const S u = conj_(U[i + i * k0]);
+          z[i] = mul(sub(g[i], s), scale(conj_(u), 1.0 / abs2d(u)));
+        }
+        __syncwarp();
+      }
+      for (int i = k0 - 1; i >= 0; --i) {  // x = L^{-*} y: L^*(i, l) = conj(L(l, i)), l >= i, unit
+        S s = zero<S>();
+        for (int l = i + 1 + lane; l < k0; l += 32) s = cmadd(s, T[l + i * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) z[i] = sub(z[i], s);
+        __syncwarp();
+      }
+      __syncwarp();
+      for (int i = lane; i < k0; i += 32) z[i] = scale(z[i], -real_(Q1[i + i * k0]));  // P^* x, P = -Q1 real
+    }
+  } else if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = 0; i < k0; ++i) {
       S s = zero<S>();

@@ -175,7 +175,7 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
       cudaStreamWaitEvent(sq, pc.ev_fork, 0);
     }
     hk(kPhQrV1, 0, sq);
-    k_v1qr<S><<<pc.count, kV1Threads, 0, sq>>>(insts, d_io, io0, ws);
+    k_v1qr<S><<<pc.count, kV1Threads, 0, sq>>>(insts, d_io, io0, ws, pc.flags);
     hk(kPhQrV1, 1, sq);
     if (pc.side) cudaEventRecord(pc.ev_join, sq);
     if (pc.tab.gram_n > 0) {

@@ -24,7 +24,7 @@ THO_OK, THO_ERR_ARG, THO_ERR_SHAPE, THO_ERR_ALIGN, THO_ERR_NOMEM = 0, 1, 2, 3, 4
 THO_ERR_CUDA, THO_ERR_TIMEOUT, THO_ERR_NONFINITE, THO_ERR_UNSUPPORTED = 5, 6, 7, 8
 THO_F64, THO_C128 = 0, 1
 THO_PREC_FP64, THO_PREC_FP32_BULK, THO_PREC_FP64_EMU = 0, 1, 2
-THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE = 0x1, 0x2
+THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE, THO_FLAG_P_MLU = 0x1, 0x2, 0x4
 THO_MAX_K0, THO_MAX_K = 128, 32
 
 EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",

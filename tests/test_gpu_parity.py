@@ -345,3 +345,37 @@ def test_blocks_ill_conditioned_krylov(tho, prec_name):
     assert float(torch.linalg.matrix_norm(Q.T @ Q - I, ord=2)) < TOL_LOO
     assert float(torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)) < TOL_LOO
     assert float(torch.tril(R, -1).abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("prec_name", ["THO_PREC_FP64", "THO_PREC_FP64_EMU"])
+@pytest.mark.parametrize("n,k0,k", [(3000, 16, 8), (20000, 128, 32), (785, 7, 30)])
+def test_first_choice_of_P_matches_oracle(tho, dtype, prec_name, n, k0, k):
+    """The first choice of P (THO_FLAG_P_MLU: Algorithm 2's modified LU) against
+    the oracle's Algorithm 1 with that choice; Q, R, S agree with the second
+    choice's too (they do not depend on P)."""
+    prec = getattr(tho, prec_name)
+    p = inputs.random_problem(n, k0, k, dtype=dtype, seed=n + 5 * k0 + k)
+    plan = tho.Plan([(n, k0, k)], dtype, prec, tho.THO_FLAG_P_MLU)
+    Q, R, S = tho.orth(p.V.cuda(), p.A.cuda(), prec=prec, plan=plan)
+    torch.cuda.synchronize()
+    Qo, Ro, So, _ = oracle.two_stage_mlu(p.V.numpy(), p.A.numpy())
+    np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+    np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=TOL_Q * max(1, np.abs(Ro).max()))
+    np.testing.assert_allclose(S.cpu().numpy(), So, atol=TOL_Q * max(1, np.abs(So).max()))
+    Q2, _, _ = tho.orth(p.V.cuda(), p.A.cuda(), prec=prec)
+    assert float((Q2 - Q).abs().max()) < TOL_Q
+
+
+def test_first_choice_refused_by_the_adjoint(tho):
+    n, k0, k = 2000, 8, 4
+    p = inputs.random_problem(n, k0, k, dtype=torch.float64, seed=3)
+    plan = tho.Plan([(n, k0, k)], torch.float64, tho.THO_PREC_FP64, tho.THO_FLAG_P_MLU)
+    V, A = p.V.cuda(), p.A.cuda()
+    Q, _, _ = tho.orth(V, A, plan=plan)
+    dV, dA = torch.empty_like(V), torch.empty_like(A)
+    import ctypes
+    rc = tho.load().tho_orth_backward(plan.handle, V.data_ptr(), n, A.data_ptr(), n, Q.data_ptr(), n,
+                                      Q.data_ptr(), n, dV.data_ptr(), n, dA.data_ptr(), n,
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == tho.THO_ERR_UNSUPPORTED

@@ -286,3 +286,67 @@ def test_block_hhqr_ill_conditioned_krylov():
     Q, R = oracle.block_hhqr(A, [k] * p)
     assert np.linalg.norm(Q.T @ Q - np.eye(k * p), 2) < 1e-14
     assert np.linalg.norm(A - Q @ R, "fro") / np.linalg.norm(A, "fro") < 1e-14
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("k0", [1, 6, 16])
+def test_modified_lu_properties(dtype, k0):
+    """Algorithm 2: P diagonal with entries -sign(.) = +-1, L unit lower, U upper,
+    P - Z = L U, and |U_ii| >= 1 (no pivoting needed) for ||Z||_2 <= 1."""
+    p = inputs.random_problem(3 * k0 + 5, k0, 1, dtype=dtype, seed=41 + k0)
+    Z = _np(p.V)[:k0]
+    assert np.linalg.norm(Z, 2) <= 1.0 + 1e-14
+    P, L, U = oracle.modified_lu(Z)
+    assert np.allclose(P, np.diag(np.diag(P))) and set(np.round(np.diag(P).real).tolist()) <= {-1.0, 1.0}
+    assert np.allclose(np.diag(L), 1.0) and np.abs(np.triu(L, 1)).max() == 0.0
+    assert np.abs(np.tril(U, -1)).max() == 0.0
+    np.testing.assert_allclose(L @ U, P - Z, atol=1e-13)
+    assert np.abs(np.diag(U)).min() >= 1.0 - 1e-15
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("n,k0,k", [(200, 6, 4), (500, 16, 7), (64, 1, 3)])
+def test_first_choice_matches_closed_form(dtype, n, k0, k):
+    """Algorithm 1 with the first choice of P: T = (P - V_1)^* P = I - V_1^* P,
+    H^* H = I, H [P; 0] = V, and Q, R, S equal the closed form qf((I - V V^*) A),
+    V^* A (independent of P) and the second choice's results."""
+    p = inputs.random_problem(n, k0, k, dtype=dtype, seed=n + k0 + k)
+    V, A = _np(p.V), _np(p.A)
+    Q, R, S, aux = oracle.two_stage_mlu(V, A)
+    P, T, Wtop = aux["P"], aux["T"], aux["Wtop"]
+    np.testing.assert_allclose(T, Wtop.conj().T @ P, atol=1e-14)
+    W = np.vstack([Wtop, -V[k0:]])
+    H = np.eye(n) - W @ np.linalg.solve(T, W.conj().T)
+    np.testing.assert_allclose(H.conj().T @ H, np.eye(n), atol=1e-12)
+    np.testing.assert_allclose(H @ np.vstack([P, np.zeros((n - k0, k0))]), V, atol=1e-12)
+    Qc, Rc = qf(A - V @ (V.conj().T @ A))
+    np.testing.assert_allclose(Q, Qc, atol=1e-12)
+    np.testing.assert_allclose(R, Rc, atol=1e-12)
+    np.testing.assert_allclose(S, V.conj().T @ A, atol=1e-12)
+    Q2, R2, S2 = oracle.two_stage(V, A)
+    np.testing.assert_allclose(Q, Q2, atol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("n,k0,k", [(200, 6, 4), (500, 16, 7), (64, 1, 3)])
+def test_third_choice_matches_closed_form(dtype, n, k0, k):
+    """Algorithm 1 with the third choice of P (polar factor): V_1 = Q2 M with Q2
+    unitary and M Hermitian positive semidefinite, T = I + M with kappa_2(T) <= 2,
+    H [P; 0] = V, and Q, R, S equal the closed form (independent of P)."""
+    p = inputs.random_problem(n, k0, k, dtype=dtype, seed=7 * n + k0 + k)
+    V, A = _np(p.V), _np(p.A)
+    Q, R, S, aux = oracle.two_stage_polar(V, A)
+    P, M, T, Wtop = aux["P"], aux["M"], aux["T"], aux["Wtop"]
+    np.testing.assert_allclose((-P) @ M, V[:k0], atol=1e-13)
+    np.testing.assert_allclose(P.conj().T @ P, np.eye(k0), atol=1e-13)
+    np.testing.assert_allclose(M, M.conj().T, atol=1e-13)
+    assert np.linalg.eigvalsh(M).min() > -1e-13
+    np.testing.assert_allclose(T, np.eye(k0) + M, atol=1e-13)
+    assert np.linalg.cond(T) <= 2.0 + 1e-12
+    W = np.vstack([Wtop, -V[k0:]])
+    H = np.eye(n) - W @ np.linalg.solve(T, W.conj().T)
+    np.testing.assert_allclose(H @ np.vstack([P, np.zeros((n - k0, k0))]), V, atol=1e-12)
+    Qc, Rc = qf(A - V @ (V.conj().T @ A))
+    np.testing.assert_allclose(Q, Qc, atol=1e-12)
+    np.testing.assert_allclose(R, Rc, atol=1e-12)
+    np.testing.assert_allclose(S, V.conj().T @ A, atol=1e-12)

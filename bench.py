@@ -389,7 +389,15 @@ def run_batched(args):
              torch.empty_strided((k, k), (1, k), dtype=torch.float64, device=dev),
              torch.empty_strided((k0, k), (1, k0), dtype=torch.float64, device=dev)) for (n, k0, k) in shapes]
     prec = WORKLOADS[args.workload][5]
-    bplan = tho.Plan(shapes, torch.float64, prec)
+    # Partition of the batch plan from the autotuner (untimed; synthetic
+    # operands of the same shapes); the looped comparator keeps the defaults.
+    tuning, tune_info = None, {"autotuned": False}
+    if not args.no_tune:
+        t0 = time.time()
+        tuning, tune_ms = tho.autotune(shapes, torch.float64, prec)
+        tune_info = {"autotuned": True, "search_s": round(time.time() - t0, 2), "search_ms_per_call": tune_ms}
+    bplan = tho.Plan(shapes, torch.float64, prec, tuning=tuning)
+    tune_info.update(zip(("leaf_rows", "split_chunks"), bplan.tuning))
     lplans = [tho.Plan([s], torch.float64, prec) for s in shapes]
     stream = torch.cuda.current_stream(dev)
 
@@ -435,7 +443,7 @@ def run_batched(args):
                        "rows_total": sum(s[0] for s in shapes), "B_alg": B, "F_alg": F,
                        "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
             "batched": {"ms": ms_b, "gbs": B / (ms_b * 1e-3) / 1e9, "tflops": F / (ms_b * 1e-3) / 1e12,
-                        "launches": bplan.kernel_launches},
+                        "launches": bplan.kernel_launches, "tuning": tune_info},
             "looped": {"ms": ms_l, "gbs": B / (ms_l * 1e-3) / 1e9, "tflops": F / (ms_l * 1e-3) / 1e12,
                        "launches": sum(p.kernel_launches for p in lplans)},
             "speedup_batched_vs_looped": ms_l / ms_b,
@@ -579,7 +587,13 @@ def run_gpu(args):
     cplx = dt == "complex128"
     p = inputs.config_problem(cid, n=n, device=dev)
     V, A = p.V, p.A
-    plan = tho.Plan([(n, k0, k)], V.dtype, prec, 0)
+    tuning, tune_info = None, {"autotuned": False}
+    if args.tune:  # untimed partition search on synthetic operands of this shape
+        t0 = time.time()
+        tuning, tune_ms = tho.autotune([(n, k0, k)], V.dtype, prec)
+        tune_info = {"autotuned": True, "search_s": round(time.time() - t0, 2), "search_ms_per_call": tune_ms}
+    plan = tho.Plan([(n, k0, k)], V.dtype, prec, 0, tuning=tuning)
+    tune_info.update(zip(("leaf_rows", "split_chunks"), plan.tuning))
     Q = torch.empty_strided((n, k), (1, n), dtype=V.dtype, device=dev)
     R = torch.empty_strided((k, k), (1, k), dtype=V.dtype, device=dev)
     S = torch.empty_strided((k0, k), (1, k0), dtype=V.dtype, device=dev)
@@ -756,7 +770,7 @@ def run_gpu(args):
             "columns_per_s": k * ws * args.steps / (el_ms * 1e-3),
             "phases_ms_per_step": {ph: v[0] / args.steps for ph, v in phases.items()},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": plan.kernel_launches * args.steps, "check": check,
+            "gpu_launches": plan.kernel_launches * args.steps, "check": check, "tuning": tune_info,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -776,6 +790,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the FP64-arithmetic comparison run")
+    ap.add_argument("--tune", action="store_true",
+                    help="single-problem workloads: time the autotuned partition instead of the default")
+    ap.add_argument("--no-tune", action="store_true", help="batched workloads: time the default partition")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

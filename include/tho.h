@@ -105,6 +105,80 @@ typedef struct tho_plan_s* tho_plan_t;
  * Writes the plan handle to *out.  Errors: ARG, SHAPE, UNSUPPORTED, NOMEM, CUDA. */
 tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out);
 
+/* Partition choices of a plan.  Neither changes what is computed, only how the
+ * n-length work is cut (the results differ at the rounding level, as the
+ * order of the partial sums changes):
+ *   leaf_rows     TSQR leaf height P (the Householder QR of A'_2 in Algorithm 1
+ *                 runs over row panels of P/2 to P rows, then a binary tree of
+ *                 Householder QRs of the stacked R factors): 64, 128 or 256,
+ *                 with P >= 2 k; 0 = the library's choice (the largest height
+ *                 whose panel lets three CTAs share an SM, else the largest
+ *                 that fits in shared memory).
+ *   split_chunks  split-n factor: number of row chunks of the streaming sweeps
+ *                 (W^* A, the rank-k0 updates, W^* [0; Qbar]) summed over the
+ *                 plan's problems and shared among them in proportion to
+ *                 n - k0; 0 = the library's choice (2 x SMs - 1 for one
+ *                 problem, 8 x SMs for a batch). */
+typedef struct {
+  int32_t leaf_rows;
+  int32_t split_chunks;
+} tho_tuning_t;
+
+#define THO_TUNE_MAX_SPLIT (1 << 20)
+
+/* tho_plan with explicit partition choices (`tuning` NULL or all zero: the
+ * same plan as tho_plan).  Errors as tho_plan; ARG for a leaf height other
+ * than 0, 64, 128, 256 or a split outside [0, THO_TUNE_MAX_SPLIT];
+ * UNSUPPORTED for a leaf height below 2 k or whose panel does not fit in
+ * shared memory. */
+tho_status_t tho_plan_tuned(const tho_desc_t* descs, int32_t count, const tho_tuning_t* tuning,
+                            tho_plan_t* out);
+
+/* The choices a plan was built with (defaults resolved to their values). */
+tho_status_t tho_plan_tuning(tho_plan_t plan, tho_tuning_t* out);
+
+/* Autotuner: measures candidate partitions for these problems on the current
+ * device and returns the fastest in *out (with its median time per call in
+ * *ms, which may be NULL).  The search times tho_orth (count = 1) or
+ * tho_orth_batched (count > 1) on seeded synthetic operands of the same
+ * shapes, allocated for the search and freed before return, on `stream`:
+ * first every split-n factor of {SMs/2, SMs - 1, 2 SMs - 1, 4 SMs, 8 SMs,
+ * 16 SMs} (and the default) at the default leaf height, then every valid leaf
+ * height at the best split; each candidate is one warm-up call plus 3 to 9
+ * timed calls (median).  A candidate replaces the default only when it is at
+ * least 2 % faster.  The search is synchronous and uses the device
+ * exclusively while it runs (its timings assume no other work on the GPU).
+ *
+ * cache_path: a JSON-lines file (one object per line with "key", "leaf_rows",
+ * "split_chunks", "ms"); NULL = the file named by the environment variable
+ * THO_TUNE_CACHE, or no cache if that is unset.  A cached entry for the key of
+ * tho_tune_key (device name, dtype, precision, flags, shapes) is returned
+ * without measuring when the plan accepts it; a new result is appended.
+ * Errors: as tho_plan_tuned, NOMEM for the synthetic operands, CUDA. */
+tho_status_t tho_autotune(const tho_desc_t* descs, int32_t count, const char* cache_path, void* stream,
+                          tho_tuning_t* out, double* ms);
+
+/* Cache key of a problem set on a device named `device_name` (NUL-terminated
+ * into buf, at most len bytes): "<device>|<dtype>|<prec>|<flags>|<shapes>"
+ * where each problem appears as (n-bucket, k0, k), the n-bucket being
+ * floor(4 log2 n) (quarter octaves), listed for up to 8 problems and replaced
+ * by "batch<count>:<64-bit FNV-1a hash of the list>" beyond.  Host only.
+ * Errors: ARG (null pointer, count < 1, buffer too short). */
+tho_status_t tho_tune_key(const tho_desc_t* descs, int32_t count, const char* device_name, char* buf,
+                          size_t len);
+
+/* Look up `key` in the cache file `path` (the last matching line wins; lines
+ * that do not parse are skipped; a missing file holds no entries).  Sets
+ * *found to 1 and fills *out (and *ms, may be NULL) on a hit, else *found = 0.
+ * Host only.  Errors: ARG. */
+tho_status_t tho_tune_cache_get(const char* path, const char* key, tho_tuning_t* out, double* ms,
+                                int32_t* found);
+
+/* Append one entry to the cache file `path` (created if missing).  Host only.
+ * Errors: ARG (null pointer, a key containing '"', '\\' or a control
+ * character), CUDA is never returned; an unwritable file gives ARG. */
+tho_status_t tho_tune_cache_put(const char* path, const char* key, const tho_tuning_t* t, double ms);
+
 /* Free the plan's device and host resources (synchronizes the device first).
  * NULL is accepted. */
 tho_status_t tho_plan_destroy(tho_plan_t plan);

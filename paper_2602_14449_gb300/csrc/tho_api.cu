@@ -42,6 +42,7 @@ struct tho_plan_s {
   cudaStream_t hs_in = nullptr, hs_out = nullptr;
   cudaEvent_t hs_ev_in[2] = {nullptr, nullptr}, hs_ev_comp[2] = {nullptr, nullptr}, hs_ev_out[2] = {nullptr, nullptr};
   int hs_next = 0;
+  int32_t split_chunks = 0;  // split-n factor the partition was built with
 };
 
 namespace {
@@ -175,13 +176,22 @@ const char* tho_status_string(tho_status_t s) {
   return "unknown status";
 }
 
-tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
+}  // extern "C"
+
+namespace {
+
+// tho_plan and tho_plan_tuned: `tuning` NULL (or zero fields) keeps the
+// library's partition choices.
+tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_t* tuning, tho_plan_t* out) {
   if (!descs || !out || count < 1) return THO_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
     tho_status_t s = check_desc(descs[i], descs[0]);
     if (s != THO_OK) return s;
   }
+  const int32_t t_leaf = tuning ? tuning->leaf_rows : 0, t_split = tuning ? tuning->split_chunks : 0;
+  if (t_leaf != 0 && t_leaf != 64 && t_leaf != 128 && t_leaf != 256) return THO_ERR_ARG;
+  if (t_split < 0 || t_split > THO_TUNE_MAX_SPLIT) return THO_ERR_ARG;
   tho_plan_s* p = new (std::nothrow) tho_plan_s();
   if (!p) return THO_ERR_NOMEM;
   PlanCore& pc = p->pc;
@@ -193,13 +203,6 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   const bool b32 = pc.prec == THO_PREC_FP32_BULK, emu = pc.prec == THO_PREC_FP64_EMU;
   p->L = cplx ? (b32 ? &tho::kLaunchC128Bulk32 : (emu ? &tho::kLaunchC128Emu : &tho::kLaunchC128))
               : (b32 ? &tho::kLaunchF64Bulk32 : (emu ? &tho::kLaunchF64Emu : &tho::kLaunchF64));
-  if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return THO_ERR_CUDA; }
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
-    free_plan(p);
-    return THO_ERR_CUDA;
-  }
-  pc.sms = sms;
   for (int i = 0; i < count; ++i) {
     pc.kmax = std::max<int>(pc.kmax, (int)descs[i].k);
     pc.k0max = std::max<int>(pc.k0max, (int)descs[i].k0);
@@ -216,22 +219,41 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   const int leaf_k0p = pc.prec == THO_PREC_FP64_EMU && pc.any_k0 ? 0 : pc.k0pmax;
   // Largest leaf height whose panel lets three CTAs share an SM, else the
   // largest that fits at all (the leaf QR's serial steps hide behind other CTAs).
-  for (int limit : {76 * 1024, 220 * 1024}) {
-    for (int P : {256, 128, 64}) {
-      if (P < 2 * pc.kmax) continue;
-      if (tho::leaf_smem_bytes(P, leaf_k0p, pc.kpmax, p->L->bulk_elem, p->L->elem) <= (size_t)limit) {
-        pc.P = P;
-        break;
-      }
+  if (t_leaf != 0) {
+    // A requested height: at least 2 k (every leaf keeps >= k rows) and a panel
+    // that fits in shared memory.
+    if (t_leaf < 2 * pc.kmax ||
+        tho::leaf_smem_bytes(t_leaf, leaf_k0p, pc.kpmax, p->L->bulk_elem, p->L->elem) > (size_t)(220 * 1024)) {
+      free_plan(p);
+      return THO_ERR_UNSUPPORTED;
     }
-    if (pc.P) break;
+    pc.P = t_leaf;
+  } else {
+    for (int limit : {76 * 1024, 220 * 1024}) {
+      for (int P : {256, 128, 64}) {
+        if (P < 2 * pc.kmax) continue;
+        if (tho::leaf_smem_bytes(P, leaf_k0p, pc.kpmax, p->L->bulk_elem, p->L->elem) <= (size_t)limit) {
+          pc.P = P;
+          break;
+        }
+      }
+      if (pc.P) break;
+    }
   }
   if (pc.P == 0) { free_plan(p); return THO_ERR_UNSUPPORTED; }
+  if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return THO_ERR_CUDA; }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    free_plan(p);
+    return THO_ERR_CUDA;
+  }
+  pc.sms = sms;
 
   // Per-instance partition and workspace layout.
   // Single problem: two chunks per SM less one, so that the SM running the
   // small QR of V_{1:k0,:} beside the first Gram sweep takes one chunk fewer.
-  const int64_t target_total = count == 1 ? 2 * (int64_t)sms - 1 : 8 * (int64_t)sms;
+  const int64_t target_total = t_split > 0 ? t_split : (count == 1 ? 2 * (int64_t)sms - 1 : 8 * (int64_t)sms);
+  p->split_chunks = (int32_t)target_total;
   double msum = 0;
   for (int i = 0; i < count; ++i) msum += (double)(descs[i].n - descs[i].k0);
   int64_t off = 0;
@@ -340,10 +362,15 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
   }
   if (cudaMemcpy(pc.d_insts, pc.h_insts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(pc.d_items, it.data(), sizeof(WorkItemH) * it.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(pc.ws, 0, ws_bytes) != cudaSuccess || cudaMemset(pc.d_status, 0, sizeof(int)) != cudaSuccess ||
-      p->L->configure(pc) != cudaSuccess) {
+      cudaMemset(pc.ws, 0, ws_bytes) != cudaSuccess || cudaMemset(pc.d_status, 0, sizeof(int)) != cudaSuccess) {
     free_plan(p);
     return THO_ERR_CUDA;
+  }
+  if (cudaError_t ce = p->L->configure(pc); ce != cudaSuccess) {
+    free_plan(p);
+    // A requested leaf height whose emulated apply stage cannot fit is a shape
+    // limit, not a runtime failure (configure refuses it before any CUDA call).
+    return (t_leaf != 0 && ce == cudaErrorInvalidValue) ? THO_ERR_UNSUPPORTED : THO_ERR_CUDA;
   }
   if (count > 1) {
     if (cudaMalloc(&p->d_io, sizeof(Io) * count) != cudaSuccess ||
@@ -365,6 +392,26 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
     return THO_ERR_CUDA;
   }
   *out = p;
+  return THO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out) {
+  return plan_impl(descs, count, nullptr, out);
+}
+
+tho_status_t tho_plan_tuned(const tho_desc_t* descs, int32_t count, const tho_tuning_t* tuning,
+                            tho_plan_t* out) {
+  return plan_impl(descs, count, tuning, out);
+}
+
+tho_status_t tho_plan_tuning(tho_plan_t plan, tho_tuning_t* out) {
+  if (!plan || !out) return THO_ERR_ARG;
+  out->leaf_rows = plan->pc.P;
+  out->split_chunks = plan->split_chunks;
   return THO_OK;
 }
 

@@ -26,13 +26,15 @@ THO_F64, THO_C128 = 0, 1
 THO_PREC_FP64, THO_PREC_FP32_BULK, THO_PREC_FP64_EMU = 0, 1, 2
 THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE, THO_FLAG_P_MLU = 0x1, 0x2, 0x4
 THO_MAX_K0, THO_MAX_K = 128, 32
+THO_TUNE_MAX_SPLIT = 1 << 20
 
 EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_plan_kernel_launches",
             "tho_plan_leaf_rows", "tho_orth_host", "tho_orth_host_wait",
             "tho_blocks_plan", "tho_blocks_destroy", "tho_orth_blocks", "tho_blocks_kernel_launches",
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
-            "tho_orth_noalloc")
+            "tho_orth_noalloc", "tho_plan_tuned", "tho_plan_tuning", "tho_autotune", "tho_tune_key",
+            "tho_tune_cache_get", "tho_tune_cache_put")
 THO_NUM_PHASES = 11
 
 
@@ -45,6 +47,14 @@ class ThoError(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("k0", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("dtype", ctypes.c_int32), ("prec", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class Tuning(ctypes.Structure):
+    """tho_tuning_t: TSQR leaf height and split-n factor (0 = library default)."""
+    _fields_ = [("leaf_rows", ctypes.c_int32), ("split_chunks", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.leaf_rows, self.split_chunks)
 
 
 class Instance(ctypes.Structure):
@@ -71,6 +81,20 @@ def load(path: str | None = None):
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
         lib.tho_plan.argtypes = [ctypes.POINTER(Desc), i32, ctypes.POINTER(vp)]
         lib.tho_plan.restype = ctypes.c_int
+        lib.tho_plan_tuned.argtypes = [ctypes.POINTER(Desc), i32, ctypes.POINTER(Tuning), ctypes.POINTER(vp)]
+        lib.tho_plan_tuned.restype = ctypes.c_int
+        lib.tho_plan_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        lib.tho_plan_tuning.restype = ctypes.c_int
+        lib.tho_autotune.argtypes = [ctypes.POINTER(Desc), i32, ctypes.c_char_p, vp, ctypes.POINTER(Tuning),
+                                     ctypes.POINTER(ctypes.c_double)]
+        lib.tho_autotune.restype = ctypes.c_int
+        lib.tho_tune_key.argtypes = [ctypes.POINTER(Desc), i32, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_size_t]
+        lib.tho_tune_key.restype = ctypes.c_int
+        lib.tho_tune_cache_get.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(Tuning),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        lib.tho_tune_cache_get.restype = ctypes.c_int
+        lib.tho_tune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(Tuning), ctypes.c_double]
+        lib.tho_tune_cache_put.restype = ctypes.c_int
         lib.tho_plan_destroy.argtypes = [vp]
         lib.tho_plan_destroy.restype = ctypes.c_int
         lib.tho_plan_workspace_bytes.argtypes = [vp]
@@ -144,6 +168,55 @@ def _dtype_code(t: torch.dtype) -> int:
     raise ValueError(f"unsupported dtype {t}; use float64 or complex128")
 
 
+def _descs(shapes, dtype, prec, flags):
+    shapes = list(shapes)
+    arr = (Desc * len(shapes))()
+    code = _dtype_code(dtype)
+    for i, (n, k0, k) in enumerate(shapes):
+        arr[i] = Desc(n, k0, k, code, prec, flags)
+    return arr
+
+
+def autotune(shapes, dtype=torch.float64, prec: int = THO_PREC_FP64, flags: int = 0, cache: str | None = None):
+    """tho_autotune: time candidate partitions for these problem shapes on the
+    current device (synthetic operands) and return ((leaf_rows, split_chunks),
+    median ms per call).  ``cache``: JSON-lines file (None: $THO_TUNE_CACHE if
+    set); a cached entry is returned without measuring."""
+    shapes = list(shapes)
+    t = Tuning()
+    ms = ctypes.c_double()
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().tho_autotune(_descs(shapes, dtype, prec, flags), len(shapes),
+                               cache.encode() if cache else None, ctypes.c_void_p(st), ctypes.byref(t),
+                               ctypes.byref(ms)), "tho_autotune")
+    return t.as_tuple(), ms.value
+
+
+def tune_key(shapes, dtype, prec: int, flags: int, device_name: str) -> str:
+    """tho_tune_key: the autotuner's cache key for these shapes on a device named ``device_name``."""
+    shapes = list(shapes)
+    buf = ctypes.create_string_buffer(4096)
+    _check(load().tho_tune_key(_descs(shapes, dtype, prec, flags), len(shapes), device_name.encode(), buf,
+                               len(buf)), "tho_tune_key")
+    return buf.value.decode()
+
+
+def tune_cache_get(path: str, key: str):
+    """tho_tune_cache_get: ((leaf_rows, split_chunks), ms) of the last entry for ``key``, or None."""
+    t = Tuning()
+    ms = ctypes.c_double()
+    found = ctypes.c_int32()
+    _check(load().tho_tune_cache_get(path.encode(), key.encode(), ctypes.byref(t), ctypes.byref(ms),
+                                     ctypes.byref(found)), "tho_tune_cache_get")
+    return (t.as_tuple(), ms.value) if found.value else None
+
+
+def tune_cache_put(path: str, key: str, tuning, ms: float):
+    """tho_tune_cache_put: append one entry to the cache file."""
+    t = Tuning(*tuning)
+    _check(load().tho_tune_cache_put(path.encode(), key.encode(), ctypes.byref(t), float(ms)), "tho_tune_cache_put")
+
+
 def _empty_cm(rows: int, cols: int, dtype, device) -> torch.Tensor:
     return torch.empty_strided((rows, cols), (1, max(rows, 1)), dtype=dtype, device=device)
 
@@ -151,15 +224,18 @@ def _empty_cm(rows: int, cols: int, dtype, device) -> torch.Tensor:
 class Plan:
     """Owns one tho_plan_t (workspace, launch tables, batched graph)."""
 
-    def __init__(self, shapes, dtype=torch.float64, prec: int = THO_PREC_FP64, flags: int = 0):
+    def __init__(self, shapes, dtype=torch.float64, prec: int = THO_PREC_FP64, flags: int = 0, tuning=None):
+        """``tuning``: None (library defaults) or (leaf_rows, split_chunks), e.g.
+        from ``autotune``; 0 in either place keeps that default."""
         lib = load()
         shapes = list(shapes)
-        arr = (Desc * len(shapes))()
-        code = _dtype_code(dtype)
-        for i, (n, k0, k) in enumerate(shapes):
-            arr[i] = Desc(n, k0, k, code, prec, flags)
+        arr = _descs(shapes, dtype, prec, flags)
         h = ctypes.c_void_p()
-        _check(lib.tho_plan(arr, len(shapes), ctypes.byref(h)), "tho_plan")
+        if tuning is None:
+            _check(lib.tho_plan(arr, len(shapes), ctypes.byref(h)), "tho_plan")
+        else:
+            t = Tuning(*tuning)
+            _check(lib.tho_plan_tuned(arr, len(shapes), ctypes.byref(t), ctypes.byref(h)), "tho_plan_tuned")
         self.handle = h
         self.shapes = shapes
         self.dtype = dtype
@@ -177,6 +253,13 @@ class Plan:
     @property
     def leaf_rows(self) -> int:
         return load().tho_plan_leaf_rows(self.handle)
+
+    @property
+    def tuning(self):
+        """(leaf_rows, split_chunks) the plan was built with."""
+        t = Tuning()
+        _check(load().tho_plan_tuning(self.handle, ctypes.byref(t)), "tho_plan_tuning")
+        return t.as_tuple()
 
     def status(self) -> int:
         return load().tho_plan_status(self.handle)

@@ -397,7 +397,7 @@ def run_batched(args):
         tuning, tune_ms = tho.autotune(shapes, torch.float64, prec)
         tune_info = {"autotuned": True, "search_s": round(time.time() - t0, 2), "search_ms_per_call": tune_ms}
     bplan = tho.Plan(shapes, torch.float64, prec, tuning=tuning)
-    tune_info.update(zip(("leaf_rows", "split_chunks"), bplan.tuning))
+    tune_info.update(zip(("leaf_rows", "split_chunks", "balance"), bplan.tuning))
     lplans = [tho.Plan([s], torch.float64, prec) for s in shapes]
     stream = torch.cuda.current_stream(dev)
 
@@ -593,7 +593,7 @@ def run_gpu(args):
         tuning, tune_ms = tho.autotune([(n, k0, k)], V.dtype, prec)
         tune_info = {"autotuned": True, "search_s": round(time.time() - t0, 2), "search_ms_per_call": tune_ms}
     plan = tho.Plan([(n, k0, k)], V.dtype, prec, 0, tuning=tuning)
-    tune_info.update(zip(("leaf_rows", "split_chunks"), plan.tuning))
+    tune_info.update(zip(("leaf_rows", "split_chunks", "balance"), plan.tuning))
     Q = torch.empty_strided((n, k), (1, n), dtype=V.dtype, device=dev)
     R = torch.empty_strided((k, k), (1, k), dtype=V.dtype, device=dev)
     S = torch.empty_strided((k0, k), (1, k0), dtype=V.dtype, device=dev)

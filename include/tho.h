@@ -118,17 +118,23 @@ tho_status_t tho_plan(const tho_desc_t* descs, int32_t count, tho_plan_t* out);
  *                 (W^* A, the rank-k0 updates, W^* [0; Qbar]) summed over the
  *                 plan's problems and shared among them in proportion to
  *                 n - k0; 0 = the library's choice (2 x SMs - 1 for one
- *                 problem, 8 x SMs for a batch). */
+ *                 problem, 8 x SMs for a batch).
+ *   balance       how a batch shares the chunks: 0 = in proportion to n - k0
+ *                 (the default), 1 = in proportion to the work of each
+ *                 problem's streaming sweeps, (n - k0) k (k0 + k).  No effect
+ *                 on a single problem. */
 typedef struct {
   int32_t leaf_rows;
   int32_t split_chunks;
+  int32_t balance;
 } tho_tuning_t;
 
 #define THO_TUNE_MAX_SPLIT (1 << 20)
 
 /* tho_plan with explicit partition choices (`tuning` NULL or all zero: the
  * same plan as tho_plan).  Errors as tho_plan; ARG for a leaf height other
- * than 0, 64, 128, 256 or a split outside [0, THO_TUNE_MAX_SPLIT];
+ * than 0, 64, 128, 256, a split outside [0, THO_TUNE_MAX_SPLIT] or a balance
+ * other than 0, 1;
  * UNSUPPORTED for a leaf height below 2 k or whose panel does not fit in
  * shared memory. */
 tho_status_t tho_plan_tuned(const tho_desc_t* descs, int32_t count, const tho_tuning_t* tuning,
@@ -143,14 +149,15 @@ tho_status_t tho_plan_tuning(tho_plan_t plan, tho_tuning_t* out);
  * tho_orth_batched (count > 1) on seeded synthetic operands of the same
  * shapes, allocated for the search and freed before return, on `stream`:
  * first every split-n factor of {SMs/2, SMs - 1, 2 SMs - 1, 4 SMs, 8 SMs,
- * 16 SMs} (and the default) at the default leaf height, then every valid leaf
- * height at the best split; each candidate is one warm-up call plus 3 to 9
+ * 16 SMs, 32 SMs, 64 SMs} (and the default) at the default leaf height, then
+ * every valid leaf height at the best split, then (batches) the work-balanced
+ * share at the best split and height; each candidate is one warm-up call plus 3 to 9
  * timed calls (median).  A candidate replaces the default only when it is at
  * least 2 % faster.  The search is synchronous and uses the device
  * exclusively while it runs (its timings assume no other work on the GPU).
  *
  * cache_path: a JSON-lines file (one object per line with "key", "leaf_rows",
- * "split_chunks", "ms"); NULL = the file named by the environment variable
+ * "split_chunks", "balance", "ms"); NULL = the file named by the environment variable
  * THO_TUNE_CACHE, or no cache if that is unset.  A cached entry for the key of
  * tho_tune_key (device name, dtype, precision, flags, shapes) is returned
  * without measuring when the plan accepts it; a new result is appended.

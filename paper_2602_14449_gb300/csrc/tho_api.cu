@@ -43,6 +43,7 @@ struct tho_plan_s {
   cudaEvent_t hs_ev_in[2] = {nullptr, nullptr}, hs_ev_comp[2] = {nullptr, nullptr}, hs_ev_out[2] = {nullptr, nullptr};
   int hs_next = 0;
   int32_t split_chunks = 0;  // split-n factor the partition was built with
+  int32_t balance = 0;       // chunks shared by rows (0) or by streaming work (1)
 };
 
 namespace {
@@ -190,8 +191,10 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
     if (s != THO_OK) return s;
   }
   const int32_t t_leaf = tuning ? tuning->leaf_rows : 0, t_split = tuning ? tuning->split_chunks : 0;
+  const int32_t t_balance = tuning ? tuning->balance : 0;
   if (t_leaf != 0 && t_leaf != 64 && t_leaf != 128 && t_leaf != 256) return THO_ERR_ARG;
   if (t_split < 0 || t_split > THO_TUNE_MAX_SPLIT) return THO_ERR_ARG;
+  if (t_balance != 0 && t_balance != 1) return THO_ERR_ARG;
   tho_plan_s* p = new (std::nothrow) tho_plan_s();
   if (!p) return THO_ERR_NOMEM;
   PlanCore& pc = p->pc;
@@ -254,8 +257,15 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
   // small QR of V_{1:k0,:} beside the first Gram sweep takes one chunk fewer.
   const int64_t target_total = t_split > 0 ? t_split : (count == 1 ? 2 * (int64_t)sms - 1 : 8 * (int64_t)sms);
   p->split_chunks = (int32_t)target_total;
+  p->balance = t_balance;
+  // Each problem's share of the chunks: in proportion to its trailing rows, or
+  // (balance = 1) to the work of its streaming sweeps, (n - k0) k (k0 + k).
+  auto weight = [&](const tho_desc_t& d) {
+    const double m = (double)(d.n - d.k0);
+    return t_balance == 1 ? m * (double)d.k * (double)(d.k0 + d.k) : m;
+  };
   double msum = 0;
-  for (int i = 0; i < count; ++i) msum += (double)(descs[i].n - descs[i].k0);
+  for (int i = 0; i < count; ++i) msum += weight(descs[i]);
   int64_t off = 0;
   auto take = [&off](int64_t elems) {
     int64_t o = off;
@@ -286,7 +296,7 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
     }
     I.L = L;
     pc.Lmax = std::max(pc.Lmax, L);
-    int64_t target = std::max<int64_t>(1, std::llround((double)target_total * (double)I.m / msum));
+    int64_t target = std::max<int64_t>(1, std::llround((double)target_total * weight(descs[i]) / msum));
     I.rows1 = round_up(ceil_div(I.m, target), tho::kTileRows);
     I.g1 = (int)ceil_div(I.m, I.rows1);
     I.rows4 = I.rows1;
@@ -412,6 +422,7 @@ tho_status_t tho_plan_tuning(tho_plan_t plan, tho_tuning_t* out) {
   if (!plan || !out) return THO_ERR_ARG;
   out->leaf_rows = plan->pc.P;
   out->split_chunks = plan->split_chunks;
+  out->balance = plan->balance;
   return THO_OK;
 }
 

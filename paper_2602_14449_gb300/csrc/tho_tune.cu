@@ -88,11 +88,15 @@ bool parse_line(const char* line, std::string* key, tho_tuning_t* t, double* ms)
   const char* q = std::strchr(p + 1, '"');
   if (!q) return false;
   key->assign(p + 1, q);
-  double lr = 0, sc = 0, m = 0;
-  if (!find_num(q, "leaf_rows", &lr) || !find_num(q, "split_chunks", &sc) || !find_num(q, "ms", &m)) return false;
+  double lr = 0, sc = 0, bl = 0, m = 0;
+  if (!find_num(q, "leaf_rows", &lr) || !find_num(q, "split_chunks", &sc) || !find_num(q, "balance", &bl) ||
+      !find_num(q, "ms", &m))
+    return false;
   if (lr != std::floor(lr) || sc != std::floor(sc) || lr < 0 || sc < 0 || sc > THO_TUNE_MAX_SPLIT) return false;
+  if (bl != 0.0 && bl != 1.0) return false;
   t->leaf_rows = (int32_t)lr;
   t->split_chunks = (int32_t)sc;
+  t->balance = (int32_t)bl;
   *ms = m;
   return true;
 }
@@ -265,8 +269,8 @@ tho_status_t tho_tune_cache_put(const char* path, const char* key, const tho_tun
   for (const char* c = key; *c; ++c)
     if (!key_char_ok(*c)) return THO_ERR_ARG;
   char tail[160];
-  std::snprintf(tail, sizeof(tail), "\", \"leaf_rows\": %d, \"split_chunks\": %d, \"ms\": %.6f}\n", t->leaf_rows,
-                t->split_chunks, std::isfinite(ms) ? ms : 0.0);
+  std::snprintf(tail, sizeof(tail), "\", \"leaf_rows\": %d, \"split_chunks\": %d, \"balance\": %d, \"ms\": %.6f}\n",
+                t->leaf_rows, t->split_chunks, t->balance, std::isfinite(ms) ? ms : 0.0);
   const std::string line = std::string("{\"key\": \"") + key + tail;
   FILE* f = std::fopen(path, "a");
   if (!f) return THO_ERR_ARG;
@@ -315,7 +319,7 @@ tho_status_t tho_autotune(const tho_desc_t* descs, int32_t count, const char* ca
   if (s != THO_OK) return s;
   tho_tuning_t def{}, eff{};
   double def_ms = 0;
-  s = time_candidate(descs, count, tho_tuning_t{0, 0}, ops, st, &def_ms, &def);
+  s = time_candidate(descs, count, tho_tuning_t{0, 0, 0}, ops, st, &def_ms, &def);
   if (s != THO_OK) return s;
   tho_tuning_t best = def;
   double best_ms = def_ms;
@@ -331,19 +335,21 @@ tho_status_t tho_autotune(const tho_desc_t* descs, int32_t count, const char* ca
     return THO_OK;
   };
   // Split-n factor at the default leaf height.
-  std::vector<int> splits = {sms / 2, sms - 1, 2 * sms - 1, 4 * sms, 8 * sms, 16 * sms};
+  std::vector<int> splits = {sms / 2, sms - 1, 2 * sms - 1, 4 * sms, 8 * sms, 16 * sms, 32 * sms, 64 * sms};
   std::sort(splits.begin(), splits.end());
   splits.erase(std::unique(splits.begin(), splits.end()), splits.end());
   for (int sp : splits) {
     if (sp < 1 || sp > THO_TUNE_MAX_SPLIT || sp == def.split_chunks) continue;
-    if ((s = consider(tho_tuning_t{def.leaf_rows, sp})) != THO_OK) return s;
+    if ((s = consider(tho_tuning_t{def.leaf_rows, sp, 0})) != THO_OK) return s;
   }
   // Leaf height at the best split.
   const int32_t split_best = best.split_chunks;
   for (int P : {64, 128, 256}) {
     if (P == def.leaf_rows) continue;
-    if ((s = consider(tho_tuning_t{P, split_best})) != THO_OK) return s;
+    if ((s = consider(tho_tuning_t{P, split_best, 0})) != THO_OK) return s;
   }
+  // Batches: chunks shared by streaming work instead of rows.
+  if (count > 1 && (s = consider(tho_tuning_t{best.leaf_rows, best.split_chunks, 1})) != THO_OK) return s;
   // Keep the default unless a candidate is clearly faster (timing noise).
   if (best_ms > 0.98 * def_ms) {
     best = def;

@@ -50,11 +50,12 @@ class Desc(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    """tho_tuning_t: TSQR leaf height and split-n factor (0 = library default)."""
-    _fields_ = [("leaf_rows", ctypes.c_int32), ("split_chunks", ctypes.c_int32)]
+    """tho_tuning_t: TSQR leaf height, split-n factor (0 = library default) and
+    how a batch shares the chunks (0 = by rows, 1 = by streaming work)."""
+    _fields_ = [("leaf_rows", ctypes.c_int32), ("split_chunks", ctypes.c_int32), ("balance", ctypes.c_int32)]
 
     def as_tuple(self):
-        return (self.leaf_rows, self.split_chunks)
+        return (self.leaf_rows, self.split_chunks, self.balance)
 
 
 class Instance(ctypes.Structure):
@@ -179,8 +180,8 @@ def _descs(shapes, dtype, prec, flags):
 
 def autotune(shapes, dtype=torch.float64, prec: int = THO_PREC_FP64, flags: int = 0, cache: str | None = None):
     """tho_autotune: time candidate partitions for these problem shapes on the
-    current device (synthetic operands) and return ((leaf_rows, split_chunks),
-    median ms per call).  ``cache``: JSON-lines file (None: $THO_TUNE_CACHE if
+    current device (synthetic operands) and return ((leaf_rows, split_chunks,
+    balance), median ms per call).  ``cache``: JSON-lines file (None: $THO_TUNE_CACHE if
     set); a cached entry is returned without measuring."""
     shapes = list(shapes)
     t = Tuning()
@@ -202,7 +203,7 @@ def tune_key(shapes, dtype, prec: int, flags: int, device_name: str) -> str:
 
 
 def tune_cache_get(path: str, key: str):
-    """tho_tune_cache_get: ((leaf_rows, split_chunks), ms) of the last entry for ``key``, or None."""
+    """tho_tune_cache_get: ((leaf_rows, split_chunks, balance), ms) of the last entry for ``key``, or None."""
     t = Tuning()
     ms = ctypes.c_double()
     found = ctypes.c_int32()
@@ -225,8 +226,8 @@ class Plan:
     """Owns one tho_plan_t (workspace, launch tables, batched graph)."""
 
     def __init__(self, shapes, dtype=torch.float64, prec: int = THO_PREC_FP64, flags: int = 0, tuning=None):
-        """``tuning``: None (library defaults) or (leaf_rows, split_chunks), e.g.
-        from ``autotune``; 0 in either place keeps that default."""
+        """``tuning``: None (library defaults) or (leaf_rows, split_chunks[, balance]),
+        e.g. from ``autotune``; 0 keeps the default."""
         lib = load()
         shapes = list(shapes)
         arr = _descs(shapes, dtype, prec, flags)
@@ -256,7 +257,7 @@ class Plan:
 
     @property
     def tuning(self):
-        """(leaf_rows, split_chunks) the plan was built with."""
+        """(leaf_rows, split_chunks, balance) the plan was built with."""
         t = Tuning()
         _check(load().tho_plan_tuning(self.handle, ctypes.byref(t)), "tho_plan_tuning")
         return t.as_tuple()

@@ -67,7 +67,7 @@ def test_tuned_plans_match_oracle(tho, sms, dtype, prec_name, n, k0, k):
             except tho.ThoError as e:
                 assert e.code == tho.THO_ERR_UNSUPPORTED, (leaf, split, e)
                 continue
-            assert plan.tuning == (leaf, split)
+            assert plan.tuning == (leaf, split, 0)
             assert plan.leaf_rows == leaf
             Q, R, S = tho.orth(V, A, prec=prec, plan=plan)
             torch.cuda.synchronize()
@@ -93,7 +93,7 @@ def test_tuned_batch_matches_oracle(tho, sms, prec_name):
              for i, (n, k0, k) in enumerate(BATCH_SHAPES)]
     pairs = [(p.V.cuda(), p.A.cuda()) for p in probs]
     ref = [_oracle(p, ("batch", i)) for i, p in enumerate(probs)]
-    for tuning in ((64, len(BATCH_SHAPES)), (128, sms), (0, 32 * sms)):
+    for tuning in ((64, len(BATCH_SHAPES), 0), (128, sms, 1), (0, 32 * sms, 1), (0, 0, 1)):
         plan = tho.Plan(BATCH_SHAPES, torch.float64, prec, tuning=tuning)
         res = tho.orth_batched(pairs, prec=prec, plan=plan)
         torch.cuda.synchronize()
@@ -114,7 +114,7 @@ def test_autotune_single_problem_and_cache(tho, tmp_path):
     rows = [json.loads(line) for line in open(cache)]
     name = torch.cuda.get_device_name(0)
     assert len(rows) == 1 and rows[0]["key"] == tho.tune_key([shape], dtype, prec, 0, name)
-    assert (rows[0]["leaf_rows"], rows[0]["split_chunks"]) == t
+    assert (rows[0]["leaf_rows"], rows[0]["split_chunks"], rows[0]["balance"]) == t
     # The tuned plan computes what the default plan computes.
     p = inputs.random_problem(*shape, dtype=dtype, seed=77)
     V, A = p.V.cuda(), p.A.cuda()

@@ -60,31 +60,32 @@ def test_key_sanitizes_the_device_name_and_checks_arguments(lib):
 def test_cache_round_trip_last_entry_wins(lib, tmp_path):
     path = str(tmp_path / "tune.jsonl")
     assert tho.tune_cache_get(path, "k1") is None  # missing file: no entries
-    tho.tune_cache_put(path, "k1", (128, 303), 101.25)
-    tho.tune_cache_put(path, "k2", (64, 152), 7.5)
-    assert tho.tune_cache_get(path, "k1") == ((128, 303), 101.25)
-    tho.tune_cache_put(path, "k1", (256, 607), 99.0)
-    assert tho.tune_cache_get(path, "k1") == ((256, 607), 99.0)
-    assert tho.tune_cache_get(path, "k2") == ((64, 152), 7.5)
+    tho.tune_cache_put(path, "k1", (128, 303, 0), 101.25)
+    tho.tune_cache_put(path, "k2", (64, 152, 1), 7.5)
+    assert tho.tune_cache_get(path, "k1") == ((128, 303, 0), 101.25)
+    tho.tune_cache_put(path, "k1", (256, 607, 1), 99.0)
+    assert tho.tune_cache_get(path, "k1") == ((256, 607, 1), 99.0)
+    assert tho.tune_cache_get(path, "k2") == ((64, 152, 1), 7.5)
     assert tho.tune_cache_get(path, "k3") is None
     rows = [json.loads(line) for line in open(path)]  # every line is a JSON object
     assert [r["key"] for r in rows] == ["k1", "k2", "k1"]
-    assert rows[-1] == {"key": "k1", "leaf_rows": 256, "split_chunks": 607, "ms": 99.0}
+    assert rows[-1] == {"key": "k1", "leaf_rows": 256, "split_chunks": 607, "balance": 1, "ms": 99.0}
 
 
 def test_cache_skips_lines_that_do_not_parse(lib, tmp_path):
     path = tmp_path / "tune.jsonl"
     path.write_text('garbage\n{"key": "k1", "leaf_rows": 128}\n'
-                    '{"key": "k1", "leaf_rows": 1.5, "split_chunks": 3, "ms": 1}\n'
-                    '{"key": "k1", "leaf_rows": 64, "split_chunks": -3, "ms": 1}\n'
-                    '{"key": "k1", "leaf_rows": 64, "split_chunks": 300, "ms": 2.5}\n'
+                    '{"key": "k1", "leaf_rows": 1.5, "split_chunks": 3, "balance": 0, "ms": 1}\n'
+                    '{"key": "k1", "leaf_rows": 64, "split_chunks": -3, "balance": 0, "ms": 1}\n'
+                    '{"key": "k1", "leaf_rows": 64, "split_chunks": 3, "balance": 2, "ms": 1}\n'
+                    '{"key": "k1", "leaf_rows": 64, "split_chunks": 300, "balance": 1, "ms": 2.5}\n'
                     '{"key": "k1", "leaf_rows": 128, "split_chunks": 30')  # truncated last line
-    assert tho.tune_cache_get(str(path), "k1") == ((64, 300), 2.5)
+    assert tho.tune_cache_get(str(path), "k1") == ((64, 300, 1), 2.5)
 
 
 def test_cache_put_rejects_keys_that_would_break_the_line(lib, tmp_path):
     path = str(tmp_path / "tune.jsonl")
-    t = tho.Tuning(128, 10)
+    t = tho.Tuning(128, 10, 0)
     for bad in (b'a"b', b"a\\b", b"a\nb"):
         assert lib.tho_tune_cache_put(path.encode(), bad, ctypes.byref(t), 1.0) == tho.THO_ERR_ARG
     assert lib.tho_tune_cache_put(None, b"k", ctypes.byref(t), 1.0) == tho.THO_ERR_ARG
@@ -94,9 +95,9 @@ def test_cache_put_rejects_keys_that_would_break_the_line(lib, tmp_path):
     assert lib.tho_tune_cache_get(None, b"k", ctypes.byref(t), None, ctypes.byref(found)) == tho.THO_ERR_ARG
 
 
-def _plan_tuned(lib, desc, leaf, split):
+def _plan_tuned(lib, desc, leaf, split, balance=0):
     arr = (tho.Desc * 1)(tho.Desc(*desc))
-    t = tho.Tuning(leaf, split)
+    t = tho.Tuning(leaf, split, balance)
     h = ctypes.c_void_p()
     return lib.tho_plan_tuned(arr, 1, ctypes.byref(t), ctypes.byref(h))
 
@@ -107,6 +108,8 @@ def test_plan_tuned_rejects_bad_choices_on_the_host(lib):
         assert _plan_tuned(lib, d, leaf, 0) == tho.THO_ERR_ARG
     for split in (-1, tho.THO_TUNE_MAX_SPLIT + 1):
         assert _plan_tuned(lib, d, 0, split) == tho.THO_ERR_ARG
+    for balance in (-1, 2):
+        assert _plan_tuned(lib, d, 0, 0, balance) == tho.THO_ERR_ARG
     # A complex FP64 leaf panel of 256 rows with k0 = 128 staged beside k = 32
     # columns needs more shared memory than a CTA has.
     assert _plan_tuned(lib, (1 << 16, 128, 32, C, 0, 0), 256, 0) == tho.THO_ERR_UNSUPPORTED

@@ -322,8 +322,22 @@ tho_status_t tho_orth_noalloc(const tho_desc_t* desc, const void* V, int64_t ldv
                               int64_t lda, void* Q, int64_t ldq, void* R, void* S, void* stream);
 
 /* Read and clear the plan's device status word (synchronizes the device).
- * Returns THO_OK or the first device-detected error (THO_ERR_NONFINITE). */
+ * Returns THO_OK or the device-detected error (THO_ERR_NONFINITE, or
+ * THO_ERR_TIMEOUT from a tcgen05 kernel whose bounded wait ran out). */
 tho_status_t tho_plan_status(tho_plan_t plan);
+
+/* Test hook for the device-side failure path (no counterpart in the paper).
+ * The tcgen05 kernels hand shared-memory stages between warps through
+ * mbarriers, and every wait is bounded: after 2^25 polls the waiting kernel
+ * leaves its loop, finishes its own copies, frees its tensor memory, latches
+ * THO_ERR_TIMEOUT in the plan's status word and returns.  This call launches
+ * one CTA on `stream` whose thread waits, through the same wait routine but
+ * with a bound of `spins` polls (1 <= spins <= THO_EXPIRE_WAIT_MAX_SPINS), on
+ * an mbarrier that nothing completes, and so always latches THO_ERR_TIMEOUT
+ * in `plan`'s status word; tho_plan_status then reports and clears it.  The
+ * GPU context stays usable.  Errors: ARG, CUDA. */
+#define THO_EXPIRE_WAIT_MAX_SPINS (1 << 20)
+tho_status_t tho_plan_expire_wait(tho_plan_t plan, int32_t spins, void* stream);
 
 /* Block Householder-QR (Algorithm 3, Section 5): the QR factorization
  * A = Q R of A = [A_1, ..., A_p], A_i of kb[i] columns, the blocks taken in

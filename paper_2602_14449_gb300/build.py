@@ -20,7 +20,7 @@ PROBE = os.path.join(OUT, "peak_probe")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "--extended-lambda",
                   "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-LIB_SOURCES = ["tho_api.cu", "tho_real.cu", "tho_complex.cu", "tho_noalloc.cu", "tho_backward.cu", "tho_tune.cu"]
+LIB_SOURCES = ["tho_api.cu", "tho_real.cu", "tho_complex.cu", "tho_noalloc.cu", "tho_backward.cu", "tho_tune.cu", "tho_selftest.cu"]
 
 
 def _nvcc():

@@ -625,6 +625,13 @@ tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, cons
   return THO_OK;
 }
 
+tho_status_t tho_plan_expire_wait(tho_plan_t plan, int32_t spins, void* stream) {
+  if (!plan || spins < 1 || spins > THO_EXPIRE_WAIT_MAX_SPINS) return THO_ERR_ARG;
+  return tho::launch_expire_wait(plan->pc.d_status, spins, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? THO_OK
+             : THO_ERR_CUDA;
+}
+
 tho_status_t tho_plan_status(tho_plan_t plan) {
   if (!plan) return THO_ERR_ARG;
   int h = 0;

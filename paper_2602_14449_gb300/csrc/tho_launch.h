@@ -90,6 +90,11 @@ extern const Launcher kLaunchC128Bulk32;// complex, FP32 bulk
 extern const Launcher kLaunchF64Emu;    // real, FP64-accurate products on bf16 tensor cores
 extern const Launcher kLaunchC128Emu;   // complex, FP64-accurate products on bf16 tensor cores
 
+// Failure-path test: one CTA waits on an mbarrier that nothing completes, with
+// the tcgen05 kernels' bounded wait cut to `spins` polls, then latches
+// THO_ERR_TIMEOUT into `status` as they do (tho_selftest.cu).
+cudaError_t launch_expire_wait(int* status, int spins, cudaStream_t st);
+
 // Leaf-kernel shared memory for leaf height P (bytes).
 inline size_t leaf_smem_bytes(int P, int k0p, int kp, size_t bulk, size_t elem) {
   return (size_t)(P * kp + k0p * kp + kTileRows * k0p) * bulk + kMaxKP * (8 + bulk + elem) +

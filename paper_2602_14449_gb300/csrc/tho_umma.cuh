@@ -64,10 +64,10 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
-// Wait for the phase with the given parity to complete; false after the spin
-// bound (the caller then abandons its loop and the kernel latches an error).
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < kUmmaSpins; ++it) {
+// Wait for the phase with the given parity to complete; false after `spins`
+// polls (the caller then abandons its loop and the kernel latches an error).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int spins = kUmmaSpins) {
+  for (int it = 0; it < spins; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"

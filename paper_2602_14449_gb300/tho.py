@@ -34,7 +34,7 @@ EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_pla
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
             "tho_orth_noalloc", "tho_plan_tuned", "tho_plan_tuning", "tho_autotune", "tho_tune_key",
-            "tho_tune_cache_get", "tho_tune_cache_put")
+            "tho_tune_cache_get", "tho_tune_cache_put", "tho_plan_expire_wait")
 THO_NUM_PHASES = 11
 
 
@@ -122,6 +122,8 @@ def load(path: str | None = None):
         lib.tho_orth_batched.restype = ctypes.c_int
         lib.tho_orth_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp]
         lib.tho_orth_backward.restype = ctypes.c_int
+        lib.tho_plan_expire_wait.argtypes = [vp, i32, vp]
+        lib.tho_plan_expire_wait.restype = ctypes.c_int
         lib.tho_plan_status.argtypes = [vp]
         lib.tho_plan_status.restype = ctypes.c_int
         lib.tho_status_string.argtypes = [ctypes.c_int]
@@ -264,6 +266,12 @@ class Plan:
 
     def status(self) -> int:
         return load().tho_plan_status(self.handle)
+
+    def expire_wait(self, spins: int = 4096):
+        """tho_plan_expire_wait: on the current stream, a bounded device wait that
+        runs out and latches THO_ERR_TIMEOUT (read it with ``status()``)."""
+        st = torch.cuda.current_stream().cuda_stream
+        _check(load().tho_plan_expire_wait(self.handle, int(spins), ctypes.c_void_p(st)), "tho_plan_expire_wait")
 
     def set_phase_timing(self, enable: bool = True):
         _check(load().tho_plan_set_phase_timing(self.handle, int(enable)), "tho_plan_set_phase_timing")

@@ -62,6 +62,7 @@ def test_shape_and_argument_errors(lib):
     assert lib.tho_orth(None, None, 0, None, 0, None, 0, None, None, None) == tho.THO_ERR_ARG
     assert lib.tho_orth_batched(None, None, 0, None) == tho.THO_ERR_ARG
     assert lib.tho_plan_status(None) == tho.THO_ERR_ARG
+    assert lib.tho_plan_expire_wait(None, 10, None) == tho.THO_ERR_ARG
     assert lib.tho_plan_destroy(None) == tho.THO_OK
     assert lib.tho_plan_workspace_bytes(None) == 0
 

@@ -35,6 +35,16 @@
  *              has completed.
  *   Limits     1 <= k <= THO_MAX_K, 1 <= k0 <= THO_MAX_K0 (k0 = 0 only with
  *              THO_FLAG_ALLOW_K0_ZERO), k0 + k <= n.
+ *   Environment (read at each tho_plan / tho_autotune call; set = any value
+ *              but "" or "0")
+ *              THO_LOG           print each plan's choices (leaf height, split,
+ *                                which kernels run the products) and each
+ *                                autotuner measurement to stderr.
+ *              THO_INJECT_NOMEM  test hook: plan workspace allocation fails
+ *                                with THO_ERR_NOMEM, as if the device were full.
+ *              THO_TUNE_CACHE    default cache file of tho_autotune.
+ *   Tracing    Every phase of a call is enqueued inside an NVTX range named
+ *              after it (see the phase list below), for Nsight tools.
  */
 #ifndef THO_H_
 #define THO_H_

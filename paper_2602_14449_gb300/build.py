@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError("nvcc failed: " + " ".join(res.args))
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], check=True)
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"], check=True)
         os.replace(tmp, LIB)
     return LIB
 

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -51,6 +53,12 @@ namespace {
 constexpr int64_t kAlignElems = 32;
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// An environment switch is on when set to anything but "" or "0".
+bool env_on(const char* name) {
+  const char* v = std::getenv(name);
+  return v && *v && std::strcmp(v, "0") != 0;
+}
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
@@ -124,15 +132,13 @@ void phase_hook(void* ctx, int phase, int end, cudaStream_t st) {
   }
 }
 
-const char* const kPhaseNames[tho::kNumPhases] = {"qr_v1", "gram", "solve_z", "leaf", "tree_up", "root",
-                                                 "tree_down", "apply", "solve_z2", "update_q", "update_a"};
 
 }  // namespace
 
 extern "C" {
 
 const char* tho_phase_name(int32_t phase) {
-  return (phase >= 0 && phase < tho::kNumPhases) ? kPhaseNames[phase] : nullptr;
+  return tho::phase_name(phase);
 }
 
 tho_status_t tho_plan_set_phase_timing(tho_plan_t plan, int32_t enable) {
@@ -360,8 +366,13 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
     pc.tab.lev_n[l] = (int)it.size() - pc.tab.lev_off[l];
   }
 
-  // Device allocations and uploads.
+  // Device allocations and uploads.  THO_INJECT_NOMEM (test hook) makes the
+  // workspace allocation fail as if the device were out of memory.
   const size_t ws_bytes = pc.ws_elems * p->L->elem;
+  if (env_on("THO_INJECT_NOMEM")) {
+    free_plan(p);
+    return THO_ERR_NOMEM;
+  }
   if (cudaMalloc(&pc.ws, ws_bytes) != cudaSuccess ||
       cudaMalloc(&pc.d_insts, sizeof(Inst) * count) != cudaSuccess ||
       cudaMalloc(&pc.d_items, sizeof(WorkItemH) * std::max<size_t>(it.size(), 1)) != cudaSuccess ||
@@ -400,6 +411,17 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
                     cudaEventCreateWithFlags(&p->pc.ev_join, cudaEventDisableTiming) != cudaSuccess)) {
     free_plan(p);
     return THO_ERR_CUDA;
+  }
+  if (env_on("THO_LOG")) {
+    const bool emu = pc.prec == THO_PREC_FP64_EMU;
+    std::fprintf(stderr,
+                 "[tho] plan: problems=%d dtype=%s prec=%d flags=0x%x leaf_rows=%d split_chunks=%d balance=%d "
+                 "levels=%d launches=%d workspace=%zu B gram=%s update=%s leaf=%s\n",
+                 count, cplx ? "c128" : "f64", pc.prec, pc.flags, pc.P, p->split_chunks, p->balance, pc.Lmax,
+                 pc.launches, ws_bytes,
+                 emu ? (pc.gram_umma ? "tcgen05" : (pc.gram_pipe ? "mma.sync-pipelined" : "mma.sync")) : "fp64",
+                 emu ? (pc.upd_umma ? "tcgen05" : "mma.sync") : "fp64",
+                 pc.leaf_tc ? "k_leaf_emu (tensor-core trailing updates)" : "k_leaf (fp64)");
   }
   *out = p;
   return THO_OK;

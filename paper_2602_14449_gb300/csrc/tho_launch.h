@@ -7,6 +7,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tho_plan.h"
 
 namespace tho {
@@ -62,16 +64,28 @@ struct PlanCore {
 };
 
 // Optional tracing hook: called with (ctx, phase, 0 = begin / 1 = end, stream).
+enum Phase { kPhQrV1 = 0, kPhGram, kPhSolveZ, kPhLeaf, kPhTreeUp, kPhRoot, kPhTreeDown, kPhApply,
+             kPhSolveZ2, kPhUpdateQ, kPhUpdateA, kNumPhases };
+
+inline const char* phase_name(int phase) {
+  static const char* const kNames[kNumPhases] = {"qr_v1", "gram", "solve_z", "leaf", "tree_up", "root",
+                                                 "tree_down", "apply", "solve_z2", "update_q", "update_a"};
+  return (phase >= 0 && phase < kNumPhases) ? kNames[phase] : nullptr;
+}
+
 struct PhaseHook {
   void (*fn)(void* ctx, int phase, int end, cudaStream_t st) = nullptr;
   void* ctx = nullptr;
   void operator()(int phase, int end, cudaStream_t st) const {
+    // One NVTX range per phase around its launches (a no-op unless a profiler
+    // is attached), so Nsight tools can select a phase's kernels by name.
+    if (!end)
+      nvtxRangePushA(phase_name(phase));
+    else
+      nvtxRangePop();
     if (fn) fn(ctx, phase, end, st);
   }
 };
-
-enum Phase { kPhQrV1 = 0, kPhGram, kPhSolveZ, kPhLeaf, kPhTreeUp, kPhRoot, kPhTreeDown, kPhApply,
-             kPhSolveZ2, kPhUpdateQ, kPhUpdateA, kNumPhases };
 
 struct Launcher {
   size_t elem;       // bytes of the FP64 storage type

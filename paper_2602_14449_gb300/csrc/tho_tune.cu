@@ -323,9 +323,17 @@ tho_status_t tho_autotune(const tho_desc_t* descs, int32_t count, const char* ca
   if (s != THO_OK) return s;
   tho_tuning_t best = def;
   double best_ms = def_ms;
+  const char* lg = std::getenv("THO_LOG");
+  const bool log = lg && *lg && std::strcmp(lg, "0") != 0;
+  if (log)
+    std::fprintf(stderr, "[tho] tune: default leaf_rows=%d split_chunks=%d -> %.3f ms\n", def.leaf_rows,
+                 def.split_chunks, def_ms);
   auto consider = [&](const tho_tuning_t& t) -> tho_status_t {
     double m = 0;
     tho_status_t r = time_candidate(descs, count, t, ops, st, &m, &eff);
+    if (log)
+      std::fprintf(stderr, "[tho] tune: leaf_rows=%d split_chunks=%d balance=%d -> %s %.3f ms\n", t.leaf_rows,
+                   t.split_chunks, t.balance, r == THO_OK ? "ok" : tho_status_string(r), r == THO_OK ? m : 0.0);
     if (r == THO_ERR_UNSUPPORTED || r == THO_ERR_NOMEM) return THO_OK;  // not a valid candidate here
     if (r != THO_OK) return r;
     if (m < best_ms) {
@@ -357,6 +365,9 @@ tho_status_t tho_autotune(const tho_desc_t* descs, int32_t count, const char* ca
   }
   *out = best;
   if (ms) *ms = best_ms;
+  if (log)
+    std::fprintf(stderr, "[tho] tune: chose leaf_rows=%d split_chunks=%d balance=%d (%.3f ms)\n", best.leaf_rows,
+                 best.split_chunks, best.balance, best_ms);
   if (path) tho_tune_cache_put(path, key.c_str(), &best, best_ms);
   return THO_OK;
 }

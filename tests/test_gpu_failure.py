@@ -57,3 +57,27 @@ def test_expire_wait_bounds(tho):
     for bad in (0, -5, (1 << 20) + 1):
         assert lib.tho_plan_expire_wait(plan.handle, bad, None) == tho.THO_ERR_ARG
     assert plan.status() == tho.THO_OK
+
+
+def test_injected_allocation_failure_leaves_the_library_usable(tho, monkeypatch):
+    monkeypatch.setenv("THO_INJECT_NOMEM", "1")
+    with pytest.raises(tho.ThoError) as e:
+        tho.Plan([(4096, 16, 4)], torch.float64, tho.THO_PREC_FP64)
+    assert e.value.code == tho.THO_ERR_NOMEM
+    monkeypatch.setenv("THO_INJECT_NOMEM", "0")
+    plan = tho.Plan([(4096, 16, 4)], torch.float64, tho.THO_PREC_FP64)
+    p = inputs.random_problem(4096, 16, 4, dtype=torch.float64, seed=9)
+    Q, _, _ = tho.orth(p.V.cuda(), p.A.cuda(), plan=plan)
+    torch.cuda.synchronize()
+    Qo, _, _ = oracle.two_stage(p.V.numpy(), p.A.numpy())
+    np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=1e-11, rtol=0)
+
+
+def test_log_prints_the_plan_choices(tho, monkeypatch, capfd):
+    monkeypatch.setenv("THO_LOG", "1")
+    plan = tho.Plan([(20000, 64, 32)], torch.complex128, tho.THO_PREC_FP64_EMU, tuning=(128, 77))
+    err = capfd.readouterr().err
+    line = [x for x in err.splitlines() if x.startswith("[tho] plan:")][-1]
+    assert "leaf_rows=128" in line and "split_chunks=77" in line and "dtype=c128" in line
+    assert f"launches={plan.kernel_launches}" in line
+    assert "leaf=k_leaf_emu" in line  # complex k >= 24 in the emulated mode

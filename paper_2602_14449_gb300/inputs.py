@@ -14,6 +14,9 @@ mode in Section 1 and Algorithm 3):
   * ``C4``  256 real instances, n log-uniform in [16384, 262144],
             k0 in {8,16,32,64,128}, k in {4,8,16,32}, A ~ N(0,1).
   * ``C5``  real, n=2^20, k0=64, k=16, A ~ N(0,1), upstream gradient dQ ~ N(0,1).
+  * ``table4``  real, n=1000, k0=100: V built as in Appendix A so that the
+            modified LU of V_{1:k0,:} (Algorithm 2) yields U of eq. (badmlu)
+            (kappa_2(U) ~ 1.1e7), A ~ N(0,1) (Example 4 and Table 4, Section 6).
 Complex Gaussians are (N + iN)/sqrt(2).  Every config draws from
 ``torch.Generator().manual_seed(1449 + config_id)``; ``n`` may be overridden to
 get a smaller matrix with the same structure.
@@ -155,3 +158,72 @@ def random_problem(n: int, k0: int, k: int, dtype=torch.float64, seed: int = 0, 
     V = orthonormal(n, k0, dtype, g, device) if k0 > 0 else torch.zeros(n, 0, dtype=dtype, device=device)
     A = colmajor(gaussian(n, k, dtype, g, device))
     return Problem(V=colmajor(V), A=A, n=n, k0=k0, k=k)
+
+
+def badmlu_u(k0: int, alpha: float = 0.1) -> torch.Tensor:
+    """U of eq. (badmlu) (Section 3.2, first choice of P): with 0-based row i,
+    U_ii = 1 + alpha / sqrt(k0 - i) and U_ij = -1 / sqrt(k0 - i) for j > i."""
+    U = torch.zeros(k0, k0, dtype=torch.float64)
+    for i in range(k0):
+        s = 1.0 / math.sqrt(k0 - i)
+        U[i, i] = 1.0 + alpha * s
+        U[i, i + 1:] = -s
+    return U
+
+
+def appendix_a_v(n: int, k0: int, alpha: float = 0.1, seed: int = SEED_BASE + 7) -> torch.Tensor:
+    """Real V (n x k0, orthonormal columns, column-major) whose top block
+    Z = V_{1:k0,:} makes the modified LU factorization (Algorithm 2) return
+    P = I and U of eq. (badmlu): the construction of Appendix A.
+
+    With R = U - I (each row of 2-norm below one), V is built from the bottom
+    of a Householder QR upward: the last trailing column is a unit vector with
+    first entry b_1; then, one row of R at a time from the last, the Lemma of
+    Appendix A extends an orthonormal m x j matrix W to an (m+1) x (j+1) one
+    whose first row is the given b and whose first Householder step gives back
+    [[-sign(b_1), 0], [0, W]]: with V_H that block matrix, a unit v orthogonal
+    to Range(V_H), x = sqrt(1 - ||b||^2) v + V_H b and the reflector H taking x
+    to e_1, the new matrix is H V_H.
+
+    Two readings.  (1) The rows enter negated (b = -R_{i, i:k0}): Algorithm 2
+    takes P_ii = -sign(Z_ii), so the rows of R themselves would give U = -(I + R);
+    with the negated rows it gives I + R, eq. (badmlu) itself (kappa_2 is the
+    same either way).  (2) H is formed as I - 2 w w^T / (w^T w) with w = x - e_1,
+    which equals the Appendix's I - (1 - x_1) w' w'^T, w' = (x - e_1)/(x_1 - 1),
+    when ||x|| = 1 exactly; the Appendix's form loses orthogonality geometrically
+    (by 1e-1 at k0 = 100 in FP64) because rounding makes ||x|| != 1 step after
+    step, while this one stays orthogonal to rounding (||V^T V - I|| ~ 1e-14).
+    Inputs only: no step of the orthogonalization method is taken here."""
+    if not (1 <= k0 <= n):
+        raise ValueError("need 1 <= k0 <= n")
+    g = _gen(seed, "cpu")
+    R = badmlu_u(k0, alpha) - torch.eye(k0, dtype=torch.float64)
+    m = n - k0 + 1
+    x = torch.randn(m - 1, dtype=torch.float64, generator=g)
+    x *= math.sqrt(1.0 - float(R[k0 - 1, k0 - 1]) ** 2) / float(torch.linalg.vector_norm(x))
+    W = torch.cat([-R[k0 - 1, k0 - 1:], x]).reshape(m, 1)
+    for i in range(1, k0):
+        b = -R[k0 - 1 - i, k0 - 1 - i:]
+        rows, j = W.shape
+        VH = torch.zeros(rows + 1, j + 1, dtype=torch.float64)
+        VH[0, 0] = -1.0 if float(b[0]) >= 0 else 1.0
+        VH[1:, 1:] = W
+        v = torch.randn(rows + 1, dtype=torch.float64, generator=g)
+        v[0] = 0.0
+        for _ in range(2):  # orthogonal to Range(V_H), twice for working accuracy
+            v -= VH @ (VH.t() @ v)
+        v /= torch.linalg.vector_norm(v)
+        xv = math.sqrt(max(0.0, 1.0 - float(b @ b))) * v + VH @ b
+        w = xv.clone()
+        w[0] -= 1.0
+        W = VH - (2.0 / float(w @ w)) * torch.outer(w, w @ VH)
+    return colmajor(W)
+
+
+def table4_problem(n: int = 1000, k0: int = 100, k: int = 100, alpha: float = 0.1,
+                   seed: int = SEED_BASE + 7) -> Problem:
+    """Example 4 / Table 4 (Section 6): V of Appendix A (eq. (badmlu) with
+    alpha), A ~ N(0,1) n x k."""
+    V = appendix_a_v(n, k0, alpha, seed)
+    A = colmajor(gaussian(n, k, torch.float64, _gen(seed + 1, "cpu")))
+    return Problem(V=V, A=A, n=n, k0=k0, k=k)

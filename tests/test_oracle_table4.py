@@ -6,9 +6,11 @@ returns the ill-conditioned U of eq. (badmlu), Algorithm 1 with the first choice
 of P loses orthogonality to ~1e-6 while the second and third choices stay at
 ~1e-15.  These tests check the oracle's modified_lu, two_stage_mlu (first
 choice), two_stage (second) and two_stage_polar (third) against those printed
-values: the unstable figures to within a factor of 10 either way (they are
-rounding errors amplified by kappa_2(U); the inputs are a fresh draw of the
-recipe), the stable ones to below 10x the printed figure.
+values: the unstable figures from 1/100 to 10 times the printed ones (they are
+rounding errors amplified by kappa_2(U), so they depend on the draw of the
+recipe and on the host's rounding: 2.4e-7 to 4.3e-6 for ||Q^*Q - I|| over the
+seeds and hosts tried, printed 3.51e-6), the stable ones to below 10x the
+printed figure.
 """
 import json
 import os
@@ -63,7 +65,7 @@ def table4():
 
 def test_table4_first_choice_loses_orthogonality_as_printed(table4):
     for got, printed in zip(table4["choice1"], GOLDEN["table4"]["choice1"]):
-        assert printed / 10 <= got <= printed * 10, (got, printed)
+        assert printed / 100 <= got <= printed * 10, (got, printed)
 
 
 @pytest.mark.parametrize("choice", ["choice2", "choice3"])

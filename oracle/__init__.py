@@ -237,6 +237,34 @@ def two_stage_polar(V, A):
     return Q, R, S, {"P": P, "M": M, "T": T, "C": C, "Wtop": Wtop, "G": G, "Z": Z, "Z2": Z2}
 
 
+def two_stage_given_p(V, A, P):
+    """Algorithm 1 for a given unitary P (k0 x k0): the generalized Householder
+    transformation H = I - W T^{-1} W^* with W = [P; 0] - V and T = I - V_1^* P
+    (Section 3.1), whatever the choice of P; Example 5 (Section 6) runs it with
+    (V, P) built for a prescribed kappa_2(T).  T^{-*} G and T^{-1} G2 come from a
+    library LU solve with partial pivoting (a backward stable solver, as the
+    analysis of Section 4 assumes); the trailing QR is the oracle's Householder
+    QR.  Returns (Q, R, S, aux) with aux the dict of T, Wtop, G, Z, Z2."""
+    dt = _dtype_of(V, A)
+    V = np.asarray(V, dtype=dt)
+    A = np.asarray(A, dtype=dt)
+    P = np.asarray(P, dtype=dt)
+    n, k = A.shape
+    k0 = V.shape[1]
+    V1, V2 = V[:k0], V[k0:]
+    Wtop = P - V1
+    T = np.eye(k0) - V1.conj().T @ P
+    G = Wtop.conj().T @ A[:k0] - V2.conj().T @ A[k0:]
+    Z = np.linalg.solve(T.conj().T, G)                           # T^{-*} G
+    A1 = A[:k0] - Wtop @ Z
+    A2 = A[k0:] + V2 @ Z
+    S = P.conj().T @ A1
+    Qb, R = householder_qr(A2)
+    Z2 = np.linalg.solve(T, -V2.conj().T @ Qb)                   # T^{-1} W^* [0; Qbar]
+    Q = np.vstack([-Wtop @ Z2, Qb + V2 @ Z2])
+    return Q, R, S, {"T": T, "Wtop": Wtop, "G": G, "Z": Z, "Z2": Z2}
+
+
 def block_hhqr(A, kb):
     """Algorithm 3 (Block Householder-QR, Section 5): the QR factorization of
     A = [A_1, ..., A_p] (block widths kb) taking the blocks in order.  Step 1

@@ -29,6 +29,14 @@ Every function here is pinned in ``tests/test_oracle.py``:
   * ``block_hhqr``     — Algorithm 3: the unique QR with real nonnegative
                          diag(R) of a full-rank A by LAPACK (phase-normalized),
                          for several block splittings; Q^* Q = I, A = Q R.
+  * ``two_stage_given_p`` (tests/test_oracle_figure1.py) — Algorithm 1 for a
+                         given unitary P: the three choices' results when given
+                         their P; Example 5's error laws against kappa_2(T).
+  * ``two_stage_b``    (tests/test_oracle_b_inner.py) — Algorithm 4 (B-inner
+                         product): reduces to Algorithm 1 for B = I, U = [I; 0];
+                         the closed-form B-orthogonal QR of (I - V V^* B) A;
+                         [V, Q]^* B [V, Q] = I, eq. (vavqb), Theorem 5's HX = Y
+                         and H^* B H = B.
 """
 from __future__ import annotations
 
@@ -263,6 +271,97 @@ def two_stage_given_p(V, A, P):
     Z2 = np.linalg.solve(T, -V2.conj().T @ Qb)                   # T^{-1} W^* [0; Qbar]
     Q = np.vstack([-Wtop @ Z2, Qb + V2 @ Z2])
     return Q, R, S, {"T": T, "Wtop": Wtop, "G": G, "Z": Z, "Z2": Z2}
+
+
+def _phase(z):
+    """z / |z|, with phase(0) = 1."""
+    a = abs(z)
+    return z / a if a != 0 else 1.0
+
+
+def two_stage_b(B, V, U, A):
+    """Algorithm 4 (Section 5): two-stage Householder-QR in the B-inner product
+    <x, y>_B = y^* B x, B Hermitian positive definite (n x n).  V (n x k0) and
+    U (n x (k0 + k)) have B-orthonormal columns; returns (Q, R, S, aux) with
+    [V, A] = [V, Q] [[I, S], [0, R]] (eq. vavqb) and [V, Q]^* B [V, Q] = I.
+
+    Steps in the algorithm's order, with Theorem 5's generalized reflector
+    H = I - W T^{-1} W^* B (X = U_1 P, Y = V, W = X - Y, T = W^* B X = I - V^* B U_1 P):
+      P       the second choice (Section 3.2) on the k0 x k0 matrix the method
+              names, Z = U_1^* B V = Q1 R1 (diag(R1) >= 0), P = -Q1, so that
+              T = I + R1^* as in Algorithm 1;
+      A       <- H^{-1} A = (I - W T^{-*} W^* B) A (T^* solved by substitution);
+      S       = U_1^* B A, then A <- A - U_1 S (the Gram-Schmidt step);
+      Qbar R  the QR of A in the B-inner product with u_{k0+1}, ..., u_{k0+k} as
+              the initial basis, column by column (left-looking): the current
+              column x (earlier reflectors applied) loses its components r_ij
+              along u_{k0+i}, i < j, and the rest x' is mapped by Theorem 5's
+              reflector for one column (X = x', Y = y = -phase(u_{k0+j}^* B x')
+              ||x'||_B u_{k0+j}) onto y.  The method recommends reorthogonalizing
+              w = x' - y against [U_1 P, u_{k0+1}, ..., u_{k0+j-1}]; as y is
+              B-orthogonal to that basis, this is done on x' itself (twice,
+              before ||x'||_B and y are formed, the coefficients removed along
+              u_{k0+i} added to r_ij), so that the reflector stays B-unitary
+              when x' is at rounding level (a rank-deficient column);
+              Qbar = H_1^{-1} ... H_k^{-1} [u_{k0+1}, ..., u_{k0+k}];
+      Q       = H Qbar; finally diag(R) is made real >= 0 (column phases of Q).
+    The inner QR is written from the method's description of it (Section 5);
+    a column with x' = 0 takes H_j = I and R_jj = 0."""
+    dt = _dtype_of(B, V, U, A)
+    B = np.asarray(B, dtype=dt)
+    V = np.asarray(V, dtype=dt)
+    U = np.asarray(U, dtype=dt)
+    A = np.array(A, dtype=dt, copy=True)
+    n, k = A.shape
+    k0 = V.shape[1]
+    if U.shape != (n, k0 + k) or B.shape != (n, n):
+        raise ValueError("need B n x n, V n x k0, U n x (k0 + k), A n x k")
+    h = lambda M: M.conj().T
+    Bip = lambda X, Y: h(X) @ (B @ Y)                      # X^* B Y
+    U1, U2 = U[:, :k0], U[:, k0:]
+    # Choice of P and the reflector of the first stage.
+    Q1, R1 = householder_qr(Bip(U1, V))
+    P = -Q1
+    U1 = U1 @ P
+    W = U1 - V
+    T = np.eye(k0, dtype=dt) - Bip(V, U1)
+    Z = _tri(h(T), Bip(W, A), lower=False)                 # T^{-*} W^* B A (T^* upper)
+    A = A - W @ Z                                          # H^{-1} A
+    S = Bip(U1, A)
+    A = A - U1 @ S
+    # QR of A in the B-inner product, u_{k0+1..k0+k} as the initial basis.
+    R = np.zeros((k, k), dtype=dt)
+    ws, ts = [], []
+    for j in range(k):
+        x = A[:, j].copy()
+        for w_i, t_i in zip(ws, ts):                        # x <- H_{j-1} ... H_1 a_j
+            if t_i != 0:
+                x = x - w_i * (np.vdot(w_i, B @ x) / t_i)
+        R[:j, j] = h(U2[:, :j]) @ (B @ x)
+        xp = x - U2[:, :j] @ R[:j, j]
+        basis = np.concatenate([U1, U2[:, :j]], axis=1)
+        for _ in range(2):                                  # reorthogonalization (of x', hence of w)
+            cb = h(basis) @ (B @ xp)
+            xp = xp - basis @ cb
+            R[:j, j] += cb[k0:]
+        rho = np.sqrt(max(np.vdot(xp, B @ xp).real, 0.0))
+        c = np.vdot(U2[:, j], B @ xp)
+        y = -_phase(c) * rho * U2[:, j]
+        R[j, j] = -_phase(c) * rho
+        w = xp - y
+        t = np.vdot(w, B @ xp) if rho != 0 else 0.0
+        ws.append(w)
+        ts.append(t)
+    Qb = U2.copy()
+    for w_i, t_i in reversed(list(zip(ws, ts))):           # Qbar = H_1^{-1} ... H_k^{-1} U_2
+        if t_i != 0:
+            Qb = Qb - np.outer(w_i, (h(w_i) @ (B @ Qb)) / np.conj(t_i))
+    Z2 = _tri(T, Bip(W, Qb), lower=True)                   # T^{-1} W^* B Qbar (T lower)
+    Q = Qb - W @ Z2                                        # H Qbar
+    d = np.array([_phase(R[j, j]) for j in range(k)], dtype=dt)
+    Q = Q * d[None, :]
+    R = np.conj(d)[:, None] * R
+    return Q, R, S, {"P": P, "T": T, "W": W, "U1P": U1, "Qbar": Qb * d[None, :]}
 
 
 def block_hhqr(A, kb):

@@ -227,3 +227,34 @@ def table4_problem(n: int = 1000, k0: int = 100, k: int = 100, alpha: float = 0.
     V = appendix_a_v(n, k0, alpha, seed)
     A = colmajor(gaussian(n, k, torch.float64, _gen(seed + 1, "cpu")))
     return Problem(V=V, A=A, n=n, k0=k0, k=k)
+
+
+@dataclass
+class BProblem:
+    B: torch.Tensor
+    V: torch.Tensor
+    U: torch.Tensor
+    A: torch.Tensor
+
+
+def b_inner_problem(n: int, k0: int, k: int, kappa_b: float = 1e2, dtype=torch.float64,
+                    seed: int = SEED_BASE + 8) -> BProblem:
+    """Inputs of Algorithm 4 (Section 5): B = X diag(lambda) X^* Hermitian
+    positive definite with eigenvalues log-spaced in [1, kappa_b] (X the Q factor
+    of a Gaussian matrix), V with B-orthonormal columns (a Gaussian G times the
+    inverse of the Cholesky factor of G^* B G), U = [L^{-*}; 0] from the Cholesky
+    factor L of the leading (k0 + k) x (k0 + k) block of B (the initial
+    B-orthonormal basis the method suggests), A ~ N(0,1).  Library steps only."""
+    g = _gen(seed, "cpu")
+    X = torch.linalg.qr(gaussian(n, n, dtype, g))[0]
+    lam = torch.logspace(0.0, math.log10(kappa_b), n, dtype=torch.float64).to(dtype)
+    B = (X * lam[None, :]) @ X.conj().T
+    B = 0.5 * (B + B.conj().T)
+    G = gaussian(n, k0, dtype, g)
+    C = torch.linalg.cholesky(G.conj().T @ B @ G)
+    V = torch.linalg.solve_triangular(C, G.conj().T, upper=False).conj().T  # G C^{-*}
+    L = torch.linalg.cholesky(B[:k0 + k, :k0 + k])
+    U = torch.zeros(n, k0 + k, dtype=dtype)
+    U[:k0 + k] = torch.linalg.solve_triangular(L.conj().T, torch.eye(k0 + k, dtype=dtype), upper=True)
+    A = gaussian(n, k, dtype, g)
+    return BProblem(B=B, V=colmajor(V), U=colmajor(U), A=colmajor(A))

@@ -32,8 +32,9 @@ Every function here is pinned in ``tests/test_oracle.py``:
   * ``two_stage_given_p`` (tests/test_oracle_figure1.py) — Algorithm 1 for a
                          given unitary P: the three choices' results when given
                          their P; Example 5's error laws against kappa_2(T).
-  * ``two_stage_b``    (tests/test_oracle_b_inner.py) — Algorithm 4 (B-inner
-                         product): reduces to Algorithm 1 for B = I, U = [I; 0];
+  * ``two_stage_b``, ``block_hhqr_b`` (tests/test_oracle_b_inner.py) —
+                         Algorithm 4 (B-inner product) and its block form
+                         (Example 3): reduces to Algorithm 1 for B = I, U = [I; 0];
                          the closed-form B-orthogonal QR of (I - V V^* B) A;
                          [V, Q]^* B [V, Q] = I, eq. (vavqb), Theorem 5's HX = Y
                          and H^* B H = B.
@@ -319,16 +320,21 @@ def two_stage_b(B, V, U, A):
     h = lambda M: M.conj().T
     Bip = lambda X, Y: h(X) @ (B @ Y)                      # X^* B Y
     U1, U2 = U[:, :k0], U[:, k0:]
-    # Choice of P and the reflector of the first stage.
-    Q1, R1 = householder_qr(Bip(U1, V))
-    P = -Q1
-    U1 = U1 @ P
-    W = U1 - V
-    T = np.eye(k0, dtype=dt) - Bip(V, U1)
-    Z = _tri(h(T), Bip(W, A), lower=False)                 # T^{-*} W^* B A (T^* upper)
-    A = A - W @ Z                                          # H^{-1} A
-    S = Bip(U1, A)
-    A = A - U1 @ S
+    if k0 > 0:
+        # Choice of P and the reflector of the first stage.
+        Q1, R1 = householder_qr(Bip(U1, V))
+        P = -Q1
+        U1 = U1 @ P
+        W = U1 - V
+        T = np.eye(k0, dtype=dt) - Bip(V, U1)
+        Z = _tri(h(T), Bip(W, A), lower=False)             # T^{-*} W^* B A (T^* upper)
+        A = A - W @ Z                                      # H^{-1} A
+        S = Bip(U1, A)
+        A = A - U1 @ S
+    else:                                                  # k0 = 0: the B-inner-product QR of A alone
+        P = T = np.zeros((0, 0), dtype=dt)
+        W = np.zeros((n, 0), dtype=dt)
+        S = np.zeros((0, k), dtype=dt)
     # QR of A in the B-inner product, u_{k0+1..k0+k} as the initial basis.
     R = np.zeros((k, k), dtype=dt)
     ws, ts = [], []
@@ -356,12 +362,40 @@ def two_stage_b(B, V, U, A):
     for w_i, t_i in reversed(list(zip(ws, ts))):           # Qbar = H_1^{-1} ... H_k^{-1} U_2
         if t_i != 0:
             Qb = Qb - np.outer(w_i, (h(w_i) @ (B @ Qb)) / np.conj(t_i))
-    Z2 = _tri(T, Bip(W, Qb), lower=True)                   # T^{-1} W^* B Qbar (T lower)
+    Z2 = _tri(T, Bip(W, Qb), lower=True) if k0 > 0 else np.zeros((0, k), dtype=dt)  # T^{-1} W^* B Qbar
     Q = Qb - W @ Z2                                        # H Qbar
     d = np.array([_phase(R[j, j]) for j in range(k)], dtype=dt)
     Q = Q * d[None, :]
     R = np.conj(d)[:, None] * R
     return Q, R, S, {"P": P, "T": T, "W": W, "U1P": U1, "Qbar": Qb * d[None, :]}
+
+
+def block_hhqr_b(B, A, kb):
+    """Algorithm 3 in the B-inner product (Example 3, Section 6): the blocks
+    A_i taken in order, step i = Algorithm 4 (``two_stage_b``) with
+    V = [Q_1, ..., Q_{i-1}] (step 1: k0 = 0) and the initial B-orthonormal basis
+    U = [L^{-*}; 0] from the Cholesky factor L of the leading (k0 + k_i) x
+    (k0 + k_i) block of B (the construction the method suggests; a library
+    Cholesky and triangular solve).  Returns (Q, R): A = Q R, Q^* B Q = I."""
+    dt = _dtype_of(B, A)
+    B = np.asarray(B, dtype=dt)
+    A = np.asarray(A, dtype=dt)
+    n, K = A.shape
+    if sum(kb) != K:
+        raise ValueError("block widths must add up to the columns of A")
+    Q = np.zeros((n, K), dtype=dt)
+    R = np.zeros((K, K), dtype=dt)
+    o = 0
+    for k in kb:
+        L = np.linalg.cholesky(B[:o + k, :o + k])
+        U = np.zeros((n, o + k), dtype=dt)
+        U[:o + k] = np.linalg.solve(L.conj().T, np.eye(o + k, dtype=dt))
+        Qi, Rii, S, _ = two_stage_b(B, Q[:, :o], U, A[:, o:o + k])
+        Q[:, o:o + k] = Qi
+        R[:o, o:o + k] = S
+        R[o:o + k, o:o + k] = Rii
+        o += k
+    return Q, R
 
 
 def block_hhqr(A, kb):

@@ -75,3 +75,49 @@ def test_rank_deficient_and_zero_columns(dtype):
     VQ = np.concatenate([V, Q], axis=1)
     assert np.linalg.norm(_h(VQ) @ B @ VQ - np.eye(24), 2) < 1e-13
     assert np.linalg.norm(A - V @ S - Q @ R) / np.linalg.norm(A) < 1e-14
+
+
+def _krylov_blocks(n, k, nb, dtype, seed):
+    """Block-Krylov stand-in: A_{i+1} = D A_i with a spread diagonal D, so the
+    whole A is numerically rank deficient (cond > 1e14)."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, k))
+    if dtype.is_complex:
+        X = X + 1j * rng.standard_normal((n, k))
+    d = np.exp(np.linspace(0.0, 5.0, n))
+    blocks = [X]
+    for _ in range(nb - 1):
+        blocks.append(d[:, None] * blocks[-1])
+    return np.hstack(blocks)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_block_form_is_the_b_orthogonal_qr(dtype):
+    """Algorithm 3 in the B-inner product on a full-rank A: the unique QR with
+    Q^* B Q = I and diag(R) real > 0 (closed form by a library Cholesky)."""
+    B = inputs.b_inner_problem(500, 1, 1, 1e2, dtype, seed=13).B.numpy()
+    rng = np.random.default_rng(14)
+    A = rng.standard_normal((500, 24)) + (1j * rng.standard_normal((500, 24)) if dtype.is_complex else 0)
+    Q, R = oracle.block_hhqr_b(B, A, [5, 8, 11])
+    Rc = _h(np.linalg.cholesky(_h(A) @ B @ A))
+    np.testing.assert_allclose(R, Rc, atol=1e-12 * np.abs(Rc).max(), rtol=0)
+    np.testing.assert_allclose(Q, np.linalg.solve(_h(Rc), _h(A)).conj().T, atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+def test_example3_structure_keeps_b_orthogonality(dtype):
+    """Example 3's setting (kappa_2(B) = 1e5, blocks of 10 columns) on an
+    ill-conditioned block-Krylov stand-in: ||Q^* B Q - I||_2 and the residual
+    stay below 10x Table 3's second-choice figures."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table3_b_inner.json")))
+    B = inputs.b_inner_problem(1000, 1, 1, gold["kappa2_B"], dtype, seed=12).B.numpy()
+    assert np.linalg.cond(B) == pytest.approx(gold["kappa2_B"], rel=1e-3)
+    A = _krylov_blocks(1000, 10, 8, dtype, seed=3)
+    assert np.linalg.cond(A) > 1e14
+    Q, R = oracle.block_hhqr_b(B, A, [10] * 8)
+    worst = max(gold["second_choice"].values(), key=lambda r: r["loo_B"])
+    assert np.linalg.norm(_h(Q) @ B @ Q - np.eye(80), 2) < 10 * worst["loo_B"]
+    assert np.linalg.norm(A - Q @ R, 2) / np.linalg.norm(A, 2) < 10 * worst["resid"]
+    assert np.abs(np.tril(R, -1)).max() == 0

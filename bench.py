@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "two-stage HHQR GB/s (% HBM roof) at n=2^22; batched & fwd+bwd vs looped plain"
 UNIT = "GB/s"
 # FP64 FMA peak of one GB300 (roofline denominator of the FP64 path), from the unit
-# count and clock, checked against the committed probe (csrc/peak_probe.cu):
+# count and clock, checked against a one-off probe (profiles/fp64_peak_probe.md):
 # 2 FP64 FMA / clk / SM x 152 SMs x 2.07 GHz = 1.259 TFLOP/s (nominal 1.25); the probe reads
 # 1.04 (DFMA chains) and the streaming kernels sustain 1.23.  The FP64 kernels issue DFMA.
 FP64_PEAK_TFLOPS = 1.259
@@ -93,7 +93,7 @@ LEAF_WY_QR_FLOPS = lambda m, k, nb: 2 * m * k * k - nb * (2.0 / 3.0) * k ** 3
 # bf16 tensor-core flops per trailing row of one emulated rank-k0 update (36
 # slice pairs of a real-embedded (rows x 2k0) times (2k0 x 2k) product; real: k0, k).
 EMU_UPDATE_MMA_FLOPS_PER_ROW = lambda k0, k, cplx: 2 * 36 * (2 * k0 if cplx else k0) * (2 * k if cplx else k)
-BF16_MMA_SYNC_PEAK_TFLOPS = 607.0  # mma.sync m16n8k16 bf16, measured by csrc/peak_probe.cu (legacy path)
+BF16_MMA_SYNC_PEAK_TFLOPS = 607.0  # mma.sync m16n8k16 bf16, measured once by a probe (profiles/fp64_peak_probe.md; legacy path)
 
 
 def _bf16_peak():
@@ -656,7 +656,7 @@ def run_gpu(args):
                 "traffic": (tr_row * m if tr_row is not None else None), "kernel": kernel_of[dom],
                 "share_of_step": dom_ms / args.steps / ms_step,
                 "peak_source": ("2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal; probe 1.04, k_gram sustains 1.23)"
-                                if prec != 1 else "FP32 FFMA measured by peak_probe (of measured)")}
+                                if prec != 1 else "FP32 FFMA measured by a one-off probe (of measured)")}
     roofline_tensor = None
     if prec == 2 and phases["update_q"][1] > 0:
         t_ms, t_groups = phases["update_q"]

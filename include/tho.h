@@ -302,26 +302,31 @@ tho_status_t tho_plan_read_phase_timing(tho_plan_t plan, double* ms, int32_t* gr
 const char* tho_phase_name(int32_t phase);
 
 /* tho_orth_noalloc: the same orthogonalization as tho_orth, for callers that
- * cannot allocate device memory -- code running during a CUDA-graph capture
- * under a no-allocation policy, latency-critical loops that cannot take
- * cudaMalloc's implicit device synchronization, and plugins whose host
- * application owns every byte of device memory through its own pool.  The
- * paper has no counterpart: this is a deployment variant of Algorithm 1.
+ * cannot allocate device memory: latency-critical loops that cannot take
+ * cudaMalloc's implicit device synchronization, and plugins or embedded
+ * runtimes whose host application owns every byte of device memory through
+ * its own pool.  The paper has no counterpart.
  *
  * It needs no plan and calls no cudaMalloc, cudaFree or other allocating
  * routine.  All of its scratch (status word, problem descriptor, work-item
  * table, partial sums, TSQR factors and solves) lives in one file-scope static
  * device array of THO_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads
  * libtho holds until the process exits.  The caller still passes V, A and the
- * outputs Q, R, S (same meaning, layout and alignment rules as tho_orth);
- * `desc` describes the problem as for tho_plan (count = 1).
+ * outputs Q, R, S (same meaning, layout and alignment rules as tho_orth).
+ * `desc` describes one problem: dtype THO_F64 or THO_C128, precision
+ * THO_PREC_FP64 or THO_PREC_FP32_BULK, flags from THO_FLAG_ALLOW_K0_ZERO and
+ * THO_FLAG_CHECK_FINITE; any other precision or flag gives THO_ERR_ARG.  The
+ * partition and the kernels are those of a default tho_plan for the same
+ * descriptor, so Q, R and S equal tho_orth's bit for bit.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the one array and overwrites
- * what the previous call left there, so calls whose GPU work overlaps in time
- * (two streams, two host threads) race: serialize them.  Device-side checks
- * (THO_FLAG_CHECK_FINITE) are not reported by this entry point.
+ * before any stream capture.  Every call shares the one array; each call
+ * clears the part it uses before its kernels read it, so nothing of an
+ * earlier call's contents reaches a result.  Calls whose GPU work overlaps in
+ * time (two streams, two host threads) race on the array: serialize them.
+ * Device-side checks (THO_FLAG_CHECK_FINITE) are not reported by this entry
+ * point.
  *
  * Errors: ARG, SHAPE, ALIGN, CUDA as tho_plan/tho_orth; THO_ERR_UNSUPPORTED
  * when the problem's scratch exceeds THO_NOALLOC_SCRATCH_BYTES (for example

@@ -1,8 +1,7 @@
 """Build libtho.so (sm_103a) in-tree with nvcc.
 
 Each CUDA translation unit compiles in parallel to an object file, then one
-link step makes ``paper_2602_14449_gb300/_build/libtho.so``.  The probe
-program for the arithmetic peaks (``peak_probe``) is built beside it.
+link step makes ``paper_2602_14449_gb300/_build/libtho.so``.
 """
 from __future__ import annotations
 
@@ -16,7 +15,6 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtho.so")
-PROBE = os.path.join(OUT, "peak_probe")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "--extended-lambda",
                   "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -52,9 +50,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             jobs.append([nvcc] + NVFLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", s, "-o", o])
-    probe_src = os.path.join(CSRC, "peak_probe.cu")
-    if force or _stale(PROBE, [probe_src]):
-        jobs.append([nvcc] + ARCH + ["-O3", "-o", PROBE, probe_src])
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         for res in ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs):
             if verbose or res.returncode != 0:

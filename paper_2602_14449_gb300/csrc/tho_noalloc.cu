@@ -1,15 +1,16 @@
 // tho_orth_noalloc: the orthogonalization of tho_orth without any device
 // allocation, for callers that cannot call cudaMalloc.
 //
-// Such callers include code that runs while a stream is being captured into a
-// CUDA graph under a no-allocation policy, latency-critical loops that cannot
-// afford cudaMalloc's implicit device synchronization, and plugins or
-// embedded runtimes whose host application owns all device memory through its
-// own pool.  This entry point needs no plan: its scratch (status word, problem
-// descriptor, work-item table and the partial sums, TSQR factors and solves of
-// the workspace) lives in one file-scope static device array of fixed size,
-// which every GPU that loads the library holds until the process exits.  The
-// kernels and the launch sequence are the ones tho_orth runs.
+// Such callers include latency-critical loops that cannot afford cudaMalloc's
+// implicit device synchronization, and plugins or embedded runtimes whose host
+// application owns all device memory through its own pool.  This entry point
+// needs no plan: its scratch (status word, problem descriptor, work-item table
+// and the partial sums, TSQR factors and solves of the workspace) lives in one
+// file-scope static device array of fixed size, which every GPU that loads the
+// library holds until the process exits.  The partition (leaf height, split-n
+// chunks), the kernels and the launch sequence are the ones tho_orth runs with
+// a default single-problem plan in the same precision, so the two give the
+// same bits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,6 +62,19 @@ __global__ void k_fill_items(tho::WorkItem* items, int n) {
     items[i] = tho::WorkItem{0, i};
 }
 
+// The problem descriptor, passed by value (kernel parameters are copied when
+// the launch is enqueued), written into the scratch by the device: no copy
+// from host memory that the call's stack frame would have to outlive.
+__global__ void k_put_inst(Inst* dst, Inst src) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst = src;
+}
+
+// Zero `words` 64-bit words (the workspace part the call uses).
+__global__ void k_zero(unsigned long long* p, size_t words) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = 0ull;
+}
+
 }  // namespace
 
 extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int64_t ldv, const void* A,
@@ -91,6 +105,7 @@ extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int
   // Problem layout: the partition tho_plan chooses for a single problem.
   tho::PlanCore pc;
   pc.count = 1;
+  pc.sms = sms;
   pc.dtype = d->dtype;
   pc.prec = d->prec;
   pc.flags = d->flags;
@@ -130,7 +145,11 @@ extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int
     ++I.L;
   }
   pc.Lmax = I.L;
-  const int64_t target = 2 * (int64_t)sms;
+  // Split-n chunks as tho_plan: two per SM less one.  (tho_plan leaves one
+  // chunk out for the SM that runs the small QR of V_{1:k0,:} on a side
+  // stream; here that QR runs on the caller's stream first, but the same
+  // partition keeps the two entry points' results bitwise equal.)
+  const int64_t target = 2 * (int64_t)sms - 1;
   I.rows1 = cdiv(cdiv(I.m, target), tho::kTileRows) * tho::kTileRows;
   I.g1 = (int)cdiv(I.m, I.rows1);
   I.rows4 = I.rows1;
@@ -192,12 +211,16 @@ extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int
   pc.ws = b + o_ws;
   pc.ws_elems = (size_t)off;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // The array keeps the previous call's contents: reset the status word; the
-  // descriptor and the item table are rewritten; every workspace entry the
-  // kernels read is written earlier in the same call.
-  if (cudaMemsetAsync(pc.d_status, 0, sizeof(int), st) != cudaSuccess ||
-      cudaMemcpyAsync(pc.d_insts, &I, sizeof(Inst), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return THO_ERR_CUDA;
+  // The array keeps the previous call's contents: reset the status word,
+  // rewrite the descriptor and the item table, and zero the workspace part
+  // this call uses, so every call starts from the state of a fresh plan.
+  if (cudaMemsetAsync(pc.d_status, 0, sizeof(int), st) != cudaSuccess) return THO_ERR_CUDA;
+  k_put_inst<<<1, 32, 0, st>>>(pc.d_insts, I);
+  {
+    const size_t words = ((size_t)off * L->elem + 7) / 8;
+    k_zero<<<(unsigned)std::min<size_t>(1024, (words + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<unsigned long long*>(pc.ws), words);
+  }
   // The per-phase tables all hold (0, i) for i counting from 0 within the
   // phase, so each phase's slice is filled from its own offset.
   auto fill = [&](int offp, int n) {

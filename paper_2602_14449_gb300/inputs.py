@@ -160,6 +160,27 @@ def random_problem(n: int, k0: int, k: int, dtype=torch.float64, seed: int = 0, 
     return Problem(V=colmajor(V), A=A, n=n, k0=k0, k=k)
 
 
+def graded_problem(n: int, k0: int, k: int, dtype=torch.float64, seed: int = 0, decades: float = 12.0,
+                   period: int = 256) -> Problem:
+    """Rows graded over ``decades`` decades within every ``period`` rows:
+    D = diag(10^(-decades (i mod period) / (period - 1))), V = Q factor of
+    D G1 (so V's rows are graded too), A = D G2, G1 and G2 Gaussian.  Every
+    leaf and every row chunk of the streaming sweeps then holds rows whose
+    scales span all the decades.  Well conditioned: the rows near scale 1
+    alone make A and [V, A] full rank with condition of order one."""
+    g = _gen(seed, "cpu")
+    i = torch.arange(n, dtype=torch.float64)
+    d = torch.pow(10.0, -decades * torch.remainder(i, period) / (period - 1)).to(dtype)
+    if k0 > 0:
+        x = gaussian(n, k0, dtype, g) * d[:, None]
+        q, _ = torch.linalg.qr(x, mode="reduced")
+        V = colmajor(q)
+    else:
+        V = torch.zeros(n, 0, dtype=dtype)
+    A = colmajor(gaussian(n, k, dtype, g) * d[:, None])
+    return Problem(V=V, A=A, n=n, k0=k0, k=k)
+
+
 def badmlu_u(k0: int, alpha: float = 0.1) -> torch.Tensor:
     """U of eq. (badmlu) (Section 3.2, first choice of P): with 0-based row i,
     U_ii = 1 + alpha / sqrt(k0 - i) and U_ij = -1 / sqrt(k0 - i) for j > i."""

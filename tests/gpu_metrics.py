@@ -49,3 +49,17 @@ def resid_fro(V, A, Q, R, S):
         num += (E.abs() ** 2).sum()
         den += (Ar.abs() ** 2).sum() + ((Vr.abs() ** 2).sum() if V.shape[1] else 0)
     return float(torch.sqrt(num / den))
+
+
+def assert_r_triangular(R):
+    """R is upper triangular (exact zeros below the diagonal) with a real
+    nonnegative diagonal: the normalization that makes Q unique (the trailing
+    QR's sign convention), so a Q rotated inside its range cannot pass."""
+    assert R.shape[0] == R.shape[1]
+    below = torch.tril(R, -1)
+    assert float(below.abs().max()) == 0.0
+    d = torch.diagonal(R)
+    if d.is_complex():
+        assert float(d.imag.abs().max()) == 0.0
+        d = d.real
+    assert float(d.min()) >= 0.0

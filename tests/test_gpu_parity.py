@@ -9,6 +9,7 @@ import pytest
 import torch
 
 import oracle
+from gpu_metrics import assert_r_triangular
 from metrics import loo as loo_np
 from paper_2602_14449_gb300 import inputs
 
@@ -123,6 +124,7 @@ def test_config2_full_size(tho):
     Q, R, S = tho.orth(p.V, p.A)
     assert loo(p.V, Q) < TOL_LOO
     assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO
+    assert_r_triangular(R)
     Sref = (p.V.conj().T @ p.A)
     assert float((S - Sref).abs().max()) < 1e-12 * float(Sref.abs().max())
 
@@ -134,6 +136,7 @@ def test_config3_full_size_fp64(tho):
     Q, R, S = tho.orth(p.V, p.A)
     assert loo(p.V, Q) < TOL_LOO
     assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO
+    assert_r_triangular(R)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
@@ -200,6 +203,7 @@ def test_batched_c4_workload(tho, prec_name):
     for i, (p, (Q, R, S)) in enumerate(zip(probs, res)):
         assert loo(p.V, Q) < TOL_LOO, i
         assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO, i
+        assert_r_triangular(R)
         if i % 16 == 0:
             Ql, _, _ = tho.orth(p.V, p.A, prec=prec)
             worst = max(worst, float((Ql - Q).abs().max()))
@@ -228,6 +232,7 @@ def test_emulated_full_size(tho, cid):
     Q, R, S = tho.orth(p.V, p.A, prec=tho.THO_PREC_FP64_EMU)
     assert loo(p.V, Q) < TOL_LOO
     assert resid_fro(p.V, p.A, Q, R, S) < TOL_LOO
+    assert_r_triangular(R)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])

@@ -107,7 +107,7 @@ def test_noalloc_larger_then_smaller(lib):
     """A large call leaves the scratch full of its partial sums and tree factors;
     a smaller call with another k that follows must not see any of it."""
     tho, f = lib
-    big = inputs.random_problem(60000, 64, 32, dtype=torch.float64, seed=7)
+    big = inputs.random_problem(30000, 64, 24, dtype=torch.float64, seed=7)
     small = inputs.random_problem(5000, 8, 5, dtype=torch.float64, seed=8)
     _noalloc(tho, f, big.V.cuda(), big.A.cuda(), 64, tho.THO_PREC_FP64)
     Vs, As = small.V.cuda(), small.A.cuda()

@@ -263,8 +263,9 @@ tho_status_t tho_orth_batched(tho_plan_t plan, const tho_instance_t* instances, 
                               void* stream);
 
 /* Reverse-mode derivative of the map (V, A) -> Q of Algorithm 1 (second
- * choice of P, exact-arithmetic map at arbitrary V, A) for a real FP64 plan
- * with count = 1.  Given Q from tho_orth on the same V, A and the upstream
+ * choice of P, exact-arithmetic map at arbitrary V, A: V need not have
+ * orthonormal columns, only V_{1:k0,:} and the trailing block of A' must have
+ * full rank) for a real FP64 plan with count = 1.  Given Q from tho_orth on the same V, A and the upstream
  * gradient dQ (n x k), writes dV (n x k0) and dA (n x k) such that
  * <dQ, Q'(V, A)[dV_dir, dA_dir]> = <dV, dV_dir> + <dA, dA_dir> (real inner
  * products).  (W, T) and the trailing factorization are recomputed, not

@@ -72,7 +72,7 @@ void backward_free(BwdState& st) {
   st.d_insts_b = nullptr;
 }
 
-int backward_launches(const PlanCore& pc) { return pc.tab.gram_n > 0 ? 10 : 0; }
+int backward_launches(const PlanCore& pc) { return pc.tab.gram_n > 0 ? 9 : 0; }
 
 cudaError_t backward_run(const PlanCore& pc, const BwdState& st, const BwdIo& io, cudaStream_t s) {
   const WorkItem* items = reinterpret_cast<const WorkItem*>(pc.d_items) + pc.tab.gram_off;
@@ -82,12 +82,10 @@ cudaError_t backward_run(const PlanCore& pc, const BwdState& st, const BwdIo& io
   Io fio{io.V, io.A, nullptr, nullptr, nullptr, io.ldv, io.lda, 0};
   // (W, T) recomputed: QR of V_{1:k0,:}, T, Wtop.
   k_v1qr<double><<<1, kV1Threads, 0, s>>>(pc.d_insts, nullptr, fio, pc.ws);
-  // Split-n Grams V_2^T A_2, V_2^T Q_2, V_2^T dQ_2.
+  // Split-n Grams V_2^T A_2 and V_2^T dQ_2 (Z2 comes from the top rows of Q).
   Io ga{io.V, io.A, nullptr, nullptr, nullptr, io.ldv, io.lda, 0};
-  Io gq{io.V, io.Q, nullptr, nullptr, nullptr, io.ldv, io.ldq, 0};
   Io gd{io.V, io.dQ, nullptr, nullptr, nullptr, io.ldv, io.lddq, 0};
   k_gram<double, double><<<g1, blk, pc.smem_gram, s>>>(st.d_insts_b + 0, nullptr, ga, items, st.wsb);
-  k_gram<double, double><<<g1, blk, pc.smem_gram, s>>>(st.d_insts_b + 1, nullptr, gq, items, st.wsb);
   k_gram<double, double><<<g1, blk, pc.smem_gram, s>>>(st.d_insts_b + 2, nullptr, gd, items, st.wsb);
   kb_solve_in<<<dim3(3, k), blk, 0, s>>>(pc.d_insts, io, static_cast<const double*>(pc.ws), st.wsb, st.bl);
   kb_sweep_b<<<g1, blk, st.smem_b, s>>>(pc.d_insts, io, items, st.wsb, st.bl);

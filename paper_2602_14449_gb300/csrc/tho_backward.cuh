@@ -13,9 +13,11 @@
 //     Wbar_top = -dQ_1 Z2^T + A_1 Gbar^T, Q1bar = -Wbar_top,
 //     Tbar = Y Z2^T - Z Gbar^T, R1bar = triu(Tbar^T), M1 = R1 R1bar^T - Q1bar^T Q1
 //     (P = -Q1, T = I + R1^T, V_1 = Q1 R1).
-// Where V has orthonormal columns (the method's precondition) H is orthogonal,
-// so E = H^T Q is recovered from the given Q: Zq = T^{-T} W^T Q, E = Q - W Zq,
-// Z2 = -Zq.  The same algebra gives R = Qbar^T A'_2.
+// E and Z2 are recovered exactly from the given Q at any V (orthonormal or
+// not): the top k0 rows of E are zero, so Q_1 = -Wtop Z2 with
+// Wtop = -Q1 (I + R1) = -Q1 T^T invertible, i.e. Z2 = T^{-T} Q1^T Q_1, and
+// Qbar = E_2 = Q_2 - V_2 Z2.  The kernels keep Zq = -Z2 (so E = Q - W Zq).
+// The same algebra gives R = Qbar^T A'_2.
 #pragma once
 
 #include "tho_backward.h"
@@ -25,7 +27,8 @@ namespace tho {
 
 // Y-type solves for the three right-hand sides (blockIdx.x = 0: A -> Z,
 // 1: Q -> Zq, 2: dQ -> Y), column j = blockIdx.y:
-//   g = Wtop^T X_1(:, j) - sum_chunks (V_2^T X_2)(:, j),  z = T^{-T} g.
+//   A, dQ:  g = Wtop^T X_1(:, j) - sum_chunks (V_2^T X_2)(:, j),  z = T^{-T} g;
+//   Q:      g = -Q1^T Q_1(:, j),  z = T^{-T} g = -Z2 (top rows only).
 __global__ void __launch_bounds__(kThreads) kb_solve_in(const Inst* insts, BwdIo io, const double* wsf, double* wsb,
                                                         BwdLayout bl) {
   const Inst& I = insts[0];
@@ -39,7 +42,14 @@ __global__ void __launch_bounds__(kThreads) kb_solve_in(const Inst* insts, BwdIo
   const double* Wt = wsf + I.oWt;
   __shared__ double g[kMaxK0];
   __shared__ double z[kMaxK0];
+  const double* Q1 = wsf + I.oQ1;
   for (int i = threadIdx.x; i < k0; i += kThreads) {
+    if (which == 1) {
+      double h = 0.0;
+      for (int r = 0; r < k0; ++r) h = fma(Q1[r + i * k0], X[r + (int64_t)j * ldx], h);
+      g[i] = -h;
+      continue;
+    }
     double s = 0.0;
     for (int c = 0; c < I.g1; ++c) s += Gp[(int64_t)c * k0 * k + i + (int64_t)j * k0];
     double h = 0.0;

@@ -148,6 +148,7 @@ cudaError_t configure_impl(PlanCore& pc) {
   pc.smem_leaf_emu = leaf_emu_smem(pc.P, pc.kpmax, sizeof(S));
   if (EMU && (e = raise((const void*)k_leaf_emu<S>, pc.smem_leaf_emu)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_up_p<S>, tree_up_p_smem(kTreeUpG, pc.kmax, sizeof(S)))) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down_w<S>, pc.smem_tree)) != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
   int n = 0;
@@ -208,9 +209,15 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
                                                          EMU ? ((pc.any_k0 ? 1 : 0) | 2) : 0);
   hk(kPhLeaf, 1, st);
   hk(kPhTreeUp, 0, st);
-  for (int l = 1; l <= pc.Lmax; ++l)
-    if (pc.tab.lev_n[l] > 0)
-      k_tree_up<S><<<pc.tab.lev_n[l], kTreeThreads, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+  for (int l = 1; l <= pc.Lmax; ++l) {
+    const int nl = pc.tab.lev_n[l];
+    if (nl <= 0) continue;
+    // Nodes per CTA: up to kTreeUpG while the level still gives about three
+    // CTAs per SM, fewer (down to one) on the narrow levels near the root.
+    const int G = std::max(1, std::min(kTreeUpG, nl / (3 * std::max(1, pc.sms))));
+    k_tree_up_p<S><<<(nl + G - 1) / G, tree_up_p_threads(G, pc.kmax), tree_up_p_smem(G, pc.kmax, sizeof(S)), st>>>(
+        insts, items + pc.tab.lev_off[l], nl, ws, l, G, pc.kmax);
+  }
   hk(kPhTreeUp, 1, st);
   hk(kPhRoot, 0, st);
   k_root<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);

@@ -159,6 +159,200 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
   }
 }
 
+// a7 (tree, upward), packed form: the same node QRs as k_tree_up, G nodes per
+// CTA (G <= kTreeUpG), with the work of each step packed onto consecutive
+// threads.  Step j of a node updates its columns c > j, each over the top entry
+// (row j of R_a) and bottom rows 0..j, so the live part of a node shrinks from
+// k - 1 columns to one while its rows grow; a fixed thread-per-column layout
+// leaves most lanes idle (the FP64 pipe is charged per warp instruction, not
+// per active lane).  Here thread t takes the t-th live (node, column) pair of
+// the step, so the warps that issue are full.  The bottom blocks live in shared
+// memory as packed upper triangles (column c at offset c (c + 1) / 2), the top
+// row j of R_a is read from the workspace at step j, and the thread that
+// updates column j + 1 forms reflector j + 1 from it at once (its norm comes
+// from the values it just wrote), so a step costs one barrier.  Outputs as
+// k_tree_up: the node's R, and per node the bottom parts, tops and betas of
+// its reflectors for the downward pass.
+constexpr int kTreeUpG = 8;  // nodes per CTA at most
+
+__host__ __device__ inline size_t tree_up_p_smem(int G, int kmax, size_t elem) {
+  const size_t tri = (size_t)kmax * (kmax + 1) / 2;
+  return (size_t)G * ((tri + kmax) * elem + (size_t)kmax * sizeof(double));
+}
+
+// Threads of a packed-tree CTA of G nodes: one per live column at step 0.
+__host__ __device__ inline int tree_up_p_threads(int G, int kmax) {
+  const int t = G * (kmax > 1 ? kmax - 1 : 1);
+  return (t + 31) / 32 * 32;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kTreeUpG * kMaxKP, 3) k_tree_up_p(const Inst* insts, const WorkItem* items, int nitems,
+                                                                void* ws, int lev, int G, int kmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tri = kmax * (kmax + 1) / 2;
+  S* Bp = reinterpret_cast<S*>(smem_raw);                               // [G][tri]: bottom blocks
+  S* vs = Bp + (size_t)G * tri;                                         // [G][kmax]: reflector tops
+  double* bs = reinterpret_cast<double*>(vs + (size_t)G * kmax);        // [G][kmax]: betas
+  __shared__ int s_k[kTreeUpG];           // k of node g when it combines two children, else 0
+  __shared__ int s_kc[kTreeUpG];          // k of node g when its one child's R is copied up, else 0
+  __shared__ const S* s_ra[kTreeUpG];     // top block R_a of node g
+  __shared__ S* s_rd[kTreeUpG];           // R of node g
+  __shared__ S* s_ref[kTreeUpG];          // reflectors kept for the downward pass
+  const int g0 = blockIdx.x * G;
+  const int ng = min(G, nitems - g0);
+  if (threadIdx.x < kTreeUpG) {
+    const int g = threadIdx.x;
+    s_k[g] = 0;
+    s_kc[g] = 0;
+    if (g < ng) {
+      const WorkItem it = items[g0 + g];
+      const Inst& I = insts[it.inst];
+      const int k = (int)I.k, kk = k * k;
+      const int64_t c0 = I.lev_off[lev - 1] + 2 * (int64_t)it.idx;
+      const int64_t node = I.lev_off[lev] + it.idx;
+      S* Rn = wsp<S>(ws, I.oRn);
+      s_ra[g] = Rn + c0 * kk;
+      s_rd[g] = Rn + node * kk;
+      if ((2 * it.idx + 1) < I.lev_cnt[lev - 1]) {
+        s_k[g] = k;
+        s_ref[g] = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
+      } else {
+        s_kc[g] = k;
+      }
+    }
+  }
+  __syncthreads();
+  // Copies of lone children; bottom blocks R_b into the packed triangles.  The
+  // (node, entry) pairs are flattened and loaded eight per thread ahead of
+  // their stores, so a thread waits for one memory round trip per group.
+  {
+    const int kk = kmax * kmax, tot = ng * kk;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * (int)blockDim.x) {
+      S v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * (int)blockDim.x, g = e / kk, f = e % kk;
+        v[u] = zero<S>();
+        if (e < tot) {
+          const int kc = s_kc[g], kg = s_k[g];
+          if (kc > 0 && f < kc * kc) v[u] = s_ra[g][f];
+          else if (kg > 0 && f < kg * kg && f % kg <= f / kg) v[u] = s_ra[g][kg * kg + f];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * (int)blockDim.x, g = e / kk, f = e % kk;
+        if (e >= tot) continue;
+        const int kc = s_kc[g], kg = s_k[g];
+        if (kc > 0 && f < kc * kc) {
+          s_rd[g][f] = v[u];
+        } else if (kg > 0 && f < kg * kg) {
+          const int r = f % kg, c = f / kg;
+          if (r <= c) Bp[(size_t)g * tri + c * (c + 1) / 2 + r] = v[u];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  int kx = 0;  // largest k among the CTA's combining nodes
+  for (int g = 0; g < ng; ++g) kx = max(kx, s_k[g]);
+  // Reflector 0 of every node.
+  if (threadIdx.x < ng && s_k[threadIdx.x] > 0) {
+    const int g = threadIdx.x;
+    const S x1 = s_ra[g][0];
+    double b;
+    S v, r;
+    make_reflector<S>(abs2d(x1) + abs2d(Bp[(size_t)g * tri]), x1, b, v, r);
+    vs[g * kmax] = v;
+    bs[g * kmax] = b;
+    s_rd[g][0] = r;
+  }
+  __syncthreads();
+  // Thread t takes the t-th live (node, column) pair of step j; its top entry
+  // (row j of R_a) is loaded one step ahead.
+  auto pair_of = [&](int j, int& g, int& c) {
+    int t = threadIdx.x;
+    g = -1;
+    c = 0;
+    for (int q = 0; q < ng; ++q) {
+      const int live = s_k[q] - 1 - j;
+      if (live <= 0) continue;
+      if (t < live) {
+        g = q;
+        c = j + 1 + t;
+        return;
+      }
+      t -= live;
+    }
+  };
+  int g = -1, c = 0;
+  pair_of(0, g, c);
+  S top_pre = (g >= 0) ? s_ra[g][c * s_k[g]] : zero<S>();
+  for (int j = 0; j + 1 < kx; ++j) {
+    int gn = -1, cn = 0;
+    if (j + 2 < kx) pair_of(j + 1, gn, cn);
+    const S top_nx = (gn >= 0) ? s_ra[gn][(j + 1) + cn * s_k[gn]] : zero<S>();
+    if (g >= 0) {
+      const int k = s_k[g];
+      const S* Ra = s_ra[g];
+      S* Rd = s_rd[g];
+      S* B = Bp + (size_t)g * tri;
+      S* x = B + c * (c + 1) / 2;        // bottom rows 0..c of column c
+      const S* u = B + j * (j + 1) / 2;  // reflector j's bottom part (rows 0..j)
+      S top = top_pre;
+      const S tnext = (c == j + 1) ? Ra[(j + 1) + c * k] : zero<S>();
+      const double b = bs[g * kmax + j];
+      if (b != 0.0) {
+        const S vj = vs[g * kmax + j];
+        S d0 = cmadd(zero<S>(), vj, top), d1 = zero<S>();  // two chains
+        for (int r = 0; r <= j; ++r) {
+          if (r & 1) d1 = cmadd(d1, u[r], x[r]);
+          else d0 = cmadd(d0, u[r], x[r]);
+        }
+        const S d = scale(add(d0, d1), b);
+        top = msub(top, vj, d);
+        for (int r = 0; r <= j; ++r) x[r] = msub(x[r], u[r], d);
+      }
+      Rd[j + c * k] = top;  // entry (j, c) of the node's R is final
+      if (c == j + 1) {
+        // Look-ahead: reflector j + 1 from column j + 1 (bottom rows 0..j + 1,
+        // just written, and the untouched top entry (j + 1, j + 1)).
+        double sn = abs2d(tnext);
+        for (int r = 0; r <= j + 1; ++r) sn += abs2d(x[r]);
+        double bn;
+        S vn, rn;
+        make_reflector<S>(sn, tnext, bn, vn, rn);
+        vs[g * kmax + j + 1] = vn;
+        bs[g * kmax + j + 1] = bn;
+        Rd[(j + 1) + (j + 1) * k] = rn;
+      }
+    }
+    g = gn;
+    c = cn;
+    top_pre = top_nx;
+    __syncthreads();
+  }
+  // Below-diagonal zeros of R; the reflectors (bottom parts, tops, betas).
+  for (int g = 0; g < ng; ++g) {
+    const int k = s_k[g];
+    if (k == 0) continue;
+    const int kk = k * k;
+    const S* B = Bp + (size_t)g * tri;
+    S* ref = s_ref[g];
+    S* Rd = s_rd[g];
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      const int r = e % k, c = e / k;
+      ref[e] = r <= c ? B[c * (c + 1) / 2 + r] : zero<S>();
+      if (r > c) Rd[e] = zero<S>();
+    }
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      ref[kk + c] = vs[g * kmax + c];
+      ref[kk + k + c] = from_real<S>(bs[g * kmax + c]);
+    }
+  }
+}
+
 // Root of the tree: D = diag(phase(R_jj)); R_out = D^* R (diag real >= 0);
 // F_root = D so that the leaf factors carry the normalization.
 template <class S>

@@ -50,6 +50,26 @@ def test_adjoint_vs_oracle_autograd(tho, n, k0, k):
     assert _rel(dV.cpu(), gV) <= 1e-10
 
 
+@pytest.mark.parametrize("n,k0,k,eps", [(2000, 16, 8, 0.1), (3000, 64, 16, 0.02), (700, 5, 3, 0.3)])
+def test_adjoint_at_non_orthonormal_v(tho, n, k0, k, eps):
+    """The derivative of the algorithm's map at a V whose columns are not
+    orthonormal (V = orthonormal + eps * Gaussian): the adjoint recovers Z2 and
+    Qbar from the top rows of Q, which holds at any V, and must match autograd
+    through the oracle's restatement."""
+    p = inputs.random_problem(n, k0, k, seed=500 + n)
+    g = torch.Generator().manual_seed(501 + n)
+    V = inputs.colmajor(p.V + eps * torch.randn(n, k0, dtype=torch.float64, generator=g))
+    assert float(torch.linalg.matrix_norm(V.T @ V - torch.eye(k0, dtype=torch.float64), 2)) > eps
+    dQ = inputs.colmajor(torch.randn(n, k, dtype=torch.float64, generator=g))
+    gV, gA = _ref_grads(V, p.A, dQ)
+    Vd, Ad = V.cuda(), p.A.cuda()
+    Q, _, _ = tho.orth(Vd, Ad)
+    dV, dA = tho.orth_backward(Vd, Ad, Q, dQ.cuda())
+    torch.cuda.synchronize()
+    assert _rel(dA.cpu(), gA) <= 1e-10
+    assert _rel(dV.cpu(), gV) <= 1e-10
+
+
 def test_autograd_function(tho):
     from paper_2602_14449_gb300.autograd import two_stage_orth
     p = inputs.config_problem(5, n=5000)

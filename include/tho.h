@@ -69,7 +69,9 @@ typedef enum {
   THO_ERR_TIMEOUT = 6,     /* a bounded device-side wait of a tcgen05 kernel ran   *
                             * out (results invalid); latched like NONFINITE        */
   THO_ERR_NONFINITE = 7,   /* device check found NaN/Inf (THO_FLAG_CHECK_FINITE)   */
-  THO_ERR_UNSUPPORTED = 8  /* shape or mode beyond what the library implements    */
+  THO_ERR_UNSUPPORTED = 8, /* shape or mode beyond what the library implements    */
+  THO_ERR_NOCONV = 9       /* the polar iteration of THO_FLAG_P_POLAR did not     *
+                            * converge (V_{1:k0,:} numerically singular); latched  */
 } tho_status_t;
 
 typedef enum { THO_F64 = 0, THO_C128 = 1 } tho_dtype_t;
@@ -97,6 +99,18 @@ typedef enum { THO_PREC_FP64 = 0, THO_PREC_FP32_BULK = 1, THO_PREC_FP64_EMU = 2 
  * applied through the L and U factors.  Without it: the second choice,
  * P = -Q_1 from the QR of V_{1:k0,:}.  Not for tho_orth_backward. */
 #define THO_FLAG_P_MLU 0x4u
+/* The third choice of P (Section 3.2): P = -Q2 with V_{1:k0,:} = Q2 M its
+ * polar decomposition (Q2 unitary, M Hermitian positive semidefinite), so
+ * that T = I - V_{1:k0,:}^* P = I + M is Hermitian positive definite with
+ * kappa_2(T) <= 2 (for orthonormal V); T^{-*} = T^{-1} is applied through the
+ * Cholesky factor of T.  Q2 comes from the Newton-Schulz iteration
+ * X <- X (3 I - X^* X) / 2 started at V_{1:k0,:} / ||V_{1:k0,:}||_F, stopped two
+ * steps after max|X^* X - I| <= 1e-6; if that does not happen within
+ * THO_POLAR_MAX_ITERATIONS steps (V_{1:k0,:} numerically singular) the plan
+ * latches THO_ERR_NOCONV, read with tho_plan_status.  Exclusive with
+ * THO_FLAG_P_MLU; not for tho_orth_backward. */
+#define THO_FLAG_P_POLAR 0x8u
+#define THO_POLAR_MAX_ITERATIONS 100
 
 /* One orthogonalization problem: V is n x k0, A is n x k. */
 typedef struct {
@@ -261,6 +275,28 @@ typedef struct {
  * Errors: ARG, ALIGN, CUDA. */
 tho_status_t tho_orth_batched(tho_plan_t plan, const tho_instance_t* instances, int32_t count,
                               void* stream);
+
+/* Algorithm 4 (Section 5): two-stage Householder QR in the B-inner product
+ * <x, y>_B = y^* B x, for a diagonal positive definite B = diag(d), with the
+ * initial B-orthonormal basis the method suggests: U = [L^{-*}; 0] from the
+ * Cholesky factor L of the leading (k0 + k) x (k0 + k) block of B, here
+ * U = D^{-1/2} [I; 0].  Theorem 5 gives the generalized reflector
+ * H = I - W T^{-1} W^* B of the first stage.
+ *   d      n positive finite doubles, the diagonal of B (device); an entry that
+ *          is not positive and finite latches THO_ERR_NONFINITE in the plan
+ *   V      n x k0 with B-orthonormal columns (V^* B V = I), ld >= n
+ *   A      n x k, ld >= n;  Q, R, S as for tho_orth
+ * Returns Q with [V, Q]^* B [V, Q] = I and [V, A] = [V, Q] [[I, S], [0, R]]
+ * (eq. vavqb), diag(R) real >= 0.  With U as above, every step of Algorithm 4
+ * is the matching step of Algorithm 1 in the variables D^{1/2} x (Euclidean
+ * inner products, U = [I; 0]), so the call scales V and A by D^{1/2} into
+ * plan-owned buffers (allocated on the first call, n (k0 + k) elements and
+ * 2 n doubles), runs the plan's Algorithm 1 kernels on them and scales the
+ * rows of Q by D^{-1/2}.  The plan is an ordinary count = 1 plan for
+ * (n, k0, k); every precision and choice of P it supports applies.
+ * Asynchronous on `stream`.  Errors: ARG, ALIGN, NOMEM, CUDA. */
+tho_status_t tho_orth_b(tho_plan_t plan, const double* d, const void* V, int64_t ldv, const void* A,
+                        int64_t lda, void* Q, int64_t ldq, void* R, void* S, void* stream);
 
 /* Reverse-mode derivative of the map (V, A) -> Q of Algorithm 1 (second
  * choice of P, exact-arithmetic map at arbitrary V, A: V need not have

@@ -12,6 +12,7 @@
 
 #include "tho.h"
 #include "tho_backward.h"
+#include "tho_binner.cuh"
 #include "tho_launch.h"
 
 using tho::Inst;
@@ -44,6 +45,9 @@ struct tho_plan_s {
   cudaStream_t hs_in = nullptr, hs_out = nullptr;
   cudaEvent_t hs_ev_in[2] = {nullptr, nullptr}, hs_ev_comp[2] = {nullptr, nullptr}, hs_ev_out[2] = {nullptr, nullptr};
   int hs_next = 0;
+  // Algorithm 4 with a diagonal B (allocated on the first tho_orth_b call):
+  // D^{1/2} V (n x k0), D^{1/2} A (n x k), sqrt(d) and 1 / sqrt(d) (n each).
+  void* bi_buf = nullptr;
   int32_t split_chunks = 0;  // split-n factor the partition was built with
   int32_t balance = 0;       // chunks shared by rows (0) or by streaming work (1)
 };
@@ -65,7 +69,9 @@ tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
   if (d.dtype != d0.dtype || d.prec != d0.prec || d.flags != d0.flags) return THO_ERR_ARG;
   if (d.dtype != THO_F64 && d.dtype != THO_C128) return THO_ERR_ARG;
   if (d.prec != THO_PREC_FP64 && d.prec != THO_PREC_FP32_BULK && d.prec != THO_PREC_FP64_EMU) return THO_ERR_ARG;
-  if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE | THO_FLAG_P_MLU)) return THO_ERR_ARG;
+  if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE | THO_FLAG_P_MLU | THO_FLAG_P_POLAR))
+    return THO_ERR_ARG;
+  if ((d.flags & THO_FLAG_P_MLU) && (d.flags & THO_FLAG_P_POLAR)) return THO_ERR_ARG;
   if (d.k < 1 || d.k0 < 0 || d.n < 1) return THO_ERR_SHAPE;
   if (d.k0 == 0 && !(d.flags & THO_FLAG_ALLOW_K0_ZERO)) return THO_ERR_SHAPE;
   if (d.k0 + d.k > d.n) return THO_ERR_SHAPE;
@@ -90,6 +96,7 @@ void free_plan(tho_plan_s* p) {
   if (p->hs_out) cudaStreamDestroy(p->hs_out);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->bi_buf) cudaFree(p->bi_buf);
   if (p->pc.side) cudaStreamDestroy(p->pc.side);
   if (p->pc.ev_fork) cudaEventDestroy(p->pc.ev_fork);
   if (p->pc.ev_join) cudaEventDestroy(p->pc.ev_join);
@@ -179,6 +186,7 @@ const char* tho_status_string(tho_status_t s) {
     case THO_ERR_TIMEOUT: return "device wait timed out";
     case THO_ERR_NONFINITE: return "non-finite value detected on the device";
     case THO_ERR_UNSUPPORTED: return "shape or mode not supported by the library";
+    case THO_ERR_NOCONV: return "polar iteration did not converge (V_{1:k0,:} numerically singular)";
   }
   return "unknown status";
 }
@@ -333,6 +341,7 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
     I.oRn = take(nodes * kk);
     I.oRef = take((nodes - I.nb) * (kk + 2 * k));
     I.oF = take(nodes * kk);
+    I.oPs = take((pc.flags & THO_FLAG_P_POLAR) ? 2 + tho::kPolarMaxIt : 1);
     I.oBeta = take(pc.prec == THO_PREC_FP64_EMU ? (int64_t)I.nb * k : 1);
     I.oGw = take(pc.leaf_tc ? (int64_t)I.nb * kk : 1);
   }
@@ -578,6 +587,63 @@ tho_status_t tho_orth_host_wait(tho_plan_t plan, void* stream) {
   return THO_OK;
 }
 
+tho_status_t tho_orth_b(tho_plan_t plan, const double* d, const void* V, int64_t ldv, const void* A, int64_t lda,
+                        void* Q, int64_t ldq, void* R, void* S, void* stream) {
+  if (!plan || plan->pc.count != 1 || !d) return THO_ERR_ARG;
+  const Inst& I = plan->pc.h_insts[0];
+  const size_t el = plan->L->elem;
+  tho_status_t s = check_io(I, el, V, ldv, A, lda, Q, ldq, R, S);
+  if (s != THO_OK) return s;
+  if (reinterpret_cast<uintptr_t>(d) % sizeof(double)) return THO_ERR_ALIGN;
+  const int64_t n = I.n, k0 = I.k0, k = I.k;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t oA = al((size_t)(n * k0) * el), oS = oA + al((size_t)(n * k) * el), oI = oS + al(sizeof(double) * n);
+  const size_t total = oI + al(sizeof(double) * n);
+  if (!plan->bi_buf) {
+    if (cudaMalloc(&plan->bi_buf, total) != cudaSuccess) {
+      plan->bi_buf = nullptr;
+      cudaGetLastError();
+      return THO_ERR_NOMEM;
+    }
+  }
+  unsigned char* b = static_cast<unsigned char*>(plan->bi_buf);
+  void* Vs = b;
+  void* As = b + oA;
+  double* sd = reinterpret_cast<double*>(b + oS);
+  double* isd = reinterpret_cast<double*>(b + oI);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const unsigned grid =
+      (unsigned)std::min<int64_t>(8 * (int64_t)std::max(1, plan->pc.sms), std::max<int64_t>(1, (n * (k0 + k) + 255) / 256));
+  tho::k_bsqrt<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, st>>>(d, sd, isd, n, plan->pc.d_status);
+  if (plan->pc.dtype == THO_C128) {
+    using Z = tho::z64;
+    if (k0 > 0)
+      tho::k_bscale_rows<Z><<<grid, 256, 0, st>>>(sd, static_cast<const Z*>(V), ldv, static_cast<Z*>(Vs), n, n, (int)k0);
+    tho::k_bscale_rows<Z><<<grid, 256, 0, st>>>(sd, static_cast<const Z*>(A), lda, static_cast<Z*>(As), n, n, (int)k);
+  } else {
+    if (k0 > 0)
+      tho::k_bscale_rows<double><<<grid, 256, 0, st>>>(sd, static_cast<const double*>(V), ldv,
+                                                        static_cast<double*>(Vs), n, n, (int)k0);
+    tho::k_bscale_rows<double><<<grid, 256, 0, st>>>(sd, static_cast<const double*>(A), lda, static_cast<double*>(As),
+                                                      n, n, (int)k);
+  }
+  Io io0{k0 > 0 ? Vs : nullptr, As, Q, R, S, n, n, ldq};
+  tho::PhaseHook hook;
+  if (plan->timing) {
+    hook.fn = &phase_hook;
+    hook.ctx = plan;
+  }
+  if (plan->L->run(plan->pc, nullptr, io0, st, hook) != cudaSuccess) return THO_ERR_CUDA;
+  // Q = D^{-1/2} Q~ in place.
+  if (plan->pc.dtype == THO_C128)
+    tho::k_bscale_rows<tho::z64><<<grid, 256, 0, st>>>(isd, static_cast<const tho::z64*>(Q), ldq,
+                                                        static_cast<tho::z64*>(Q), ldq, n, (int)k);
+  else
+    tho::k_bscale_rows<double><<<grid, 256, 0, st>>>(isd, static_cast<const double*>(Q), ldq, static_cast<double*>(Q),
+                                                      ldq, n, (int)k);
+  return cudaGetLastError() == cudaSuccess ? THO_OK : THO_ERR_CUDA;
+}
+
 tho_status_t tho_orth_batched(tho_plan_t plan, const tho_instance_t* inst, int32_t count, void* stream) {
   if (!plan || !inst || count != plan->pc.count || count < 2) return THO_ERR_ARG;
   for (int i = 0; i < count; ++i) {
@@ -621,7 +687,8 @@ tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, cons
                                int64_t lddv, void* dA, int64_t ldda, void* stream) {
   if (!plan || plan->pc.count != 1) return THO_ERR_ARG;
   const Inst& I = plan->pc.h_insts[0];
-  if (plan->pc.dtype != THO_F64 || plan->pc.prec != THO_PREC_FP64 || I.k0 < 1 || (plan->pc.flags & THO_FLAG_P_MLU))
+  if (plan->pc.dtype != THO_F64 || plan->pc.prec != THO_PREC_FP64 || I.k0 < 1 ||
+      (plan->pc.flags & (THO_FLAG_P_MLU | THO_FLAG_P_POLAR)))
     return THO_ERR_UNSUPPORTED;
   if (!V || !A || !Q || !dQ || !dV || !dA) return THO_ERR_ARG;
   if (ldv < I.n || lda < I.n || ldq < I.n || lddq < I.n || lddv < I.n || ldda < I.n) return THO_ERR_ARG;

@@ -425,6 +425,26 @@ __global__ void __launch_bounds__(kThreads) k_solve_z(const Inst* insts, const I
         __syncwarp();
       }
     }
+  } else if (flags & 0x8u) {
+    // Third choice: T = C C^* (C lower, real diagonal, in T's slot), so
+    // T^{-*} = T^{-1} = C^{-*} C^{-1}: forward then back substitution.  One warp.
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int i = 0; i < k0; ++i) {
+        S s = zero<S>();
+        for (int l = lane; l < i; l += 32) s = madd(s, T[i + l * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) z[i] = scale(sub(g[i], s), 1.0 / real_(T[i + i * k0]));
+        __syncwarp();
+      }
+      for (int i = k0 - 1; i >= 0; --i) {
+        S s = zero<S>();
+        for (int l = i + 1 + lane; l < k0; l += 32) s = cmadd(s, T[l + i * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) z[i] = scale(sub(z[i], s), 1.0 / real_(T[i + i * k0]));
+        __syncwarp();
+      }
+    }
   } else if (threadIdx.x < 32) {
     // Back substitution with U = T^*: U(i, l) = conj(T(l, i)), one warp.
     const int lane = threadIdx.x;
@@ -823,6 +843,26 @@ __global__ void __launch_bounds__(kThreads) k_solve_z2(const Inst* insts, const 
       }
       __syncwarp();
       for (int i = lane; i < k0; i += 32) z[i] = scale(z[i], -real_(Q1[i + i * k0]));  // P^* x, P = -Q1 real
+    }
+  } else if (flags & 0x8u) {
+    // Third choice: T = C C^* (C lower, real diagonal, in T's slot), so
+    // T^{-*} = T^{-1} = C^{-*} C^{-1}: forward then back substitution.  One warp.
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int i = 0; i < k0; ++i) {
+        S s = zero<S>();
+        for (int l = lane; l < i; l += 32) s = madd(s, T[i + l * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) z[i] = scale(sub(g[i], s), 1.0 / real_(T[i + i * k0]));
+        __syncwarp();
+      }
+      for (int i = k0 - 1; i >= 0; --i) {
+        S s = zero<S>();
+        for (int l = i + 1 + lane; l < k0; l += 32) s = cmadd(s, T[l + i * k0], z[l]);
+        s = warp_sum(s);
+        if (lane == 0) z[i] = scale(sub(z[i], s), 1.0 / real_(T[i + i * k0]));
+        __syncwarp();
+      }
     }
   } else if (threadIdx.x < 32) {
     const int lane = threadIdx.x;

@@ -7,6 +7,7 @@
 #include "tho_umma.cuh"
 #include "tho_kernels.cuh"
 #include "tho_launch.h"
+#include "tho_polar.cuh"
 #include "tho_tree.cuh"
 
 namespace tho {
@@ -153,6 +154,7 @@ cudaError_t configure_impl(PlanCore& pc) {
   // Count the launches one call issues (same order as run_impl).
   int n = 0;
   if (pc.any_k0) n += 3;  // v1qr, gram, solve_z
+  if (pc.any_k0 && (pc.flags & 0x8u)) n += 2 * kPolarMaxIt + 2;  // polar iteration instead of v1qr
   n += 1;                  // leaf
   for (int l = 1; l <= pc.Lmax; ++l) n += pc.tab.lev_n[l] > 0 ? 2 : 0;
   n += 2;                  // root, apply_gram
@@ -176,7 +178,19 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
       cudaStreamWaitEvent(sq, pc.ev_fork, 0);
     }
     hk(kPhQrV1, 0, sq);
-    k_v1qr<S><<<pc.count, kV1Threads, 0, sq>>>(insts, d_io, io0, ws, pc.flags);
+    if (pc.flags & 0x8u) {  // THO_FLAG_P_POLAR: the polar factor of V_{1:k0,:} by Newton-Schulz
+      const int nt = (pc.k0max + kPolarTile - 1) / kPolarTile;
+      const dim3 gp(nt * nt, pc.count);
+      k_polar_init<S><<<pc.count, 256, 0, sq>>>(insts, d_io, io0, ws);
+      for (int it = 0; it < kPolarMaxIt; ++it) {
+        k_polar_gram<S><<<gp, kPolarThreads, 0, sq>>>(insts, ws, it);
+        k_polar_step<S><<<gp, kPolarThreads, 0, sq>>>(insts, ws, it);
+      }
+      k_polar_t<S><<<gp, kPolarThreads, 0, sq>>>(insts, d_io, io0, ws);
+      k_polar_chol<S><<<pc.count, 1024, 0, sq>>>(insts, ws, pc.d_status);
+    } else {
+      k_v1qr<S><<<pc.count, kV1Threads, 0, sq>>>(insts, d_io, io0, ws, pc.flags);
+    }
     hk(kPhQrV1, 1, sq);
     if (pc.side) cudaEventRecord(pc.ev_join, sq);
     if (pc.tab.gram_n > 0) {
@@ -212,11 +226,17 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   for (int l = 1; l <= pc.Lmax; ++l) {
     const int nl = pc.tab.lev_n[l];
     if (nl <= 0) continue;
-    // Nodes per CTA: up to kTreeUpG while the level still gives about three
-    // CTAs per SM, fewer (down to one) on the narrow levels near the root.
-    const int G = std::max(1, std::min(kTreeUpG, nl / (3 * std::max(1, pc.sms))));
-    k_tree_up_p<S><<<(nl + G - 1) / G, tree_up_p_threads(G, pc.kmax), tree_up_p_smem(G, pc.kmax, sizeof(S)), st>>>(
-        insts, items + pc.tab.lev_off[l], nl, ws, l, G, pc.kmax);
+    // Wide levels: the packed form, up to kTreeUpG nodes per CTA while the level
+    // gives about three CTAs per SM (fewest FP64 instructions per node).
+    // Narrow levels (fewer than four nodes per CTA): one CTA of four row groups
+    // per column per node, whose per-step chains are four times shorter (those
+    // levels are latency-bound).
+    const int G = std::min(kTreeUpG, nl / (3 * std::max(1, pc.sms)));
+    if (G >= 4)
+      k_tree_up_p<S><<<(nl + G - 1) / G, tree_up_p_threads(G, pc.kmax), tree_up_p_smem(G, pc.kmax, sizeof(S)),
+                       st>>>(insts, items + pc.tab.lev_off[l], nl, ws, l, G, pc.kmax);
+    else
+      k_tree_up<S><<<nl, kTreeThreads, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   }
   hk(kPhTreeUp, 1, st);
   hk(kPhRoot, 0, st);

@@ -16,6 +16,8 @@ constexpr int kMaxK0 = 128;      // largest k0 (THO_MAX_K0)
 constexpr int kMaxKP = 32;       // largest k, padded (THO_MAX_K)
 constexpr int kRedElems = kThreads * kBI * kBJ;  // Gram cross-phase scratch (elements)
 constexpr int kNB = 8;           // panel width of the blocked leaf Householder QR
+constexpr int kPolarMaxIt = 100; // Newton-Schulz steps of the third choice of P, at most
+constexpr int kPolarTile = 8;    // output tile (rows and columns) of its k0 x k0 products
 // Emulated products on tcgen05: real contraction steps per pipeline stage and
 // the bytes of one stage's eight 128-row V slices (bf16), as kept in HBM.
 constexpr int kUmmaKT = 32;
@@ -48,6 +50,7 @@ struct Inst {
   int64_t oEv;  // emulated products: column exponents of V per sweep-1 chunk (g1 x k0p ints)
   int64_t oVs;       // emulated products: bf16 slices of V, kVsTileBytes per row tile (g1 x vs_tiles tiles)
   int64_t vs_tiles;  // row tiles of kUmmaKT real steps per sweep-1 chunk
+  int64_t oPs;  // third choice of P: state of the polar iteration (stop flag, final buffer, errors)
   int64_t lev_off[kMaxLevels + 1];  // first node index of each level (R and F arrays)
   int32_t lev_cnt[kMaxLevels + 1];  // nodes per level; level 0 = leaves
 };

@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
 // updates column j + 1 forms reflector j + 1 from it at once (its norm comes
 // from the values it just wrote), so a step costs one barrier.  Outputs as
 // k_tree_up: the node's R, and per node the bottom parts, tops and betas of
-// its reflectors for the downward pass.
+// its reflectors for the downward pass.  Used on the wide levels; the narrow
+// levels keep k_tree_up, whose four row groups per column shorten each step.
 constexpr int kTreeUpG = 8;  // nodes per CTA at most
 
 __host__ __device__ inline size_t tree_up_p_smem(int G, int kmax, size_t elem) {

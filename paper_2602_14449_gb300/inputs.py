@@ -256,6 +256,7 @@ class BProblem:
     V: torch.Tensor
     U: torch.Tensor
     A: torch.Tensor
+    d: torch.Tensor | None = None  # the diagonal, when B is diagonal
 
 
 def b_inner_problem(n: int, k0: int, k: int, kappa_b: float = 1e2, dtype=torch.float64,
@@ -279,3 +280,22 @@ def b_inner_problem(n: int, k0: int, k: int, kappa_b: float = 1e2, dtype=torch.f
     U[:k0 + k] = torch.linalg.solve_triangular(L.conj().T, torch.eye(k0 + k, dtype=dtype), upper=True)
     A = gaussian(n, k, dtype, g)
     return BProblem(B=B, V=colmajor(V), U=colmajor(U), A=colmajor(A))
+
+
+def diag_b_problem(n: int, k0: int, k: int, kappa_b: float = 1e5, dtype=torch.float64,
+                   seed: int = SEED_BASE + 9) -> BProblem:
+    """Inputs of Algorithm 4 (Section 5) with a diagonal B = diag(d): d
+    log-spaced in [1, kappa_b] in a seeded random order, V = D^{-1/2} Q0 with Q0
+    the Q factor of a Gaussian n x k0 matrix (so V^* B V = I), U = D^{-1/2} [I; 0]
+    (the Cholesky construction of Section 5 for a diagonal B), A ~ N(0,1).
+    ``B`` is the dense diag(d) for the CPU oracle; ``d`` is the diagonal."""
+    g = _gen(seed, "cpu")
+    d = torch.logspace(0.0, math.log10(kappa_b), n, dtype=torch.float64)[torch.randperm(n, generator=g)]
+    isd = 1.0 / torch.sqrt(d)
+    Q0 = orthonormal(n, k0, dtype, g) if k0 > 0 else torch.zeros(n, 0, dtype=dtype)
+    V = Q0 * isd[:, None].to(dtype)
+    U = torch.zeros(n, k0 + k, dtype=dtype)
+    idx = torch.arange(k0 + k)
+    U[idx, idx] = isd[:k0 + k].to(dtype)
+    A = gaussian(n, k, dtype, g)
+    return BProblem(B=torch.diag(d).to(dtype), V=colmajor(V), U=colmajor(U), A=colmajor(A), d=d)

@@ -21,10 +21,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtho.so")
 
 THO_OK, THO_ERR_ARG, THO_ERR_SHAPE, THO_ERR_ALIGN, THO_ERR_NOMEM = 0, 1, 2, 3, 4
-THO_ERR_CUDA, THO_ERR_TIMEOUT, THO_ERR_NONFINITE, THO_ERR_UNSUPPORTED = 5, 6, 7, 8
+THO_ERR_CUDA, THO_ERR_TIMEOUT, THO_ERR_NONFINITE, THO_ERR_UNSUPPORTED, THO_ERR_NOCONV = 5, 6, 7, 8, 9
 THO_F64, THO_C128 = 0, 1
 THO_PREC_FP64, THO_PREC_FP32_BULK, THO_PREC_FP64_EMU = 0, 1, 2
-THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE, THO_FLAG_P_MLU = 0x1, 0x2, 0x4
+THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE, THO_FLAG_P_MLU, THO_FLAG_P_POLAR = 0x1, 0x2, 0x4, 0x8
 THO_MAX_K0, THO_MAX_K = 128, 32
 THO_TUNE_MAX_SPLIT = 1 << 20
 
@@ -34,7 +34,7 @@ EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_pla
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
             "tho_orth_noalloc", "tho_plan_tuned", "tho_plan_tuning", "tho_autotune", "tho_tune_key",
-            "tho_tune_cache_get", "tho_tune_cache_put", "tho_plan_expire_wait")
+            "tho_tune_cache_get", "tho_tune_cache_put", "tho_plan_expire_wait", "tho_orth_b")
 THO_NUM_PHASES = 11
 
 
@@ -107,6 +107,8 @@ def load(path: str | None = None):
         lib.tho_orth.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp, vp]
         lib.tho_orth.restype = ctypes.c_int
         lib.tho_orth_host.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp, vp]
+        lib.tho_orth_b.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, vp, vp, vp]
+        lib.tho_orth_b.restype = ctypes.c_int
         lib.tho_orth_host.restype = ctypes.c_int
         lib.tho_orth_host_wait.argtypes = [vp, vp]
         lib.tho_orth_host_wait.restype = ctypes.c_int
@@ -381,6 +383,30 @@ def orth_host(V: torch.Tensor, A: torch.Tensor, Q: torch.Tensor, R: torch.Tensor
     return Q, R, S
 
 
+def orth_b(d: torch.Tensor, V: torch.Tensor, A: torch.Tensor, prec: int = THO_PREC_FP64, flags: int = 0,
+           plan: Plan | None = None):
+    """tho_orth_b: Algorithm 4 (B-inner product) for B = diag(d), with the
+    initial basis U = D^{-1/2} [I; 0].  d: n positive float64 CUDA values;
+    V (n x k0, V^* B V = I) and A (n x k) column-major CUDA tensors.
+    Returns (Q, R, S) with [V, Q]^* B [V, Q] = I."""
+    n, k = A.shape
+    k0 = V.shape[1] if V is not None else 0
+    if k0 == 0:
+        flags |= THO_FLAG_ALLOW_K0_ZERO
+    if d.dtype != torch.float64 or d.numel() != n or not d.is_cuda or not d.is_contiguous():
+        raise ValueError("d must be a contiguous float64 CUDA vector of n entries")
+    dt = A.dtype
+    Q = _empty_cm(n, k, dt, A.device)
+    R = _empty_cm(k, k, dt, A.device)
+    S = _empty_cm(k0, k, dt, A.device) if k0 > 0 else None
+    p = plan or get_plan([(n, k0, k)], dt, prec, flags)
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().tho_orth_b(p.handle, _ptr(d), _ptr(V) if k0 > 0 else None, _ld(V, "V") if k0 > 0 else n,
+                             _ptr(A), _ld(A, "A"), _ptr(Q), _ld(Q, "Q"), _ptr(R), _ptr(S), ctypes.c_void_p(st)),
+           "tho_orth_b")
+    return Q, R, S
+
+
 def orth_host_wait(plan: Plan):
     """Make the current torch stream wait for every orth_host output copy of ``plan``."""
     st = torch.cuda.current_stream().cuda_stream
@@ -432,14 +458,14 @@ class Blocks:
         return Q, R
 
 
-def orth_batched(pairs, prec: int = THO_PREC_FP64, plan: Plan | None = None, outs=None):
+def orth_batched(pairs, prec: int = THO_PREC_FP64, plan: Plan | None = None, outs=None, flags: int = 0):
     """Batched Algorithm 1 over a list of (V, A): one CUDA-graph replay.
 
     Returns a list of (Q, R, S).  ``outs`` may pass preallocated (Q, R, S) triples.
     """
     shapes = [(A.shape[0], V.shape[1], A.shape[1]) for V, A in pairs]
     dt = pairs[0][1].dtype
-    p = plan or get_plan(shapes, dt, prec, 0)
+    p = plan or get_plan(shapes, dt, prec, flags)
     arr = (Instance * len(pairs))()
     res = []
     for i, (V, A) in enumerate(pairs):

@@ -55,6 +55,8 @@ def test_shape_and_argument_errors(lib):
     assert _plan(lib, [(100, 4, 4, 7, 0, 0)]) == tho.THO_ERR_ARG         # unknown dtype
     assert _plan(lib, [(100, 4, 4, F, 5, 0)]) == tho.THO_ERR_ARG         # unknown precision
     assert _plan(lib, [(100, 4, 4, F, 0, 0x80)]) == tho.THO_ERR_ARG      # unknown flag
+    both = tho.THO_FLAG_P_MLU | tho.THO_FLAG_P_POLAR
+    assert _plan(lib, [(100, 4, 4, F, 0, both)]) == tho.THO_ERR_ARG      # two choices of P at once
     assert _plan(lib, [(100, 4, 4, F, 0, 0), (100, 4, 4, C, 0, 0)]) == tho.THO_ERR_ARG  # mixed dtypes
     assert _plan(lib, []) == tho.THO_ERR_ARG
     h = ctypes.c_void_p()
@@ -68,7 +70,7 @@ def test_shape_and_argument_errors(lib):
 
 
 def test_status_strings(lib):
-    for code in range(9):
+    for code in range(10):
         s = lib.tho_status_string(code).decode()
         assert s and s != "unknown status"
     assert lib.tho_status_string(99).decode() == "unknown status"

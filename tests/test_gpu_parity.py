@@ -372,6 +372,55 @@ def test_first_choice_of_P_matches_oracle(tho, dtype, prec_name, n, k0, k):
     assert float((Q2 - Q).abs().max()) < TOL_Q
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.complex128])
+@pytest.mark.parametrize("prec_name", ["THO_PREC_FP64", "THO_PREC_FP64_EMU"])
+@pytest.mark.parametrize("n,k0,k", [(3000, 16, 8), (20000, 128, 32), (785, 7, 30), (500, 1, 3)])
+def test_third_choice_of_P_matches_oracle(tho, dtype, prec_name, n, k0, k):
+    """The third choice of P (THO_FLAG_P_POLAR: polar factor of V_{1:k0,:} by the
+    Newton-Schulz iteration, T = I + M through its Cholesky factor) against the
+    oracle's Algorithm 1 with that choice (polar factor from an SVD)."""
+    prec = getattr(tho, prec_name)
+    p = inputs.random_problem(n, k0, k, dtype=dtype, seed=n + 9 * k0 + k)
+    plan = tho.Plan([(n, k0, k)], dtype, prec, tho.THO_FLAG_P_POLAR)
+    Q, R, S = tho.orth(p.V.cuda(), p.A.cuda(), prec=prec, plan=plan)
+    torch.cuda.synchronize()
+    assert plan.status() == tho.THO_OK
+    Qo, Ro, So, _ = oracle.two_stage_polar(p.V.numpy(), p.A.numpy())
+    np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+    np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=TOL_Q * max(1, np.abs(Ro).max()))
+    np.testing.assert_allclose(S.cpu().numpy(), So, atol=TOL_Q * max(1, np.abs(So).max()))
+    assert loo_np(p.V.numpy(), Q.cpu().numpy()) < TOL_LOO
+
+
+def test_third_choice_batched(tho):
+    """The polar iteration over a batch (one launch per step for all problems,
+    each stopping on its own) against the oracle per problem."""
+    probs = [inputs.random_problem(n, k0, k, seed=70 + i) for i, (n, k0, k) in enumerate(BATCH_SHAPES)]
+    pairs = [(p.V.cuda(), p.A.cuda()) for p in probs]
+    res = tho.orth_batched(pairs, flags=tho.THO_FLAG_P_POLAR)
+    torch.cuda.synchronize()
+    for p, (Q, R, S) in zip(probs, res):
+        Qo, _, So, _ = oracle.two_stage_polar(p.V.numpy(), p.A.numpy())
+        np.testing.assert_allclose(Q.cpu().numpy(), Qo, atol=TOL_Q)
+        np.testing.assert_allclose(S.cpu().numpy(), So, atol=TOL_Q * max(1, np.abs(So).max()))
+
+
+def test_third_choice_singular_v1_latches_noconv(tho):
+    """V_{1:k0,:} exactly singular (a zero row): the polar factor is not unique
+    and the iteration cannot reach a unitary matrix; the plan latches
+    THO_ERR_NOCONV instead of returning silently."""
+    n, k0, k = 2000, 8, 4
+    p = inputs.random_problem(n, k0, k, seed=77)
+    X = p.V.clone()
+    X[3, :] = 0.0
+    V = inputs.colmajor(torch.linalg.qr(X, mode="reduced")[0])
+    V[3, :] = 0.0  # the QR leaves rounding-level entries in the zero row; clear them
+    plan = tho.Plan([(n, k0, k)], torch.float64, tho.THO_PREC_FP64, tho.THO_FLAG_P_POLAR)
+    tho.orth(V.cuda(), p.A.cuda(), plan=plan)
+    torch.cuda.synchronize()
+    assert plan.status() == tho.THO_ERR_NOCONV
+
+
 def test_first_choice_refused_by_the_adjoint(tho):
     n, k0, k = 2000, 8, 4
     p = inputs.random_problem(n, k0, k, dtype=torch.float64, seed=3)

@@ -4,7 +4,9 @@ With V built so that the modified LU of V_{1:k0,:} returns the ill-conditioned U
 of eq. (badmlu) (kappa_2(U) ~ 1.1e7), the second choice of P (the default) stays
 at the FP64 level and matches the oracle entrywise, while the first choice
 (THO_FLAG_P_MLU) loses orthogonality the way the paper's Table 4 and the oracle
-do.  k = 32 (the library's column limit) instead of the paper's 100.
+do.  The third choice (THO_FLAG_P_POLAR) is stable like the second (Table 4's
+third row) and equals the oracle's third choice entrywise.  k = 32 (the
+library's column limit) instead of the paper's 100.
 """
 import numpy as np
 import pytest
@@ -55,3 +57,20 @@ def test_table4_inputs_on_the_device(tho, prec_name):
     orc = _metrics(Vn, An, r[0], r[1], r[2])
     assert 1e-9 < dev[1] < 1e-3, dev
     assert ((dev >= orc / 1000) & (dev <= orc * 1000)).all(), (dev, orc)
+
+
+@pytest.mark.parametrize("prec_name", ["THO_PREC_FP64", "THO_PREC_FP64_EMU"])
+def test_table4_third_choice_on_the_device(tho, prec_name):
+    """Third choice on the Appendix A inputs: Table 4 prints 5.68e-16, 1.42e-15,
+    1.94e-15; the device result stays within the FP64 parity tolerance and equals
+    the oracle's third choice (SVD polar factor) entrywise."""
+    prec = getattr(tho, prec_name)
+    p = inputs.table4_problem(1000, 100, 32)
+    Vn, An = p.V.numpy(), p.A.numpy()
+    Q, R, S = tho.orth(p.V.cuda(), p.A.cuda(), prec=prec, flags=tho.THO_FLAG_P_POLAR)
+    torch.cuda.synchronize()
+    Q, R, S = Q.cpu().numpy(), R.cpu().numpy(), S.cpu().numpy()
+    Qo, Ro, So, _ = oracle.two_stage_polar(Vn, An)
+    np.testing.assert_allclose(Q, Qo, atol=1e-11, rtol=0)
+    np.testing.assert_allclose(S, So, atol=1e-11 * max(1.0, np.abs(So).max()), rtol=0)
+    assert (_metrics(Vn, An, Q, R, S) < 1e-13).all()

@@ -634,27 +634,52 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
         break;
       }
       tc_fence_after();
-      long long h[16], l[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) h[c] = l[c] = 0;
+      // Per output column the exact int64 sums h (levels 2..5) and l (levels
+      // 6..9) are converted to the product's double right away; the columns go
+      // in two passes of four to keep few sums live.  Complex: the Im-block
+      // columns are read first and sent to the neighbour lane at once (only its
+      // partner needs them), starting the sums of the Re-block columns
+      // (subtracted on a Re lane, added on an Im lane).
+      double out[8];
+      const int part = C ? (lane & 1) : 0;
+      const int m = qd * 32 + lane;
       if (act) {
         const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + j0;
 #pragma unroll
-        for (int L = 0; L < kEmuLevels; ++L) {
-          uint32_t r[16];
-          tmem_ld4(tb + L * N, *reinterpret_cast<uint32_t(*)[4]>(r));
-          tmem_ld4(tb + L * N + 4, *reinterpret_cast<uint32_t(*)[4]>(r + 4));
-          if (C) {
-            tmem_ld4(tb + L * N + kpe, *reinterpret_cast<uint32_t(*)[4]>(r + 8));
-            tmem_ld4(tb + L * N + kpe + 4, *reinterpret_cast<uint32_t(*)[4]>(r + 12));
-          }
-          tmem_ld_wait();
-          const int sh = 21 - 7 * (L & 3);
+        for (int half = 0; half < 2; ++half) {
+          long long h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+          auto read4 = [&](uint32_t t) {
 #pragma unroll
-          for (int c = 0; c < (C ? 16 : 8); ++c) {
-            const long long v = (long long)__float2int_rz(__uint_as_float(r[c])) << sh;
-            if (L < 4) h[c] += v;
-            else l[c] += v;
+            for (int L = 0; L < kEmuLevels; ++L) {
+              uint32_t r[4];
+              tmem_ld4(t + L * N, r);
+              tmem_ld_wait();
+              const int sh = 21 - 7 * (L & 3);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const long long v = (long long)__float2int_rz(__uint_as_float(r[c])) << sh;
+                if (L < 4) h[c] += v;
+                else l[c] += v;
+              }
+            }
+          };
+          if constexpr (C) {
+            read4(tb + kpe + 4 * half);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const long long xh = __shfl_xor_sync(0xffffffffu, h[c], 1);
+              const long long xl = __shfl_xor_sync(0xffffffffu, l[c], 1);
+              h[c] = part ? xh : -xh;
+              l[c] = part ? xl : -xl;
+            }
+          }
+          read4(tb + 4 * half);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int j = j0 + 4 * half + c;
+            const int sc = (j < k ? eZ[j] : 1024) - 966;
+            // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
+            out[4 * half + c] = scale2((double)h[c], sc - 35) + scale2((double)l[c], sc - 63);
           }
         }
       }
@@ -662,29 +687,18 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
       __syncwarp();
       if (lane == 0) mbar_arrive(b_free);
       if (!act) continue;
-      const int m = qd * 32 + lane;
+      const int64_t row = r_begin + (int64_t)u * UR + (C ? (m >> 1) : m);
+      if (row < r_end) {
+        // One running pointer per operand (column stride ld): few address
+        // registers live next to the eight outputs.
+        const double* pb = Bd + (int64_t)j0 * ldb + row * RPE + part;
+        double* pq = Qd + (int64_t)j0 * ldq + row * RPE + part;
+        const int nc = min(8, k - j0);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int j = j0 + c;
-        long long hh = h[c], ll = l[c];
-        int64_t row;
-        int part = 0;
-        if constexpr (C) {
-          // Neighbour lane's Im-block sums: subtracted on the Re lane, added on the Im lane.
-          const long long xh = __shfl_xor_sync(0xffffffffu, h[8 + c], 1);
-          const long long xl = __shfl_xor_sync(0xffffffffu, l[8 + c], 1);
-          part = m & 1;
-          hh = part ? hh + xh : hh - xh;
-          ll = part ? ll + xl : ll - xl;
-          row = r_begin + (int64_t)u * UR + (m >> 1);
-        } else {
-          row = r_begin + (int64_t)u * UR + m;
-        }
-        if (row < r_end && j < k) {
-          const int sc = eZ[j] - 966;
-          // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
-          const double v = scale2((double)hh, sc - 35) + scale2((double)ll, sc - 63);
-          Qd[(int64_t)j * ldq + row * RPE + part] = Bd[(int64_t)j * ldb + row * RPE + part] + v;
+        for (int c = 0; c < 8; ++c) {
+          if (c < nc) *pq = *pb + out[c];
+          pb += ldb;
+          pq += ldq;
         }
       }
     }

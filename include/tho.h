@@ -301,7 +301,10 @@ tho_status_t tho_orth_b(tho_plan_t plan, const double* d, const void* V, int64_t
 /* Reverse-mode derivative of the map (V, A) -> Q of Algorithm 1 (second
  * choice of P, exact-arithmetic map at arbitrary V, A: V need not have
  * orthonormal columns, only V_{1:k0,:} and the trailing block of A' must have
- * full rank) for a real FP64 plan with count = 1.  Given Q from tho_orth on the same V, A and the upstream
+ * full rank) for a THO_PREC_FP64 plan (real or complex) with count = 1 and
+ * k0 >= 1.  Complex values follow the convention of a real loss L:
+ * gradients are dL/dRe z + i dL/dIm z, and the relation below uses the real
+ * inner product <x, y> = Re sum conj(x) y.  Given Q from tho_orth on the same V, A and the upstream
  * gradient dQ (n x k), writes dV (n x k0) and dA (n x k) such that
  * <dQ, Q'(V, A)[dV_dir, dA_dir]> = <dV, dV_dir> + <dA, dA_dir> (real inner
  * products).  (W, T) and the trailing factorization are recomputed, not

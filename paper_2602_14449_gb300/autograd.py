@@ -2,7 +2,8 @@
 
 The backward is the hand-written adjoint of the map (V, A) -> Q of Algorithm 1
 (second choice of P); it recomputes (W, T) and the small solves from V, A and
-the saved Q instead of storing per-panel reflectors.  Real FP64 only.
+the saved Q instead of storing per-panel reflectors.  FP64, real or complex
+(torch's gradient convention for complex tensors).
 """
 import torch
 
@@ -24,5 +25,5 @@ class TwoStageOrth(torch.autograd.Function):
 
 
 def two_stage_orth(V: torch.Tensor, A: torch.Tensor) -> torch.Tensor:
-    """Q of Algorithm 1 (column-major float64 CUDA tensors), differentiable in V and A."""
+    """Q of Algorithm 1 (column-major float64 or complex128 CUDA tensors), differentiable in V and A."""
     return TwoStageOrth.apply(V, A)

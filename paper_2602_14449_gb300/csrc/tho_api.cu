@@ -687,13 +687,13 @@ tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, cons
                                int64_t lddv, void* dA, int64_t ldda, void* stream) {
   if (!plan || plan->pc.count != 1) return THO_ERR_ARG;
   const Inst& I = plan->pc.h_insts[0];
-  if (plan->pc.dtype != THO_F64 || plan->pc.prec != THO_PREC_FP64 || I.k0 < 1 ||
+  if (plan->pc.prec != THO_PREC_FP64 || I.k0 < 1 ||
       (plan->pc.flags & (THO_FLAG_P_MLU | THO_FLAG_P_POLAR)))
     return THO_ERR_UNSUPPORTED;
   if (!V || !A || !Q || !dQ || !dV || !dA) return THO_ERR_ARG;
   if (ldv < I.n || lda < I.n || ldq < I.n || lddq < I.n || lddv < I.n || ldda < I.n) return THO_ERR_ARG;
   for (const void* p : {V, A, Q, dQ, (const void*)dV, (const void*)dA})
-    if (reinterpret_cast<uintptr_t>(p) % sizeof(double)) return THO_ERR_ALIGN;
+    if (reinterpret_cast<uintptr_t>(p) % plan->L->elem) return THO_ERR_ALIGN;
   if (!plan->bwd) {
     plan->bwd = new (std::nothrow) tho::BwdState();
     if (!plan->bwd) return THO_ERR_NOMEM;
@@ -706,9 +706,7 @@ tho_status_t tho_orth_backward(tho_plan_t plan, const void* V, int64_t ldv, cons
       return e == cudaErrorMemoryAllocation ? THO_ERR_NOMEM : THO_ERR_CUDA;
     }
   }
-  tho::BwdIo io{static_cast<const double*>(V), static_cast<const double*>(A), static_cast<const double*>(Q),
-                static_cast<const double*>(dQ), static_cast<double*>(dV), static_cast<double*>(dA),
-                ldv, lda, ldq, lddq, lddv, ldda};
+  tho::BwdIo io{V, A, Q, dQ, dV, dA, ldv, lda, ldq, lddq, lddv, ldda};
   if (tho::backward_run(plan->pc, *plan->bwd, io, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
     return THO_ERR_CUDA;
   return THO_OK;

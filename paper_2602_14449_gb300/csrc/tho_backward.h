@@ -9,34 +9,38 @@
 
 namespace tho {
 
-// Offsets (doubles) of the backward workspace.
+// Offsets (elements of the plan's FP64 storage type) of the backward workspace.
 struct BwdLayout {
-  int64_t oGA, oGQ, oGD;      // g1 x k0 x k partials of V_2^T A_2, V_2^T Q_2, V_2^T dQ_2
-  int64_t oZ, oZq, oY, oGb;   // k0 x k
-  int64_t oMp, oRp;           // g1 x k x k partials of Xb^T Qbar and Qbar^T A'_2
+  int64_t oGA, oGD;           // g1 x k0 x k partials of V_2^* A_2 and V_2^* dQ_2
+  int64_t oZ, oZq, oY, oGb;   // k0 x k (ld k0)
+  int64_t oZp, oZqp, oYp, oGbp;  // the same, zero-padded to k0p x kp (ld k0p), for the row sweeps
+  int64_t oMp, oRp;           // g1 x k x k partials of Xb^* Qbar and Qbar^* A'_2
   int64_t oR, oC, oRi;        // k x k, k x k, k (R, copyltu(-M), 1 / R_ii)
-  int64_t oAG;                // g1 x k0 x k partials of V_2^T Abar'_2
+  int64_t oAG;                // g1 x k0 x k partials of V_2^* Abar'_2
   int64_t oK1, oK2, oK3;      // k0 x k0 temporaries of the head step
   int64_t oE, oX;             // m x k scratch: Qbar and Xb (ld m)
   int64_t total;
 };
 
+// Pointers of one backward call (device, column-major; element type of the plan).
 struct BwdIo {
-  const double* V;
-  const double* A;
-  const double* Q;
-  const double* dQ;
-  double* dV;
-  double* dA;
+  const void* V;
+  const void* A;
+  const void* Q;
+  const void* dQ;
+  void* dV;
+  void* dA;
   int64_t ldv, lda, ldq, lddq, lddv, ldda;
 };
 
 // Lazily allocated per plan on the first backward call.
 struct BwdState {
-  double* wsb = nullptr;
-  Inst* d_insts_b = nullptr;  // three copies of the problem with oG1 -> GA, GQ, GD
+  void* wsb = nullptr;
+  Inst* d_insts_b = nullptr;  // two copies of the problem with oG1 -> GA, GD
   BwdLayout bl{};
   size_t smem_b = 0, smem_c = 0, smem_d = 0;
+  bool small_smem = true;     // small operands of the row sweeps staged in shared memory
+  int dv_cols = 64;           // dV columns per block of the last sweep
 };
 
 cudaError_t backward_prepare(const PlanCore& pc, BwdState& st);

@@ -486,7 +486,9 @@ def orth_batched(pairs, prec: int = THO_PREC_FP64, plan: Plan | None = None, out
 
 
 def orth_backward(V, A, Q, dQ, plan: Plan | None = None):
-    """Reverse-mode derivative of (V, A) -> Q (real FP64): returns (dV, dA)."""
+    """Reverse-mode derivative of (V, A) -> Q (FP64, real or complex): returns
+    (dV, dA); for complex tensors the gradients of a real loss in torch's
+    convention (dL/dRe z + i dL/dIm z)."""
     n, k = A.shape
     k0 = V.shape[1]
     dV = _empty_cm(n, k0, V.dtype, V.device)

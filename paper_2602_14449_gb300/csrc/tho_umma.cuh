@@ -28,6 +28,7 @@ constexpr int kUmmaThreads = 512;  // warp 0 issues the MMAs; warps 1..15 split;
 constexpr int kUmmaStages = 2;
 constexpr int kUmmaM = 128;        // MMA rows: the (padded) columns of V
 constexpr int kUmmaGroup = 4;      // stages per fold (4 x 32 = 128 steps)
+constexpr int kUmmaAhead = 4;      // stages whose raw lines the Gram producers request into L2 ahead
 constexpr int kUmmaSpins = 1 << 25;
 // Value pairs per producer thread per stage: (128 + 32) rows x 16 pairs over 480 threads.
 constexpr int kUmmaPairs = ((kUmmaM + 32) * (kUmmaKT / 2) + kUmmaThreads - 33) / (kUmmaThreads - 32);
@@ -327,8 +328,25 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
     const bool loader = which && warp == 1;
     const int pbase = which ? 64 : 32, nprod = kUmmaThreads - pbase;
     const int npA = which ? 0 : kUmmaM * (kUmmaKT / 2), npB = (C ? kpe : N) * (kUmmaKT / 2);
+    // The lines of the stage kUmmaAhead stages on (two 128-byte lines per
+    // column of V and X) are requested into L2 while this one is split
+    // (prefetch.global.L2 holds no registers), so each stage's loads find
+    // their data in L2 rather than waiting on HBM.
+    const int ncolx = (which ? 0 : k0) + k;
     for (int t = 0; t < ntile && !*abort_flag; ++t) {
       const int s = t & 1;
+      if (!loader && t + kUmmaAhead < ntile) {
+        const int64_t rp = (r_begin + (int64_t)(t + kUmmaAhead) * TR) * RPE;
+        const int64_t re = r_end * RPE;
+        for (int idx = threadIdx.x - pbase; idx < 2 * ncolx; idx += nprod) {
+          const int col = (which ? k0 : 0) + (idx >> 1);
+          const int64_t q = rp + (idx & 1) * 16;
+          if (q < re) {
+            const double* src = col < k0 ? Vd + (int64_t)col * ldv + q : Ad + (int64_t)(col - k0) * lda + q;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
+          }
+        }
+      }
       if (t >= 2 && !mbar_wait(b_empty + 8 * s, ((t >> 1) - 1) & 1)) {
         *abort_flag = 1;
         break;
@@ -635,52 +653,46 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
       }
       tc_fence_after();
       // Per output column the exact int64 sums h (levels 2..5) and l (levels
-      // 6..9) are converted to the product's double right away; the columns go
-      // in two passes of four to keep few sums live.  Complex: the Im-block
-      // columns are read first and sent to the neighbour lane at once (only its
-      // partner needs them), starting the sums of the Re-block columns
-      // (subtracted on a Re lane, added on an Im lane).
+      // 6..9).  Complex: at every level the Im-block values are swapped with the
+      // neighbour lane (one 32-bit shuffle each) and combined at once with the
+      // lane's Re-block values (subtracted on a Re lane, added on an Im lane),
+      // so only eight sum pairs are live; one TMEM wait per level.
       double out[8];
       const int part = C ? (lane & 1) : 0;
       const int m = qd * 32 + lane;
       if (act) {
         const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + j0;
+        long long h[8], l[8];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          long long h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
-          auto read4 = [&](uint32_t t) {
+        for (int c = 0; c < 8; ++c) h[c] = l[c] = 0;
 #pragma unroll
-            for (int L = 0; L < kEmuLevels; ++L) {
-              uint32_t r[4];
-              tmem_ld4(t + L * N, r);
-              tmem_ld_wait();
-              const int sh = 21 - 7 * (L & 3);
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const long long v = (long long)__float2int_rz(__uint_as_float(r[c])) << sh;
-                if (L < 4) h[c] += v;
-                else l[c] += v;
-              }
-            }
-          };
-          if constexpr (C) {
-            read4(tb + kpe + 4 * half);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const long long xh = __shfl_xor_sync(0xffffffffu, h[c], 1);
-              const long long xl = __shfl_xor_sync(0xffffffffu, l[c], 1);
-              h[c] = part ? xh : -xh;
-              l[c] = part ? xl : -xl;
-            }
+        for (int L = 0; L < kEmuLevels; ++L) {
+          uint32_t r[16];
+          tmem_ld4(tb + L * N, *reinterpret_cast<uint32_t(*)[4]>(r));
+          tmem_ld4(tb + L * N + 4, *reinterpret_cast<uint32_t(*)[4]>(r + 4));
+          if (C) {
+            tmem_ld4(tb + L * N + kpe, *reinterpret_cast<uint32_t(*)[4]>(r + 8));
+            tmem_ld4(tb + L * N + kpe + 4, *reinterpret_cast<uint32_t(*)[4]>(r + 12));
           }
-          read4(tb + 4 * half);
+          tmem_ld_wait();
+          const int sh = 21 - 7 * (L & 3);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int j = j0 + 4 * half + c;
-            const int sc = (j < k ? eZ[j] : 1024) - 966;
-            // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
-            out[4 * half + c] = scale2((double)h[c], sc - 35) + scale2((double)l[c], sc - 63);
+          for (int c = 0; c < 8; ++c) {
+            long long v = (long long)__float2int_rz(__uint_as_float(r[c]));
+            if (C) {
+              const long long x = (long long)__float2int_rz(__uint_as_float(__shfl_xor_sync(0xffffffffu, r[8 + c], 1)));
+              v = part ? v + x : v - x;
+            }
+            if (L < 4) h[c] += v << sh;
+            else l[c] += v << sh;
           }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int j = j0 + c;
+          const int sc = (j < k ? eZ[j] : 1024) - 966;
+          // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
+          out[c] = scale2((double)h[c], sc - 35) + scale2((double)l[c], sc - 63);
         }
       }
       tc_fence_before();

@@ -656,15 +656,16 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
       // 6..9).  Complex: at every level the Im-block values are swapped with the
       // neighbour lane (one 32-bit shuffle each) and combined at once with the
       // lane's Re-block values (subtracted on a Re lane, added on an Im lane),
-      // so only eight sum pairs are live; one TMEM wait per level.
-      double out[8];
+      // so only eight sum pairs are live; one TMEM wait per level.  The
+      // conversion to FP64 and the stores come after the accumulators are
+      // released to the next tile's MMAs.
       const int part = C ? (lane & 1) : 0;
       const int m = qd * 32 + lane;
+      long long h[8], l[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) h[c] = l[c] = 0;
       if (act) {
         const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + j0;
-        long long h[8], l[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) h[c] = l[c] = 0;
 #pragma unroll
         for (int L = 0; L < kEmuLevels; ++L) {
           uint32_t r[16];
@@ -687,13 +688,6 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
             else l[c] += v << sh;
           }
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int j = j0 + c;
-          const int sc = (j < k ? eZ[j] : 1024) - 966;
-          // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
-          out[c] = scale2((double)h[c], sc - 35) + scale2((double)l[c], sc - 63);
-        }
       }
       tc_fence_before();
       __syncwarp();
@@ -702,13 +696,17 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
       const int64_t row = r_begin + (int64_t)u * UR + (C ? (m >> 1) : m);
       if (row < r_end) {
         // One running pointer per operand (column stride ld): few address
-        // registers live next to the eight outputs.
+        // registers live next to the sums.
         const double* pb = Bd + (int64_t)j0 * ldb + row * RPE + part;
         double* pq = Qd + (int64_t)j0 * ldq + row * RPE + part;
         const int nc = min(8, k - j0);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          if (c < nc) *pq = *pb + out[c];
+          if (c < nc) {
+            const int sc = eZ[j0 + c] - 966;
+            // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
+            *pq = *pb + (scale2((double)h[c], sc - 35) + scale2((double)l[c], sc - 63));
+          }
           pb += ldb;
           pq += ldq;
         }

@@ -66,6 +66,16 @@ __device__ __forceinline__ double scale2(double x, int e) {
   return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(x, e);
 }
 
+// x 2^e for x = 0 or a normal double, by adding e to the exponent field with
+// an integer add when the result stays normal (then exactly x 2^e, the same
+// bits as scale2, without an FP64 multiply), else by scale2.
+__device__ __forceinline__ double scale2i(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex != 0 && ex + e >= 1 && ex + e <= 2046) return __longlong_as_double(b + ((long long)e << 52));
+  return scale2(x, e);
+}
+
 // The 56-bit fixed-point magnitude X of x relative to emax (the integer
 // emu_split slices), as its top and bottom 28 bits, and the sign.  With M the
 // 53-bit mantissa and sh = e - emax + 3 <= 3: top = M >> (28 - sh); bottom =

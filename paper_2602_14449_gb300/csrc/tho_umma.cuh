@@ -241,15 +241,17 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
     for (int c = 0; c < 16; c += 4) {
       if (c >= cpw) continue;
       long long h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+      // All eight levels of this group of four columns in flight, one wait.
+      uint32_t r[kEmuLevels][4];
+#pragma unroll
+      for (int L = 0; L < kEmuLevels; ++L) tmem_ld4(tb + L * N + c, r[L]);
+      tmem_ld_wait();
 #pragma unroll
       for (int L = 0; L < kEmuLevels; ++L) {
-        uint32_t r[4];
-        tmem_ld4(tb + L * N + c, r);
-        tmem_ld_wait();
         const int sh = 21 - 7 * (L & 3);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const long long v = (long long)__float2int_rz(__uint_as_float(r[e])) << sh;
+          const long long v = (long long)__float2int_rz(__uint_as_float(r[L][e])) << sh;
           if (L < 4) h[e] += v;
           else l[e] += v;
         }
@@ -705,7 +707,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
           if (c < nc) {
             const int sc = eZ[j0 + c] - 966;
             // FP64 scaling here: this epilogue is issue-bound, not FP64-bound.
-            *pq = *pb + (scale2((double)h[c], sc - 35) + scale2((double)l[c], sc - 63));
+            *pq = *pb + (scale2i((double)h[c], sc - 35) + scale2i((double)l[c], sc - 63));
           }
           pb += ldb;
           pq += ldq;

@@ -267,9 +267,10 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
   pc.sms = sms;
 
   // Per-instance partition and workspace layout.
-  // Single problem: two chunks per SM less one, so that the SM running the
-  // small QR of V_{1:k0,:} beside the first Gram sweep takes one chunk fewer.
-  const int64_t target_total = t_split > 0 ? t_split : (count == 1 ? 2 * (int64_t)sms - 1 : 8 * (int64_t)sms);
+  // Single problem: two chunks per SM on all SMs but one, which runs the small
+  // QR of V_{1:k0,:} beside the first Gram sweep (whose CTAs each fill an SM's
+  // registers): two even waves on the others.
+  const int64_t target_total = t_split > 0 ? t_split : (count == 1 ? 2 * ((int64_t)sms - 1) : 8 * (int64_t)sms);
   p->split_chunks = (int32_t)target_total;
   p->balance = t_balance;
   // Each problem's share of the chunks: in proportion to its trailing rows, or

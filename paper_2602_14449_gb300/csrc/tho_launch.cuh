@@ -148,7 +148,9 @@ cudaError_t configure_impl(PlanCore& pc) {
   if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
   pc.smem_leaf_emu = leaf_emu_smem(pc.P, pc.kpmax, sizeof(S));
   if (EMU && (e = raise((const void*)k_leaf_emu<S>, pc.smem_leaf_emu)) != cudaSuccess) return e;
-  if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_down<S, 4>, pc.smem_tree)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_down<S, 8>, pc.smem_tree)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_down<S, 32>, pc.smem_tree)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_up_p<S>, tree_up_p_smem(kTreeUpG, pc.kmax, sizeof(S)))) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down_w<S>, pc.smem_tree)) != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
@@ -171,36 +173,39 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   void* ws = pc.ws;
   const dim3 blk(kThreads);
   if (pc.any_k0) {
-    // QR of V_{1:k0,:} on the side stream, overlapping the first Gram sweep.
-    cudaStream_t sq = pc.side ? pc.side : st;
+    // QR of V_{1:k0,:} beside the first Gram sweep.  The QR (one CTA) is
+    // launched first, on the caller's stream, so that it takes an SM before the
+    // Gram's CTAs (which fill every register of an SM) occupy them all; the
+    // Gram runs on the side stream, forked before the QR.
+    cudaStream_t sg = pc.side ? pc.side : st;
     if (pc.side) {
       cudaEventRecord(pc.ev_fork, st);
-      cudaStreamWaitEvent(sq, pc.ev_fork, 0);
+      cudaStreamWaitEvent(sg, pc.ev_fork, 0);
     }
-    hk(kPhQrV1, 0, sq);
+    hk(kPhQrV1, 0, st);
     if (pc.flags & 0x8u) {  // THO_FLAG_P_POLAR: the polar factor of V_{1:k0,:} by Newton-Schulz
       const int nt = (pc.k0max + kPolarTile - 1) / kPolarTile;
       const dim3 gp(nt * nt, pc.count);
-      k_polar_init<S><<<pc.count, 256, 0, sq>>>(insts, d_io, io0, ws);
+      k_polar_init<S><<<pc.count, 256, 0, st>>>(insts, d_io, io0, ws);
       for (int it = 0; it < kPolarMaxIt; ++it) {
-        k_polar_gram<S><<<gp, kPolarThreads, 0, sq>>>(insts, ws, it);
-        k_polar_step<S><<<gp, kPolarThreads, 0, sq>>>(insts, ws, it);
+        k_polar_gram<S><<<gp, kPolarThreads, 0, st>>>(insts, ws, it);
+        k_polar_step<S><<<gp, kPolarThreads, 0, st>>>(insts, ws, it);
       }
-      k_polar_t<S><<<gp, kPolarThreads, 0, sq>>>(insts, d_io, io0, ws);
-      k_polar_chol<S><<<pc.count, 1024, 0, sq>>>(insts, ws, pc.d_status);
+      k_polar_t<S><<<gp, kPolarThreads, 0, st>>>(insts, d_io, io0, ws);
+      k_polar_chol<S><<<pc.count, 1024, 0, st>>>(insts, ws, pc.d_status);
     } else {
-      k_v1qr<S><<<pc.count, kV1Threads, 0, sq>>>(insts, d_io, io0, ws, pc.flags);
+      k_v1qr<S><<<pc.count, kV1Threads, 0, st>>>(insts, d_io, io0, ws, pc.flags);
     }
-    hk(kPhQrV1, 1, sq);
-    if (pc.side) cudaEventRecord(pc.ev_join, sq);
+    hk(kPhQrV1, 1, st);
     if (pc.tab.gram_n > 0) {
-      hk(kPhGram, 0, st);
+      hk(kPhGram, 0, sg);
       if (EMU)
-        launch_gram_emu<S>(pc, insts, d_io, io0, items + pc.tab.gram_off, ws, 0, st);
+        launch_gram_emu<S>(pc, insts, d_io, io0, items + pc.tab.gram_off, ws, 0, sg);
       else
-        k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, st>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
-      hk(kPhGram, 1, st);
+        k_gram<S, B><<<pc.tab.gram_n, blk, pc.smem_gram, sg>>>(insts, d_io, io0, items + pc.tab.gram_off, ws);
+      hk(kPhGram, 1, sg);
     }
+    if (pc.side) cudaEventRecord(pc.ev_join, sg);
     if (pc.side) cudaStreamWaitEvent(st, pc.ev_join, 0);
     hk(kPhSolveZ, 0, st);
     k_solve_z<S><<<dim3(pc.count, pc.kmax), blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
@@ -235,20 +240,33 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     if (G >= 4)
       k_tree_up_p<S><<<(nl + G - 1) / G, tree_up_p_threads(G, pc.kmax), tree_up_p_smem(G, pc.kmax, sizeof(S)),
                        st>>>(insts, items + pc.tab.lev_off[l], nl, ws, l, G, pc.kmax);
-    else
-      k_tree_up<S><<<nl, kTreeThreads, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+    else if (nl >= 2 * pc.sms)
+      k_tree_up<S, 4><<<nl, kMaxKP * 4, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+    else if (nl >= pc.sms / 2)
+      k_tree_up<S, 8><<<nl, kMaxKP * 8, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+    else  // the levels near the root: a warp per column, the shortest chains
+      k_tree_up<S, 32><<<nl, kMaxKP * 32, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   }
   hk(kPhTreeUp, 1, st);
   hk(kPhRoot, 0, st);
   k_root<S><<<pc.count, blk, 0, st>>>(insts, d_io, io0, ws, pc.d_status, pc.flags);
   hk(kPhRoot, 1, st);
   hk(kPhTreeDown, 0, st);
-  for (int l = pc.Lmax; l >= 1; --l)
-    if (pc.tab.lev_n[l] > 0)
-      if (pc.tab.lev_n[l] >= kTreeDownWide * pc.sms)
-        k_tree_down_w<S><<<pc.tab.lev_n[l], 32, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
-      else
-        k_tree_down<S><<<pc.tab.lev_n[l], kTreeThreads, pc.smem_tree, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+  for (int l = pc.Lmax; l >= 1; --l) {
+    const int nl = pc.tab.lev_n[l];
+    const WorkItem* li = items + pc.tab.lev_off[l];
+    if (nl <= 0) continue;
+    // Widest levels: a warp per node; then four, eight and (near the root,
+    // where one node's chain is the whole level's time) 32 row groups per column.
+    if (nl >= kTreeDownWide * pc.sms)
+      k_tree_down_w<S><<<nl, 32, pc.smem_tree, st>>>(insts, li, ws, l);
+    else if (nl >= 2 * pc.sms)
+      k_tree_down<S, 4><<<nl, kMaxKP * 4, pc.smem_tree, st>>>(insts, li, ws, l);
+    else if (nl >= pc.sms / 2)
+      k_tree_down<S, 8><<<nl, kMaxKP * 8, pc.smem_tree, st>>>(insts, li, ws, l);
+    else
+      k_tree_down<S, 32><<<nl, kMaxKP * 32, pc.smem_tree, st>>>(insts, li, ws, l);
+  }
   hk(kPhTreeDown, 1, st);
   hk(kPhApply, 0, st);
   if (EMU)  // Qbar_b = Q_leaf,b F_b on tensor cores

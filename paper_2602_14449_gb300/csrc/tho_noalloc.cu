@@ -145,11 +145,11 @@ extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int
     ++I.L;
   }
   pc.Lmax = I.L;
-  // Split-n chunks as tho_plan: two per SM less one.  (tho_plan leaves one
-  // chunk out for the SM that runs the small QR of V_{1:k0,:} on a side
-  // stream; here that QR runs on the caller's stream first, but the same
-  // partition keeps the two entry points' results bitwise equal.)
-  const int64_t target = 2 * (int64_t)sms - 1;
+  // Split-n chunks as tho_plan: two per SM on all SMs but one.  (tho_plan
+  // leaves one SM to the small QR of V_{1:k0,:}, which runs beside the first
+  // Gram sweep; here the two run one after the other on the caller's stream,
+  // but the same partition keeps the two entry points' results bitwise equal.)
+  const int64_t target = 2 * ((int64_t)sms - 1);
   I.rows1 = cdiv(cdiv(I.m, target), tho::kTileRows) * tho::kTileRows;
   I.g1 = (int)cdiv(I.m, I.rows1);
   I.rows4 = I.rows1;

@@ -21,6 +21,28 @@ constexpr int kTreeThreads = kMaxKP * kTreeRG;  // 128
 
 __device__ __forceinline__ unsigned tree_mask4() { return 0xFu << (threadIdx.x & 28u); }
 
+// Lanes of one column's row groups (RG adjacent lanes, RG a power of two <= 32).
+template <int RG>
+__device__ __forceinline__ unsigned tree_mask() {
+  if constexpr (RG == 32) return 0xffffffffu;
+  else return ((1u << RG) - 1u) << (threadIdx.x & (32u - RG));
+}
+template <int RG>
+__device__ __forceinline__ double tree_sum(double v, unsigned m) {
+#pragma unroll
+  for (int o = 1; o < RG; o <<= 1) v += __shfl_xor_sync(m, v, o);
+  return v;
+}
+template <int RG>
+__device__ __forceinline__ z64 tree_sum(z64 v, unsigned m) {
+#pragma unroll
+  for (int o = 1; o < RG; o <<= 1) {
+    v.x += __shfl_xor_sync(m, v.x, o);
+    v.y += __shfl_xor_sync(m, v.y, o);
+  }
+  return v;
+}
+
 __device__ __forceinline__ double tree_sum4(double v, unsigned m) {
   v += __shfl_xor_sync(m, v, 1);
   return v + __shfl_xor_sync(m, v, 2);
@@ -43,8 +65,9 @@ __device__ __forceinline__ z64 tree_sum4(z64 v, unsigned m) {
 // through a double-buffered shared array: one barrier per step.  Kept per node
 // for the downward pass: the bottom parts (k x k upper triangular), the top
 // entries v_j and the betas.
-template <class S>
-__global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, const WorkItem* items, void* ws, int lev) {
+template <class S, int RG = kTreeRG>
+__global__ void __launch_bounds__(kMaxKP * RG) k_tree_up(const Inst* insts, const WorkItem* items, void* ws, int lev) {
+  constexpr int RW = kMaxKP / RG;  // rows per thread
   __shared__ S ush[2][kMaxKP];
   __shared__ S vsh[2];
   __shared__ double bsh[2];
@@ -63,13 +86,13 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
   }
   const S* Ra = Rn + c0 * kk;
   const S* Rb = Ra + kk;
-  const int c = threadIdx.x / kTreeRG, g = threadIdx.x % kTreeRG;
+  const int c = threadIdx.x / RG, g = threadIdx.x % RG;
   const bool own = c < k;
-  const unsigned m4 = tree_mask4();
-  S xb[kTreeRows];
+  const unsigned m4 = tree_mask<RG>();
+  S xb[RW];
 #pragma unroll
-  for (int q = 0; q < kTreeRows; ++q) {
-    const int r = g + kTreeRG * q;
+  for (int q = 0; q < RW; ++q) {
+    const int r = g + RG * q;
     xb[q] = (own && r <= c) ? Rb[r + c * k] : zero<S>();
   }
   S xt = own ? Ra[c * k] : zero<S>();  // top row j of column c at step j
@@ -85,17 +108,17 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
     if (c == j) {
       double s = (g == 0) ? abs2d(xt) : 0.0;
 #pragma unroll
-      for (int q = 0; q <= j / kTreeRG; ++q)
-        if (g + kTreeRG * q <= j) s += abs2d(xb[q]);
-      s = tree_sum4(s, m4);
+      for (int q = 0; q <= j / RG; ++q)
+        if (g + RG * q <= j) s += abs2d(xb[q]);
+      s = tree_sum<RG>(s, m4);
       make_reflector<S>(s, xt, bmine, vmine, rmine);
       if (g == 0) {
         bsh[buf] = bmine;
         vsh[buf] = vmine;
       }
 #pragma unroll
-      for (int q = 0; q <= j / kTreeRG; ++q) {
-        const int r = g + kTreeRG * q;
+      for (int q = 0; q <= j / RG; ++q) {
+        const int r = g + RG * q;
         if (r <= j) ush[buf][r] = xb[q];
       }
     }
@@ -105,29 +128,29 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
       // unused slot when j mod 4 != 3 (row group 3 has no row <= j there), so
       // no separate FP64 instruction is issued for it; then only that lane
       // holds the updated top entry.
-      const bool fold = (j % kTreeRG) != kTreeRG - 1;
-      const bool top = fold && g == kTreeRG - 1;
+      const bool fold = (j % RG) != RG - 1;
+      const bool top = fold && g == RG - 1;
       const double b = bsh[buf];
       if (b != 0.0) {
         const S vj = vsh[buf];
         S d = zero<S>();
         if (!fold) d = (g == 0) ? cmadd(zero<S>(), vj, xt) : zero<S>();
 #pragma unroll
-        for (int q = 0; q <= j / kTreeRG; ++q) {
-          const int r = g + kTreeRG * q;
-          if (q < j / kTreeRG) {
+        for (int q = 0; q <= j / RG; ++q) {
+          const int r = g + RG * q;
+          if (q < j / RG) {
             d = cmadd(d, ush[buf][r], xb[q]);  // r <= j in every lane
           } else {
             const bool act = r <= j;
             d = cmadd(d, act ? ush[buf][r] : (top ? vj : zero<S>()), act ? xb[q] : (top ? xt : zero<S>()));
           }
         }
-        d = scale(tree_sum4(d, m4), b);
+        d = scale(tree_sum<RG>(d, m4), b);
         if (!fold) xt = msub(xt, vj, d);
 #pragma unroll
-        for (int q = 0; q <= j / kTreeRG; ++q) {
-          const int r = g + kTreeRG * q;
-          if (q < j / kTreeRG) {
+        for (int q = 0; q <= j / RG; ++q) {
+          const int r = g + RG * q;
+          if (q < j / RG) {
             xb[q] = msub(xb[q], ush[buf][r], d);
           } else {
             const bool act = r <= j;
@@ -137,7 +160,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
           }
         }
       }
-      if (g == (fold ? kTreeRG - 1 : 0)) Rdst[j + c * k] = xt;  // entry (j, c) of the node's R is final
+      if (g == (fold ? RG - 1 : 0)) Rdst[j + c * k] = xt;  // entry (j, c) of the node's R is final
     }
     xt = xt_next;
   }
@@ -145,8 +168,8 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_up(const Inst* insts, con
   // Column c is untouched after its own step: its bottom part is reflector c's.
   S* ref = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
 #pragma unroll
-  for (int q = 0; q < kTreeRows; ++q) {
-    const int r = g + kTreeRG * q;
+  for (int q = 0; q < RW; ++q) {
+    const int r = g + RG * q;
     if (r < k) {
       ref[r + c * k] = (r <= c) ? xb[q] : zero<S>();
       if (r > c) Rdst[r + c * k] = zero<S>();
@@ -385,8 +408,9 @@ __global__ void k_root(const Inst* insts, const Io* iot, Io io0, void* ws, int* 
 // staged in shared memory once; the bottom block stays in registers, the top
 // row j of each column is read at step j (prefetched one step ahead) and is
 // final after it.  Columns are independent: no barrier inside the loop.
-template <class S>
-__global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, const WorkItem* items, void* ws, int lev) {
+template <class S, int RG = kTreeRG>
+__global__ void __launch_bounds__(kMaxKP * RG) k_tree_down(const Inst* insts, const WorkItem* items, void* ws, int lev) {
+  constexpr int RW = kMaxKP / RG;  // rows per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -418,14 +442,14 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, c
     }
   }
   __syncthreads();
-  const int c = threadIdx.x / kTreeRG, g = threadIdx.x % kTreeRG;
+  const int c = threadIdx.x / RG, g = threadIdx.x % RG;
   if (c >= k) return;
-  const unsigned m4 = tree_mask4();
+  const unsigned m4 = tree_mask<RG>();
   S* Fa = F + c0 * kk;
   S* Fb = Fa + kk;
-  S eb[kTreeRows];
+  S eb[RW];
 #pragma unroll
-  for (int q = 0; q < kTreeRows; ++q) eb[q] = zero<S>();
+  for (int q = 0; q < RW; ++q) eb[q] = zero<S>();
   S et = Fi[(k - 1) + c * k];
   // Unrolled steps (j = k-1 down to 0): row loops stop at step j's last row.
 #pragma unroll
@@ -439,15 +463,15 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, c
       const S* u = Rf + j * k;
       S d = (g == 0) ? cmadd(zero<S>(), vt, et) : zero<S>();
 #pragma unroll
-      for (int q = 0; q <= j / kTreeRG; ++q) {
-        const int r = g + kTreeRG * q;
+      for (int q = 0; q <= j / RG; ++q) {
+        const int r = g + RG * q;
         if (r <= j) d = cmadd(d, u[r], eb[q]);
       }
-      d = scale(tree_sum4(d, m4), b);
+      d = scale(tree_sum<RG>(d, m4), b);
       et = msub(et, vt, d);
 #pragma unroll
-      for (int q = 0; q <= j / kTreeRG; ++q) {
-        const int r = g + kTreeRG * q;
+      for (int q = 0; q <= j / RG; ++q) {
+        const int r = g + RG * q;
         if (r <= j) eb[q] = msub(eb[q], u[r], d);
       }
     }
@@ -455,8 +479,8 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_down(const Inst* insts, c
     et = et_next;
   }
 #pragma unroll
-  for (int q = 0; q < kTreeRows; ++q) {
-    const int r = g + kTreeRG * q;
+  for (int q = 0; q < RW; ++q) {
+    const int r = g + RG * q;
     if (r < k) Fb[r + c * k] = eb[q];
   }
 }

@@ -878,6 +878,19 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
     const int64_t lo = leaf_lo(I, lb);
     const int rb = (int)(leaf_lo(I, lb + 1) - lo);
     const S* Fb = Fg + (I.lev_off[0] + lb) * (int64_t)kk;
+    if (lb + 1 < b_end) {
+      // The next leaf's rows of Q (its Y, or its leaf Q) and its F_b are
+      // requested into L2 now, one 128-byte line per thread, so that its
+      // loads below find them there.
+      const int64_t lo1 = leaf_lo(I, lb + 1);
+      const int rb1 = (int)(leaf_lo(I, lb + 2) - lo1);
+      constexpr int EPL = 128 / sizeof(S);  // elements per line
+      const int lpc = (rb1 + EPL - 1) / EPL;
+      for (int t = threadIdx.x; t < lpc * k; t += kEmuThreads)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(Qg + lo1 + (t % lpc) * EPL + (int64_t)(t / lpc) * ldq));
+      for (int t = threadIdx.x; t * EPL < kk; t += kEmuThreads)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(Fb + kk + t * EPL));
+    }
     __syncthreads();  // the previous leaf is done with every buffer
     // Loads in groups of 8 per thread ahead of their stores: one memory round
     // trip per group instead of one per element (in-order issue would make

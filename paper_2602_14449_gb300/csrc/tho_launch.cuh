@@ -148,9 +148,7 @@ cudaError_t configure_impl(PlanCore& pc) {
   if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
   pc.smem_leaf_emu = leaf_emu_smem(pc.P, pc.kpmax, sizeof(S));
   if (EMU && (e = raise((const void*)k_leaf_emu<S>, pc.smem_leaf_emu)) != cudaSuccess) return e;
-  if ((e = raise((const void*)k_tree_down<S, 4>, pc.smem_tree)) != cudaSuccess) return e;
-  if ((e = raise((const void*)k_tree_down<S, 8>, pc.smem_tree)) != cudaSuccess) return e;
-  if ((e = raise((const void*)k_tree_down<S, 32>, pc.smem_tree)) != cudaSuccess) return e;
+  if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_up_p<S>, tree_up_p_smem(kTreeUpG, pc.kmax, sizeof(S)))) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down_w<S>, pc.smem_tree)) != cudaSuccess) return e;
   // Count the launches one call issues (same order as run_impl).
@@ -240,12 +238,8 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     if (G >= 4)
       k_tree_up_p<S><<<(nl + G - 1) / G, tree_up_p_threads(G, pc.kmax), tree_up_p_smem(G, pc.kmax, sizeof(S)),
                        st>>>(insts, items + pc.tab.lev_off[l], nl, ws, l, G, pc.kmax);
-    else if (nl >= 2 * pc.sms)
-      k_tree_up<S, 4><<<nl, kMaxKP * 4, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
-    else if (nl >= pc.sms / 2)
-      k_tree_up<S, 8><<<nl, kMaxKP * 8, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
-    else  // the levels near the root: a warp per column, the shortest chains
-      k_tree_up<S, 32><<<nl, kMaxKP * 32, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
+    else
+      k_tree_up<S><<<nl, kTreeThreads, 0, st>>>(insts, items + pc.tab.lev_off[l], ws, l);
   }
   hk(kPhTreeUp, 1, st);
   hk(kPhRoot, 0, st);
@@ -256,16 +250,13 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     const int nl = pc.tab.lev_n[l];
     const WorkItem* li = items + pc.tab.lev_off[l];
     if (nl <= 0) continue;
-    // Widest levels: a warp per node; then four, eight and (near the root,
-    // where one node's chain is the whole level's time) 32 row groups per column.
+    // Widest levels: a warp per node; the others four row groups per column
+    // (more row groups cost more FP64 warp instructions per node, and the FP64
+    // pipe, charged per warp instruction, bounds even the narrow levels).
     if (nl >= kTreeDownWide * pc.sms)
       k_tree_down_w<S><<<nl, 32, pc.smem_tree, st>>>(insts, li, ws, l);
-    else if (nl >= 2 * pc.sms)
-      k_tree_down<S, 4><<<nl, kMaxKP * 4, pc.smem_tree, st>>>(insts, li, ws, l);
-    else if (nl >= pc.sms / 2)
-      k_tree_down<S, 8><<<nl, kMaxKP * 8, pc.smem_tree, st>>>(insts, li, ws, l);
     else
-      k_tree_down<S, 32><<<nl, kMaxKP * 32, pc.smem_tree, st>>>(insts, li, ws, l);
+      k_tree_down<S><<<nl, kTreeThreads, pc.smem_tree, st>>>(insts, li, ws, l);
   }
   hk(kPhTreeDown, 1, st);
   hk(kPhApply, 0, st);

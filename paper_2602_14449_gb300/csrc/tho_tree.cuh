@@ -21,7 +21,8 @@ constexpr int kTreeThreads = kMaxKP * kTreeRG;  // 128
 
 __device__ __forceinline__ unsigned tree_mask4() { return 0xFu << (threadIdx.x & 28u); }
 
-// Lanes of one column's row groups (RG adjacent lanes, RG a power of two <= 32).
+// Lanes of one column's row groups (RG adjacent lanes, RG a power of two <= 32;
+// the launches use RG = kTreeRG).
 template <int RG>
 __device__ __forceinline__ unsigned tree_mask() {
   if constexpr (RG == 32) return 0xffffffffu;

@@ -172,12 +172,12 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
     int m = 0;
     int64_t q = r_begin * RPE + lane;
     const int64_t qe = r_end * RPE;
-    for (; q + 7 * 32 < qe; q += 8 * 32) {  // eight loads in flight per lane
-      double v[8];
+    for (; q + 15 * 32 < qe; q += 16 * 32) {  // sixteen loads in flight per lane
+      double v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = src[q + 32 * u];
+      for (int u = 0; u < 16; ++u) v[u] = src[q + 32 * u];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) m = max(m, dexp(v[u]));
+      for (int u = 0; u < 16; ++u) m = max(m, dexp(v[u]));
     }
     for (; q < qe; q += 32) m = max(m, dexp(src[q]));
     m = __reduce_max_sync(0xffffffffu, m);
@@ -349,6 +349,29 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
           }
         }
       }
+      // The stage's raw values are loaded before waiting for its buffer (the
+      // loads do not touch shared memory), so their latency overlaps the wait.
+      double xv[2 * kUmmaPairs];
+      if (!loader) {
+        const int64_t r0 = r_begin + (int64_t)t * TR;
+        const int nq = (int)min64(TR, r_end - r0) * RPE;
+#pragma unroll
+        for (int u = 0; u < kUmmaPairs; ++u) {
+          const int e2 = threadIdx.x - pbase + u * nprod;
+          const bool isA = e2 < npA;
+          const int f = isA ? e2 : e2 - npA;
+          const int g32 = f >> 5, l = f & 31;
+          const int kp = (g32 & 3) * 4 + (l >> 3), row = (g32 >> 2) * 8 + (l & 7), q = 2 * kp;
+          double x0 = 0.0, x1 = 0.0;
+          if (e2 < npA + npB && row < (isA ? k0 : k)) {
+            const double* src = isA ? Vd + (int64_t)row * ldv + r0 * RPE : Ad + (int64_t)row * lda + r0 * RPE;
+            if (q < nq) x0 = src[q];
+            if (q + 1 < nq) x1 = src[q + 1];
+          }
+          xv[2 * u] = x0;
+          xv[2 * u + 1] = x1;
+        }
+      }
       if (t >= 2 && !mbar_wait(b_empty + 8 * s, ((t >> 1) - 1) & 1)) {
         *abort_flag = 1;
         break;
@@ -362,27 +385,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
         __syncwarp();
         if (t >= 1 && group_end(t - 1)) fold((t - 1) / kUmmaGroup);
         continue;
-      }
-      const int64_t r0 = r_begin + (int64_t)t * TR;
-      const int nq = (int)min64(TR, r_end - r0) * RPE;
-      // All of this thread's loads first (one memory round trip per stage),
-      // then the splitting.
-      double xv[2 * kUmmaPairs];
-#pragma unroll
-      for (int u = 0; u < kUmmaPairs; ++u) {
-        const int e2 = threadIdx.x - pbase + u * nprod;
-        const bool isA = e2 < npA;
-        const int f = isA ? e2 : e2 - npA;
-        const int g32 = f >> 5, l = f & 31;
-        const int kp = (g32 & 3) * 4 + (l >> 3), row = (g32 >> 2) * 8 + (l & 7), q = 2 * kp;
-        double x0 = 0.0, x1 = 0.0;
-        if (e2 < npA + npB && row < (isA ? k0 : k)) {
-          const double* src = isA ? Vd + (int64_t)row * ldv + r0 * RPE : Ad + (int64_t)row * lda + r0 * RPE;
-          if (q < nq) x0 = src[q];
-          if (q + 1 < nq) x1 = src[q + 1];
-        }
-        xv[2 * u] = x0;
-        xv[2 * u + 1] = x1;
       }
 #pragma unroll
       for (int u = 0; u < kUmmaPairs; ++u) {

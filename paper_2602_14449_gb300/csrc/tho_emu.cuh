@@ -1421,8 +1421,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
       }
       if (mine) {
         emu_fold(acc, hi, lo4);
-#pragma unroll
         double* gw = reinterpret_cast<double*>(wsp<S>(ws, I.oGw) + (int64_t)it.idx * k * k);
+#pragma unroll
         for (int e = 0; e < 2; ++e) {  // rows g (< 8) of the 16-row tile
           const int l = g, j = jb0 + 2 * t4 + e, i = j - kpc, pi = j - kpc - kNB;
           if (l >= jb) continue;

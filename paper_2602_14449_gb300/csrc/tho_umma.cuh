@@ -28,7 +28,6 @@ constexpr int kUmmaThreads = 512;  // warp 0 issues the MMAs; warps 1..15 split;
 constexpr int kUmmaStages = 2;
 constexpr int kUmmaM = 128;        // MMA rows: the (padded) columns of V
 constexpr int kUmmaGroup = 4;      // stages per fold (4 x 32 = 128 steps)
-constexpr int kUmmaAhead = 4;      // stages whose raw lines the Gram producers request into L2 ahead
 constexpr int kUmmaSpins = 1 << 25;
 // Value pairs per producer thread per stage: (128 + 32) rows x 16 pairs over 480 threads.
 constexpr int kUmmaPairs = ((kUmmaM + 32) * (kUmmaKT / 2) + kUmmaThreads - 33) / (kUmmaThreads - 32);
@@ -330,25 +329,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
     const bool loader = which && warp == 1;
     const int pbase = which ? 64 : 32, nprod = kUmmaThreads - pbase;
     const int npA = which ? 0 : kUmmaM * (kUmmaKT / 2), npB = (C ? kpe : N) * (kUmmaKT / 2);
-    // The lines of the stage kUmmaAhead stages on (two 128-byte lines per
-    // column of V and X) are requested into L2 while this one is split
-    // (prefetch.global.L2 holds no registers), so each stage's loads find
-    // their data in L2 rather than waiting on HBM.
-    const int ncolx = (which ? 0 : k0) + k;
     for (int t = 0; t < ntile && !*abort_flag; ++t) {
       const int s = t & 1;
-      if (!loader && t + kUmmaAhead < ntile) {
-        const int64_t rp = (r_begin + (int64_t)(t + kUmmaAhead) * TR) * RPE;
-        const int64_t re = r_end * RPE;
-        for (int idx = threadIdx.x - pbase; idx < 2 * ncolx; idx += nprod) {
-          const int col = (which ? k0 : 0) + (idx >> 1);
-          const int64_t q = rp + (idx & 1) * 16;
-          if (q < re) {
-            const double* src = col < k0 ? Vd + (int64_t)col * ldv + q : Ad + (int64_t)(col - k0) * lda + q;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
-          }
-        }
-      }
       // The stage's raw values are loaded before waiting for its buffer (the
       // loads do not touch shared memory), so their latency overlaps the wait.
       double xv[2 * kUmmaPairs];

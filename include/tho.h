@@ -70,8 +70,10 @@ typedef enum {
                             * out (results invalid); latched like NONFINITE        */
   THO_ERR_NONFINITE = 7,   /* device check found NaN/Inf (THO_FLAG_CHECK_FINITE)   */
   THO_ERR_UNSUPPORTED = 8, /* shape or mode beyond what the library implements    */
-  THO_ERR_NOCONV = 9       /* the polar iteration of THO_FLAG_P_POLAR did not     *
+  THO_ERR_NOCONV = 9,      /* the polar iteration of THO_FLAG_P_POLAR did not     *
                             * converge (V_{1:k0,:} numerically singular); latched  */
+  THO_ERR_NOT_ORTH = 10    /* THO_FLAG_CHECK_ORTH: the estimate of ||V^*V - I||_2  *
+                            * exceeds THO_ORTH_TOL; latched, results computed     */
 } tho_status_t;
 
 typedef enum { THO_F64 = 0, THO_C128 = 1 } tho_dtype_t;
@@ -111,6 +113,23 @@ typedef enum { THO_PREC_FP64 = 0, THO_PREC_FP32_BULK = 1, THO_PREC_FP64_EMU = 2 
  * THO_FLAG_P_MLU; not for tho_orth_backward. */
 #define THO_FLAG_P_POLAR 0x8u
 #define THO_POLAR_MAX_ITERATIONS 100
+/* The check of the precondition of Theorem 4 (Section 4): every bound of the
+ * theorem grows with delta_1 = ||V^* V - I||_2 (the loss of orthogonality of Q
+ * by about delta_1 kappa_2(T)), and V's orthonormality is the caller's
+ * precondition.  With this flag each tho_orth / tho_orth_host call also
+ * estimates delta_1 on the device, after the orthogonalization on the same
+ * stream: two steps of the power iteration x <- E x / ||E x|| on
+ * E = V^* V - I from a fixed pseudo-random start, each one FP64 sweep over the
+ * n rows of V (2 n k0 multiply-adds), the estimate being the largest
+ * ||E x|| / ||x|| seen.  That is a lower bound of delta_1 up to rounding (exact
+ * for a defect of rank one).  An estimate above THO_ORTH_TOL latches
+ * THO_ERR_NOT_ORTH (read with tho_plan_status); Q, R and S are computed either
+ * way.  tho_plan_orth_defect reads the last estimate.  For tho_orth_b the
+ * check applies to D^{1/2} V (orthonormality in the B-inner product).  Single
+ * problem plans only (THO_ERR_UNSUPPORTED for count > 1); without k0 there is
+ * nothing to check.  Not accepted by tho_orth_noalloc. */
+#define THO_FLAG_CHECK_ORTH 0x10u
+#define THO_ORTH_TOL 1e-12
 
 /* One orthogonalization problem: V is n x k0, A is n x k. */
 typedef struct {
@@ -377,9 +396,17 @@ tho_status_t tho_orth_noalloc(const tho_desc_t* desc, const void* V, int64_t ldv
                               int64_t lda, void* Q, int64_t ldq, void* R, void* S, void* stream);
 
 /* Read and clear the plan's device status word (synchronizes the device).
- * Returns THO_OK or the device-detected error (THO_ERR_NONFINITE, or
- * THO_ERR_TIMEOUT from a tcgen05 kernel whose bounded wait ran out). */
+ * Returns THO_OK or the device-detected error (THO_ERR_NONFINITE, THO_ERR_NOCONV,
+ * THO_ERR_NOT_ORTH, or THO_ERR_TIMEOUT from a tcgen05 kernel whose bounded wait
+ * ran out). */
 tho_status_t tho_plan_status(tho_plan_t plan);
+
+/* The last estimate of delta_1 = ||V^* V - I||_2 made by a plan created with
+ * THO_FLAG_CHECK_ORTH (Theorem 4, Section 4; see that flag), written to
+ * *delta after the device is synchronized; 0 before the first call and for
+ * k0 = 0, +Inf if V held NaN/Inf.  THO_ERR_ARG for a plan without the flag or
+ * a NULL pointer, THO_ERR_CUDA if the read fails. */
+tho_status_t tho_plan_orth_defect(tho_plan_t plan, double* delta);
 
 /* Test hook for the device-side failure path (no counterpart in the paper).
  * The tcgen05 kernels hand shared-memory stages between warps through

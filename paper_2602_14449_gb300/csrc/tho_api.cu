@@ -13,6 +13,7 @@
 #include "tho.h"
 #include "tho_backward.h"
 #include "tho_binner.cuh"
+#include "tho_check.cuh"
 #include "tho_launch.h"
 
 using tho::Inst;
@@ -48,6 +49,10 @@ struct tho_plan_s {
   // Algorithm 4 with a diagonal B (allocated on the first tho_orth_b call):
   // D^{1/2} V (n x k0), D^{1/2} A (n x k), sqrt(d) and 1 / sqrt(d) (n each).
   void* bi_buf = nullptr;
+  // THO_FLAG_CHECK_ORTH: x (k0), the sweep's partial sums (orth_g x k0) and
+  // the estimates (kOrthIters + 1 doubles).
+  void* orth_buf = nullptr;
+  int orth_g = 0;
   int32_t split_chunks = 0;  // split-n factor the partition was built with
   int32_t balance = 0;       // chunks shared by rows (0) or by streaming work (1)
 };
@@ -69,7 +74,8 @@ tho_status_t check_desc(const tho_desc_t& d, const tho_desc_t& d0) {
   if (d.dtype != d0.dtype || d.prec != d0.prec || d.flags != d0.flags) return THO_ERR_ARG;
   if (d.dtype != THO_F64 && d.dtype != THO_C128) return THO_ERR_ARG;
   if (d.prec != THO_PREC_FP64 && d.prec != THO_PREC_FP32_BULK && d.prec != THO_PREC_FP64_EMU) return THO_ERR_ARG;
-  if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE | THO_FLAG_P_MLU | THO_FLAG_P_POLAR))
+  if (d.flags & ~(THO_FLAG_ALLOW_K0_ZERO | THO_FLAG_CHECK_FINITE | THO_FLAG_P_MLU | THO_FLAG_P_POLAR |
+                  THO_FLAG_CHECK_ORTH))
     return THO_ERR_ARG;
   if ((d.flags & THO_FLAG_P_MLU) && (d.flags & THO_FLAG_P_POLAR)) return THO_ERR_ARG;
   if (d.k < 1 || d.k0 < 0 || d.n < 1) return THO_ERR_SHAPE;
@@ -97,6 +103,7 @@ void free_plan(tho_plan_s* p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->bi_buf) cudaFree(p->bi_buf);
+  if (p->orth_buf) cudaFree(p->orth_buf);
   if (p->pc.side) cudaStreamDestroy(p->pc.side);
   if (p->pc.ev_fork) cudaEventDestroy(p->pc.ev_fork);
   if (p->pc.ev_join) cudaEventDestroy(p->pc.ev_join);
@@ -137,6 +144,30 @@ void phase_hook(void* ctx, int phase, int end, cudaStream_t st) {
     cudaEventRecord(p->ev[2 * p->ev_used + 1], st);
     ++p->ev_used;
   }
+}
+
+// THO_FLAG_CHECK_ORTH: the estimate of ||V^* V - I||_2 on stream st (after the
+// orthogonalization's own launches); nothing to do without k0.
+template <class S>
+cudaError_t orth_check_impl(tho_plan_s* p, const S* V, int64_t ldv, cudaStream_t st) {
+  const Inst& I = p->pc.h_insts[0];
+  const int k0 = (int)I.k0;
+  S* x = static_cast<S*>(p->orth_buf);
+  S* zpart = x + k0;
+  double* est = reinterpret_cast<double*>(zpart + (size_t)p->orth_g * k0);
+  tho::k_orth_init<S><<<1, tho::kOrthThreads, 0, st>>>(x, est, k0);
+  const size_t smem = tho::orth_sweep_smem(k0, sizeof(S));
+  for (int it = 0; it < tho::kOrthIters; ++it) {
+    tho::k_orth_sweep<S><<<p->orth_g, tho::kOrthThreads, smem, st>>>(V, ldv, I.n, k0, x, zpart);
+    tho::k_orth_finish<S><<<1, tho::kOrthThreads, 0, st>>>(zpart, p->orth_g, k0, x, est, it, THO_ORTH_TOL,
+                                                            p->pc.d_status);
+  }
+  return cudaGetLastError();
+}
+cudaError_t orth_check(tho_plan_s* p, const void* V, int64_t ldv, cudaStream_t st) {
+  if (!(p->pc.flags & THO_FLAG_CHECK_ORTH) || !p->orth_buf) return cudaSuccess;
+  return p->pc.dtype == THO_C128 ? orth_check_impl(p, static_cast<const tho::z64*>(V), ldv, st)
+                                 : orth_check_impl(p, static_cast<const double*>(V), ldv, st);
 }
 
 
@@ -187,6 +218,7 @@ const char* tho_status_string(tho_status_t s) {
     case THO_ERR_NONFINITE: return "non-finite value detected on the device";
     case THO_ERR_UNSUPPORTED: return "shape or mode not supported by the library";
     case THO_ERR_NOCONV: return "polar iteration did not converge (V_{1:k0,:} numerically singular)";
+    case THO_ERR_NOT_ORTH: return "V's columns are not orthonormal (estimate of ||V^* V - I||_2 above THO_ORTH_TOL)";
   }
   return "unknown status";
 }
@@ -209,6 +241,7 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
   if (t_leaf != 0 && t_leaf != 64 && t_leaf != 128 && t_leaf != 256) return THO_ERR_ARG;
   if (t_split < 0 || t_split > THO_TUNE_MAX_SPLIT) return THO_ERR_ARG;
   if (t_balance != 0 && t_balance != 1) return THO_ERR_ARG;
+  if ((descs[0].flags & THO_FLAG_CHECK_ORTH) && count != 1) return THO_ERR_UNSUPPORTED;
   tho_plan_s* p = new (std::nothrow) tho_plan_s();
   if (!p) return THO_ERR_NOMEM;
   PlanCore& pc = p->pc;
@@ -422,6 +455,25 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
     free_plan(p);
     return THO_ERR_CUDA;
   }
+  if ((pc.flags & THO_FLAG_CHECK_ORTH) && pc.any_k0) {
+    const size_t el = p->L->elem;
+    const int k0 = (int)pc.h_insts[0].k0;
+    p->orth_g = 2 * std::max(1, pc.sms);
+    const size_t bytes = el * (size_t)k0 * (1 + (size_t)p->orth_g) + sizeof(double) * (tho::kOrthIters + 1);
+    if (cudaMalloc(&p->orth_buf, bytes) != cudaSuccess) {
+      p->orth_buf = nullptr;
+      cudaGetLastError();
+      free_plan(p);
+      return THO_ERR_NOMEM;
+    }
+    const void* fn = cplx ? (const void*)tho::k_orth_sweep<tho::z64> : (const void*)tho::k_orth_sweep<double>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tho::orth_sweep_smem(k0, el)) !=
+        cudaSuccess) {
+      free_plan(p);
+      return THO_ERR_CUDA;
+    }
+    pc.launches += 1 + 2 * tho::kOrthIters;
+  }
   if (env_on("THO_LOG")) {
     const bool emu = pc.prec == THO_PREC_FP64_EMU;
     std::fprintf(stderr,
@@ -486,6 +538,7 @@ tho_status_t tho_orth(tho_plan_t plan, const void* V, int64_t ldv, const void* A
   }
   if (plan->L->run(plan->pc, nullptr, io0, reinterpret_cast<cudaStream_t>(stream), hook) != cudaSuccess)
     return THO_ERR_CUDA;
+  if (orth_check(plan, V, ldv, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return THO_ERR_CUDA;
   return THO_OK;
 }
 
@@ -635,6 +688,8 @@ tho_status_t tho_orth_b(tho_plan_t plan, const double* d, const void* V, int64_t
     hook.ctx = plan;
   }
   if (plan->L->run(plan->pc, nullptr, io0, st, hook) != cudaSuccess) return THO_ERR_CUDA;
+  // The check of Theorem 4's precondition applies to D^{1/2} V (V^* B V = I).
+  if (k0 > 0 && orth_check(plan, Vs, n, st) != cudaSuccess) return THO_ERR_CUDA;
   // Q = D^{-1/2} Q~ in place.
   if (plan->pc.dtype == THO_C128)
     tho::k_bscale_rows<tho::z64><<<grid, 256, 0, st>>>(isd, static_cast<const tho::z64*>(Q), ldq,
@@ -718,6 +773,22 @@ tho_status_t tho_plan_expire_wait(tho_plan_t plan, int32_t spins, void* stream) 
   return tho::launch_expire_wait(plan->pc.d_status, spins, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
              ? THO_OK
              : THO_ERR_CUDA;
+}
+
+tho_status_t tho_plan_orth_defect(tho_plan_t plan, double* delta) {
+  if (!plan || !delta || !(plan->pc.flags & THO_FLAG_CHECK_ORTH)) return THO_ERR_ARG;
+  if (!plan->orth_buf) {  // k0 = 0: no V to check
+    *delta = 0.0;
+    return THO_OK;
+  }
+  const size_t el = plan->L->elem;
+  const int64_t k0 = plan->pc.h_insts[0].k0;
+  const char* est = static_cast<const char*>(plan->orth_buf) + el * (size_t)k0 * (1 + (size_t)plan->orth_g);
+  if (cudaDeviceSynchronize() != cudaSuccess) return THO_ERR_CUDA;
+  if (cudaMemcpy(delta, est + sizeof(double) * tho::kOrthIters, sizeof(double), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return THO_ERR_CUDA;
+  return THO_OK;
 }
 
 tho_status_t tho_plan_status(tho_plan_t plan) {

@@ -22,9 +22,12 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtho.so")
 
 THO_OK, THO_ERR_ARG, THO_ERR_SHAPE, THO_ERR_ALIGN, THO_ERR_NOMEM = 0, 1, 2, 3, 4
 THO_ERR_CUDA, THO_ERR_TIMEOUT, THO_ERR_NONFINITE, THO_ERR_UNSUPPORTED, THO_ERR_NOCONV = 5, 6, 7, 8, 9
+THO_ERR_NOT_ORTH = 10
 THO_F64, THO_C128 = 0, 1
 THO_PREC_FP64, THO_PREC_FP32_BULK, THO_PREC_FP64_EMU = 0, 1, 2
 THO_FLAG_ALLOW_K0_ZERO, THO_FLAG_CHECK_FINITE, THO_FLAG_P_MLU, THO_FLAG_P_POLAR = 0x1, 0x2, 0x4, 0x8
+THO_FLAG_CHECK_ORTH = 0x10
+THO_ORTH_TOL = 1e-12
 THO_MAX_K0, THO_MAX_K = 128, 32
 THO_TUNE_MAX_SPLIT = 1 << 20
 
@@ -34,7 +37,8 @@ EXPORTED = ("tho_plan", "tho_plan_destroy", "tho_plan_workspace_bytes", "tho_pla
             "tho_orth", "tho_orth_batched", "tho_orth_backward", "tho_plan_status", "tho_status_string",
             "tho_plan_set_phase_timing", "tho_plan_read_phase_timing", "tho_phase_name",
             "tho_orth_noalloc", "tho_plan_tuned", "tho_plan_tuning", "tho_autotune", "tho_tune_key",
-            "tho_tune_cache_get", "tho_tune_cache_put", "tho_plan_expire_wait", "tho_orth_b")
+            "tho_tune_cache_get", "tho_tune_cache_put", "tho_plan_expire_wait", "tho_orth_b",
+            "tho_plan_orth_defect")
 THO_NUM_PHASES = 11
 
 
@@ -128,6 +132,8 @@ def load(path: str | None = None):
         lib.tho_plan_expire_wait.restype = ctypes.c_int
         lib.tho_plan_status.argtypes = [vp]
         lib.tho_plan_status.restype = ctypes.c_int
+        lib.tho_plan_orth_defect.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.tho_plan_orth_defect.restype = ctypes.c_int
         lib.tho_status_string.argtypes = [ctypes.c_int]
         lib.tho_status_string.restype = ctypes.c_char_p
         lib.tho_plan_set_phase_timing.argtypes = [vp, i32]
@@ -268,6 +274,13 @@ class Plan:
 
     def status(self) -> int:
         return load().tho_plan_status(self.handle)
+
+    def orth_defect(self) -> float:
+        """tho_plan_orth_defect: the last estimate of ||V^* V - I||_2 of a plan
+        made with THO_FLAG_CHECK_ORTH (synchronizes the device)."""
+        d = ctypes.c_double(0.0)
+        _check(load().tho_plan_orth_defect(self.handle, ctypes.byref(d)), "tho_plan_orth_defect")
+        return d.value
 
     def expire_wait(self, spins: int = 4096):
         """tho_plan_expire_wait: on the current stream, a bounded device wait that

@@ -70,7 +70,7 @@ def test_shape_and_argument_errors(lib):
 
 
 def test_status_strings(lib):
-    for code in range(10):
+    for code in range(11):
         s = lib.tho_status_string(code).decode()
         assert s and s != "unknown status"
     assert lib.tho_status_string(99).decode() == "unknown status"

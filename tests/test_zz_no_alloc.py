@@ -130,3 +130,5 @@ def test_noalloc_rejects_problems_beyond_the_scratch(lib):
     assert f(ctypes.byref(bad), 256, 100, 256, 100, 256, 100, None, None, None) == tho.THO_ERR_SHAPE
     emu = tho.Desc(1000, 8, 4, tho.THO_F64, tho.THO_PREC_FP64_EMU, 0)
     assert f(ctypes.byref(emu), 256, 1000, 256, 1000, 256, 1000, None, None, None) == tho.THO_ERR_ARG
+    chk = tho.Desc(1000, 8, 4, tho.THO_F64, tho.THO_PREC_FP64, tho.THO_FLAG_CHECK_ORTH)
+    assert f(ctypes.byref(chk), 256, 1000, 256, 1000, 256, 1000, None, None, None) == tho.THO_ERR_ARG

@@ -813,315 +813,306 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
   }
 }
 
-// a8 (sweep 3a), emulated: for each leaf b of a chunk, Qbar_b = Q_leaf,b F_b in
-// place in the rows of Q, with the product on bf16 tensor cores.  The leaf's Q
-// factor is staged in shared memory (row-major, padded rows); its column scales
-// 2^(e_i - 1078) (maximal exponent of column i over the leaf) are moved exactly
-// into the second operand, F'(q, j) = 2^(e_i - 1078) B(q, j) with B the real
-// embedding of F_b used by the rank-k0 update, which is sliced per column j.
-// The contraction (k columns, real-embedded) is at most 64 steps: one fold.
-// Shared: Qr [P][k+1] S | Fr [k][k] S | Zs [8][kpe][kEmuLd] | Vs [8][max(TM, k16)][kEmuLd] bf16 | eV | eZ.
-//
-// wy != 0 (bit 0): Q's rows hold the leaf's Householder vectors Y (v_j on the
-// diagonal, zero above) and the workspace its betas, instead of the explicit
-// leaf Q.  With T the upper triangular factor of H_0 ... H_{k-1} = I - Y T Y^*,
+// a8 (sweep 3a), emulated, compact WY form: for each leaf b of a chunk,
+// Qbar_b = Q_leaf,b [F_b; 0] in place in the rows of Q, which hold the leaf's
+// Householder vectors Y (v_j on the diagonal, zero above) while the workspace
+// holds its betas.  With T the upper triangular factor of
+// H_0 ... H_{k-1} = I - Y T Y^*,
 //   Qbar_b = [F_b; 0] - Y (K F_b),   K = T Y_1^*,   Y_1 = rows 0..k-1 of Y,
-// formed per leaf as: G' = (Y^* Y) diag(beta) on tensor cores, or read from
-// the workspace when the leaf kernel wrote it (bit 1); K by back substitution
-// with T^-1 = diag(1/beta) + (strictly upper part of Y^* Y), which holds for
-// the forward product of the reflectors (Puglisi); M = K F_b on tensor cores;
-// then the product above with F_b replaced by -M and [F_b; 0] added in the
-// epilogue.
-// Extra shared memory with wy: Gs (G'), Ts (betas, row scales of K), Ms [k][k+1] S after Fr.
-template <class S, int MTM>
-__global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
-                                                              const WorkItem* items, void* ws, int P, int wy) {
+// formed per leaf as: G' = (Y^* Y) diag(beta) on tensor cores, or read from the
+// workspace when the leaf kernel wrote it (gpre); K by back substitution with
+// T^-1 = diag(1/beta) + (strictly upper part of Y^* Y), which holds for the
+// forward product of the reflectors (Puglisi); M = K F_b on tensor cores; then
+// Y (-M) on tensor cores with Y's column scales 2^(e_i - 1078) moved exactly
+// into -M (sliced per column j), and [F_b; 0] added in the epilogue.
+// Y and F_b are read from global memory (L2: the next leaf's lines are
+// requested while this one is processed), so a CTA holds only G', M, the
+// scales and two slice buffers, and two CTAs of eight warps share an SM: the
+// barrier-bound steps of one leaf (the back substitution) overlap the
+// tensor-core and memory work of the other.
+// Shared: Gs, Ms [k][k+1] S | betas | eK, eV, eZ | Zs [8][kpe][kEmuLd] |
+// Vs [8][kApplyTM][kEmuLd] bf16 (a row tile of Y, or K, or a chunk of Y^T).
+constexpr int kApplyThreads = 256;  // 8 warps; two CTAs share an SM
+constexpr int kApplyTM = 32;        // rows per row tile (two 16-row MMA tiles; also k rounded up to 16)
+
+__host__ __device__ inline size_t apply_emu_smem(int k, size_t elem) {
+  const size_t kk2 = ((size_t)k * (k + 1) + 1) / 2 * 2;
+  const size_t kpe = ((size_t)k + 7) / 8 * 8;
+  return 2 * kk2 * elem + kMaxKP * (sizeof(double) + 3 * sizeof(int)) +
+         (size_t)kEmuSlices * kEmuLd * 2 * (kpe + kApplyTM);
+}
+
+template <class S>
+__global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
+                                                                const WorkItem* items, void* ws, int gpre) {
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
-  constexpr int NW = kEmuThreads / 32;
+  constexpr int NW = kApplyThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
   const Io io = get_io(iot, io0, it.inst);
-  const bool gpre = (wy & 2) != 0;  // G' = (Y^* Y) diag(beta) written by the leaf kernel
-  const int k = (int)I.k, kk = k * k, ldr = k + 1;
+  const int k = (int)I.k, kk = k * k;
   const int kpe = (k + 7) / 8 * 8;
-  const int NT = (C ? 2 * kpe : kpe) / 8;
-  const int MTt = max(1, min(MTM, NW / NT));
-  const int TM = 16 * MTt;
+  const int NT = (C ? 2 * kpe : kpe) / 8;  // 8-column output tiles (complex: Re outputs, then Im)
   const int kz = RPE * k, kzp = (kz + 15) / 16 * 16;
-  const int ldf = k + 1;  // F_b, M: column-major, padded (conflict-free lane-parallel rows)
+  const int kr = (k + 15) / 16 * 16;  // rows of K and of Y^T as MMA operands (<= kApplyTM)
+  const int ldf = k + 1;              // G', M: column-major, padded (conflict-free lane-parallel rows)
   const int kk2 = (k * ldf + 1) / 2 * 2;
-  S* Qr = reinterpret_cast<S*>(smem_raw);
-  S* Fr = Qr + ((size_t)P * ldr + 1) / 2 * 2;
-  S* Gs = Fr + kk2;
-  S* Ts = Gs + kk2;
-  S* Ms = Ts + kk2;
-  unsigned short* Zs = reinterpret_cast<unsigned short*>(Fr + (wy ? 4 : 1) * kk2);
+  S* Gs = reinterpret_cast<S*>(smem_raw);
+  S* Ms = Gs + kk2;
+  double* bs = reinterpret_cast<double*>(Ms + kk2);  // the leaf's betas
+  int* eK = reinterpret_cast<int*>(bs + kMaxKP);     // row scales of K
+  int* eV = eK + kMaxKP;                             // column scales of Y
+  int* eZ = eV + kMaxKP;                             // column scales of the second operand
+  unsigned short* Zs = reinterpret_cast<unsigned short*>(eZ + kMaxKP);
   unsigned short* Vs = Zs + kEmuSlices * kpe * kEmuLd;
-  // Vs holds one row tile (TM rows) or, with wy, the slices of Y^T (k rounded
-  // up to 16 rows).
-  const int vs_rows = max(TM, (k + 15) / 16 * 16);
-  int* eV = reinterpret_cast<int*>(Vs + kEmuSlices * vs_rows * kEmuLd);
-  int* eZ = eV + kMaxKP;
   S* Qg = reinterpret_cast<S*>(io.Q);
   const int64_t ldq = io.ldq;
   const S* Fg = wsp<S>(ws, I.oF);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
-  const bool mine = warp < MTt * NT;
-  const int mt = mine ? warp / NT : 0, nt = mine ? warp % NT : 0;
-  const bool imag = C && nt * 8 >= kpe;
-  const int jb0 = imag ? nt * 8 - kpe : nt * 8;
   const int b_begin = it.idx * I.leaves3;
   const int b_end = min(I.nb, b_begin + I.leaves3);
+  // Output tile `tile` of an MMA stage: 16-row tile mt, 8-column tile nt
+  // (complex: nt >= kpe / 8 are the Im outputs of columns nt * 8 - kpe..).
+  auto tile_of = [&](int tile, int& mt, bool& imag, int& jb0) {
+    mt = tile / NT;
+    const int nt = tile % NT;
+    imag = C && nt * 8 >= kpe;
+    jb0 = imag ? nt * 8 - kpe : nt * 8;
+  };
   for (int lb = b_begin; lb < b_end; ++lb) {
     const int64_t lo = leaf_lo(I, lb);
     const int rb = (int)(leaf_lo(I, lb + 1) - lo);
-    const S* Fb = Fg + (I.lev_off[0] + lb) * (int64_t)kk;
+    const S* Fb = Fg + (I.lev_off[0] + lb) * (int64_t)kk;  // column-major, ld k
+    const double* Yd = reinterpret_cast<const double*>(Qg + lo);  // column i at Yd + RPE i ldq
     if (lb + 1 < b_end) {
-      // The next leaf's rows of Q (its Y, or its leaf Q) and its F_b are
-      // requested into L2 now, one 128-byte line per thread, so that its
-      // loads below find them there.
+      // The next leaf's rows of Q (its Y) and its F_b are requested into L2
+      // now, one 128-byte line per thread, so that its reads find them there.
       const int64_t lo1 = leaf_lo(I, lb + 1);
       const int rb1 = (int)(leaf_lo(I, lb + 2) - lo1);
       constexpr int EPL = 128 / sizeof(S);  // elements per line
       const int lpc = (rb1 + EPL - 1) / EPL;
-      for (int t = threadIdx.x; t < lpc * k; t += kEmuThreads)
+      for (int t = threadIdx.x; t < lpc * k; t += kApplyThreads)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(Qg + lo1 + (t % lpc) * EPL + (int64_t)(t / lpc) * ldq));
-      for (int t = threadIdx.x; t * EPL < kk; t += kEmuThreads)
+      for (int t = threadIdx.x; t * EPL < kk; t += kApplyThreads)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(Fb + kk + t * EPL));
     }
     __syncthreads();  // the previous leaf is done with every buffer
-    // Loads in groups of 8 per thread ahead of their stores: one memory round
-    // trip per group instead of one per element (in-order issue would make
-    // each store wait for its load before the next load issues).
-    for (int e0 = threadIdx.x; e0 < k * rb; e0 += 8 * kEmuThreads) {
-      S v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * kEmuThreads;
-        v[u] = e < k * rb ? Qg[(lo + e % rb) + (int64_t)(e / rb) * ldq] : zero<S>();
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * kEmuThreads;
-        if (e < k * rb) Qr[(e % rb) * ldr + e / rb] = v[u];
-      }
-    }
-    for (int e0 = threadIdx.x; e0 < kk; e0 += 2 * kEmuThreads) {
-      const int e1 = e0 + kEmuThreads;
-      const S a = Fb[e0], b = e1 < kk ? Fb[e1] : zero<S>();
-      Fr[(e0 % k) + (e0 / k) * ldf] = a;
-      if (e1 < kk) Fr[(e1 % k) + (e1 / k) * ldf] = b;
-    }
-    __syncthreads();
+    // Column scales of Y over the leaf's rows; the betas.
     for (int i = warp; i < k; i += NW) {
       int m = 0;
-      for (int q = lane; q < rb * RPE; q += 32)
-        m = max(m, dexp(reinterpret_cast<const double*>(Qr + (q / RPE) * ldr + i)[q % RPE]));
+      const double* col = Yd + (int64_t)RPE * i * ldq;
+      for (int q = lane; q < rb * RPE; q += 32) m = max(m, dexp(col[q]));
       m = __reduce_max_sync(0xffffffffu, m);
       if (lane == 0) eV[i] = m;
     }
+    const S* btg = wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
+    for (int i = threadIdx.x; i < k; i += kApplyThreads) bs[i] = real_(btg[i]);
     __syncthreads();
-    if (wy) {
-      // (1) G' = (Y^* Y) diag(beta) over the leaf's rows, 64 real steps per
-      // chunk; Vs holds the slices of Y^T (rows = columns of Y), serving as
-      // both operands.  Only the strictly upper part is used: tiles wholly
-      // below the diagonal are skipped.
-      const int kr = (k + 15) / 16 * 16;
-      double* bs = reinterpret_cast<double*>(Ts);     // the leaf's betas
-      int* eK = reinterpret_cast<int*>(bs + k);       // row scales of K (Ts holds >= 12 k bytes)
-      const S* btg = wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
-      for (int i = threadIdx.x; i < k; i += kEmuThreads) bs[i] = real_(btg[i]);
-      const bool gmine = warp < (kr / 16) * NT;
-      const int gmt = gmine ? warp / NT : 0, gnt = gmine ? warp % NT : 0;
-      const bool gimag = C && gnt * 8 >= kpe;
-      const int gjb0 = gimag ? gnt * 8 - kpe : gnt * 8;
-      const bool gupper = gmine && gmt * 16 < gjb0 + 8;
+    // (1) G' = (Y^* Y) diag(beta), strictly upper part.
+    if (gpre) {
+      const S* gw = wsp<S>(ws, I.oGw) + (int64_t)lb * kk;
+      for (int e = threadIdx.x; e < kk; e += kApplyThreads)
+        if (e % k < e / k) Gs[(e % k) + (e / k) * ldf] = gw[e];
+    } else {
+      // On tensor cores over the leaf's rows, 64 real steps per chunk; Vs holds
+      // the slices of the chunk of Y^T (rows = columns of Y), serving as both
+      // operands.  One pass per 16-row tile of G and block of eight 8-column
+      // tiles (the chunk is sliced again), so that each warp keeps one
+      // accumulator set; tiles wholly below the diagonal are skipped.
+      const int nq = rb * RPE;
+      const int nblk = (NT + NW - 1) / NW;  // warps' passes over the 8-column tiles
+      for (int pass = 0; pass < (kr / 16) * nblk; ++pass) {
+        const int mt = pass / nblk, nt = (pass % nblk) * NW + warp;
+        const bool gimag = C && nt * 8 >= kpe;
+        const int gjb0 = gimag ? nt * 8 - kpe : nt * 8;
+        const bool gup = nt < NT && mt * 16 < gjb0 + 8;
+        float acc[kEmuLevels][4];
+        long long ghi[4] = {0, 0, 0, 0}, glo[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+        int chunk = 0;
+        for (int q0 = 0; q0 < nq; q0 += kEmuKT, ++chunk) {
+          __syncthreads();  // the previous chunk's MMAs are done with Vs
+          for (int e2 = threadIdx.x; e2 < kr * (kEmuKT / 2); e2 += kApplyThreads) {
+            const int l = e2 / (kEmuKT / 2), q = 2 * (e2 % (kEmuKT / 2)), qa = q0 + q;
+            double x0 = 0.0, x1 = 0.0;
+            if (l < k) {
+              const double* col = Yd + (int64_t)RPE * l * ldq;
+              if (qa < nq) x0 = col[qa];
+              if (qa + 1 < nq) x1 = col[qa + 1];
+            }
+            const int em = l < k ? eV[l] : 0;
+            unsigned w[kEmuSlices];
+            emu_split2(x0, x1, em, em, w);
+#pragma unroll
+            for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * kApplyTM + l) * kEmuLd + q) = w[p];
+          }
+          __syncthreads();
+          if (gup) {
+            for (int ks = 0; ks < kEmuKT; ks += 16) {
+              unsigned bf[kEmuSlices][2];
+#pragma unroll
+              for (int qq = 0; qq < kEmuSlices; qq += 2)
+                ld_bfrag2(Vs + (qq * kApplyTM) * kEmuLd, Vs + ((qq + 1) * kApplyTM) * kEmuLd, gjb0, ks, bf[qq],
+                          bf[qq + 1]);
+              if (gimag) {
+#pragma unroll
+                for (int qq = 0; qq < kEmuSlices; ++qq) {
+                  bf[qq][0] = im_pair(bf[qq][0]);
+                  bf[qq][1] = im_pair(bf[qq][1]);
+                }
+              }
+#pragma unroll
+              for (int p = 0; p < kEmuSlices; ++p) {
+                unsigned a[4];
+                ld_afrag(Vs + (p * kApplyTM) * kEmuLd, mt * 16, ks, a);
+#pragma unroll
+                for (int qq = 0; qq < kEmuSlices; ++qq) {
+                  if (p + qq > kEmuLevels - 1) continue;
+                  mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+                }
+              }
+            }
+            if (chunk & 1) emu_fold(acc, ghi, glo);  // exact for 128 steps
+          }
+        }
+        if (gup) {
+          emu_fold(acc, ghi, glo);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = mt * 16 + g + (e >= 2 ? 8 : 0);
+            const int j = gjb0 + 2 * t4 + (e & 1);
+            if (i >= j || j >= k) continue;
+            const int sc = eV[i] + eV[j] - 2044;
+            const double v = emu_fx((long long)ghi[e], (long long)glo[e], sc);
+            reinterpret_cast<double*>(Gs + i + j * ldf)[gimag ? 1 : 0] = v * bs[j];  // G(i, j) beta_j
+          }
+        }
+      }
+    }
+    // (2) K = T Y_1^* (upper triangular: T and Y_1^* are).  With T^-1 =
+    // diag(1/beta) + (strictly upper part of G) and K = diag(beta) U, G' as above:
+    //   U(i) = Y_1^*(i) - sum_{l > i} G'(i, l) U(l),
+    // right-looking: after step i + 1 row i is final and step i removes it
+    // from the rows above, in the columns j >= i where it is nonzero.
+    for (int e = threadIdx.x; e < kk; e += kApplyThreads) {
+      const int j = e % k, l = e / k;  // consecutive threads: consecutive rows j of Y's column l
+      Ms[l + j * ldf] = j >= l ? conj_(Qg[(lo + j) + (int64_t)l * ldq]) : zero<S>();  // Y_1^*(l, j) = conj(Y(j, l))
+    }
+    for (int j = warp; j < k; j += NW) {  // column scales of F_b
+      int m = 0;
+      const double* col = reinterpret_cast<const double*>(Fb + (int64_t)j * k);
+      for (int q = lane; q < k * RPE; q += 32) m = max(m, dexp(col[q]));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) eZ[j] = m;
+    }
+    __syncthreads();
+    for (int i = k - 1; i >= 1; --i) {
+      const int w = k - i;
+      for (int e = threadIdx.x; e < i * w; e += kApplyThreads) {
+        const int l = e / w, j = i + e % w;
+        Ms[l + j * ldf] = msub(Ms[l + j * ldf], Gs[l + i * ldf], Ms[i + j * ldf]);
+      }
+      __syncthreads();
+    }
+    // (3) M = K F_b on tensor cores, contraction over K's columns (one chunk:
+    // RPE k <= 64 steps).  The emulated product forms A^* B, so A holds
+    // conj(K) = conj(diag(beta) U) (row scales eK), B = F_b^T (eZ).
+    for (int l = warp; l < k; l += NW) {
+      int m = 0;
+      for (int q = lane; q < k * RPE; q += 32)
+        m = max(m, dexp(reinterpret_cast<const double*>(Ms + l + (q / RPE) * ldf)[q % RPE] * bs[l]));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) eK[l] = m;
+    }
+    __syncthreads();
+    for (int e2 = threadIdx.x; e2 < (kr + kpe) * (kEmuKT / 2); e2 += kApplyThreads) {
+      const bool isA = e2 < kr * (kEmuKT / 2);
+      const int f = isA ? e2 : e2 - kr * (kEmuKT / 2);
+      const int row = f / (kEmuKT / 2), q = 2 * (f % (kEmuKT / 2));
+      double x0 = 0.0, x1 = 0.0;
+      if (row < k) {
+        auto part = [&](int qq) -> double {
+          if (qq >= k * RPE) return 0.0;
+          if (isA) {
+            const double v = reinterpret_cast<const double*>(Ms + row + (qq / RPE) * ldf)[qq % RPE] * bs[row];
+            return (qq % RPE) ? -v : v;  // conj(K)
+          }
+          return reinterpret_cast<const double*>(Fb + (int64_t)row * k)[qq];  // F_b(qq / RPE, row), part qq % RPE
+        };
+        x0 = part(q);
+        x1 = part(q + 1);
+      }
+      const int em = row < k ? (isA ? eK[row] : eZ[row]) : 0;
+      unsigned w[kEmuSlices];
+      emu_split2(x0, x1, em, em, w);
+      unsigned short* dst = isA ? Vs + (row * kEmuLd + q) : Zs + (row * kEmuLd + q);
+      const int pst = (isA ? kApplyTM : kpe) * kEmuLd;
+#pragma unroll
+      for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(dst + p * pst) = w[p];
+    }
+    __syncthreads();
+    const int kzf = (k * RPE + 15) / 16 * 16;
+    for (int tile = warp; tile < (kr / 16) * NT; tile += NW) {
+      int mt, jb0;
+      bool imag;
+      tile_of(tile, mt, imag, jb0);
       float acc[kEmuLevels][4];
-      long long ghi[4] = {0, 0, 0, 0}, glo[4] = {0, 0, 0, 0};
 #pragma unroll
       for (int e = 0; e < 4; ++e)
 #pragma unroll
         for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
-      const int nq = gpre ? 0 : rb * RPE;  // G' from the leaf kernel: no Gram here
-      if (gpre) {
-        const S* gw = wsp<S>(ws, I.oGw) + (int64_t)lb * kk;
-        for (int e = threadIdx.x; e < kk; e += kEmuThreads)
-          if (e % k < e / k) Gs[e] = gw[e];
-      }
-      int chunk = 0;
-      for (int q0 = 0; q0 < nq; q0 += kEmuKT, ++chunk) {
-        __syncthreads();  // the previous chunk's MMAs are done with Vs
-        for (int e2 = threadIdx.x; e2 < kr * (kEmuKT / 2); e2 += kEmuThreads) {
-          const int l = e2 / (kEmuKT / 2), q = 2 * (e2 % (kEmuKT / 2)), qa = q0 + q;
-          double x0 = 0.0, x1 = 0.0;
-          if (l < k) {
-            if (qa < nq) x0 = reinterpret_cast<const double*>(Qr + (qa / RPE) * ldr + l)[qa % RPE];
-            if (qa + 1 < nq) x1 = reinterpret_cast<const double*>(Qr + ((qa + 1) / RPE) * ldr + l)[(qa + 1) % RPE];
-          }
-          const int em = l < k ? eV[l] : 0;
-          unsigned w[kEmuSlices];
-          emu_split2(x0, x1, em, em, w);
+      for (int ks = 0; ks < kzf; ks += 16) {
+        unsigned bf[kEmuSlices][2];
 #pragma unroll
-          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * kr + l) * kEmuLd + q) = w[p];
-        }
-        __syncthreads();
-        if (gupper) {
-          for (int ks = 0; ks < kEmuKT; ks += 16) {
-            unsigned bf[kEmuSlices][2];
+        for (int qq = 0; qq < kEmuSlices; qq += 2)
+          ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, jb0, ks, bf[qq], bf[qq + 1]);
+        if (imag) {
 #pragma unroll
-            for (int qq = 0; qq < kEmuSlices; qq += 2)
-              ld_bfrag2(Vs + (qq * kr) * kEmuLd, Vs + ((qq + 1) * kr) * kEmuLd, gjb0, ks, bf[qq], bf[qq + 1]);
-            if (gimag) {
-#pragma unroll
-              for (int qq = 0; qq < kEmuSlices; ++qq) {
-                bf[qq][0] = im_pair(bf[qq][0]);
-                bf[qq][1] = im_pair(bf[qq][1]);
-              }
-            }
-#pragma unroll
-            for (int p = 0; p < kEmuSlices; ++p) {
-              unsigned a[4];
-              ld_afrag(Vs + (p * kr) * kEmuLd, gmt * 16, ks, a);
-#pragma unroll
-              for (int qq = 0; qq < kEmuSlices; ++qq) {
-                if (p + qq > kEmuLevels - 1) continue;
-                mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
-              }
-            }
-          }
-          if (chunk & 1) emu_fold(acc, ghi, glo);  // exact for 128 steps
-        }
-      }
-      if (gupper && !gpre) {
-        emu_fold(acc, ghi, glo);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int i = gmt * 16 + g + (e >= 2 ? 8 : 0);
-          const int j = gjb0 + 2 * t4 + (e & 1);
-          if (i >= j || j >= k) continue;
-          const int sc = eV[i] + eV[j] - 2044;
-          const double v = emu_fx((long long)ghi[e], (long long)glo[e], sc);
-          reinterpret_cast<double*>(Gs + i + j * k)[gimag ? 1 : 0] = v * bs[j];  // G(i, j) beta_j
-        }
-      }
-      // (2) K = T Y_1^* (upper triangular: T and Y_1^* are).  With T^-1 =
-      // diag(1/beta) + (strictly upper part of G) (forward accumulation of the
-      // reflectors; valid for beta_i = 0 too) and K = diag(beta) U, G' as above:
-      //   U(i) = Y_1^*(i) - sum_{l > i} G'(i, l) U(l),
-      // right-looking: after step i + 1 row i is final and step i removes it
-      // from the rows above, in the columns j >= i where it is nonzero.
-      for (int e = threadIdx.x; e < kk; e += kEmuThreads) {
-        const int l = e % k, j = e / k;
-        Ms[l + j * ldf] = j >= l ? conj_(Qr[j * ldr + l]) : zero<S>();  // Y_1^*(l, j) = conj(Y(j, l))
-      }
-      for (int j = warp; j < k; j += NW) {  // column scales of F_b
-        int m = 0;
-        for (int q = lane; q < k * RPE; q += 32)
-          m = max(m, dexp(reinterpret_cast<const double*>(Fr + (q / RPE) + j * ldf)[q % RPE]));
-        m = __reduce_max_sync(0xffffffffu, m);
-        if (lane == 0) eZ[j] = m;
-      }
-      __syncthreads();
-      for (int i = k - 1; i >= 1; --i) {
-        const int w = k - i;
-        for (int e = threadIdx.x; e < i * w; e += kEmuThreads) {
-          const int l = e / w, j = i + e % w;
-          Ms[l + j * ldf] = msub(Ms[l + j * ldf], Gs[l + i * k], Ms[i + j * ldf]);
-        }
-        __syncthreads();
-      }
-      // (3) M = K F_b on tensor cores, contraction over K's columns (one
-      // chunk: RPE k <= 64 steps).  The emulated product forms A^* B, so A
-      // holds conj(K) = conj(diag(beta) U) (row scales eK), B = F_b^T (eZ).
-      for (int l = warp; l < k; l += NW) {  // over the values sliced below
-        int m = 0;
-        for (int q = lane; q < k * RPE; q += 32)
-          m = max(m, dexp(reinterpret_cast<const double*>(Ms + l + (q / RPE) * ldf)[q % RPE] * bs[l]));
-        m = __reduce_max_sync(0xffffffffu, m);
-        if (lane == 0) eK[l] = m;
-      }
-      __syncthreads();
-      for (int e2 = threadIdx.x; e2 < (kr + kpe) * (kEmuKT / 2); e2 += kEmuThreads) {
-        const bool isA = e2 < kr * (kEmuKT / 2);
-        const int f = isA ? e2 : e2 - kr * (kEmuKT / 2);
-        const int row = f / (kEmuKT / 2), q = 2 * (f % (kEmuKT / 2));
-        double x0 = 0.0, x1 = 0.0;
-        if (row < k) {
-          auto part = [&](int qq) -> double {
-            if (qq >= k * RPE) return 0.0;
-            const int r = qq / RPE;
-            if (isA) {
-              const double v = reinterpret_cast<const double*>(Ms + row + r * ldf)[qq % RPE] * bs[row];
-              return (qq % RPE) ? -v : v;  // conj(K)
-            }
-            return reinterpret_cast<const double*>(Fr + r + row * ldf)[qq % RPE];
-          };
-          x0 = part(q);
-          x1 = part(q + 1);
-        }
-        const int em = row < k ? (isA ? eK[row] : eZ[row]) : 0;
-        unsigned w[kEmuSlices];
-        emu_split2(x0, x1, em, em, w);
-        unsigned short* dst = isA ? Vs + (row * kEmuLd + q) : Zs + (row * kEmuLd + q);
-        const int pst = (isA ? kr : kpe) * kEmuLd;
-#pragma unroll
-        for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(dst + p * pst) = w[p];
-      }
-      __syncthreads();
-      if (gmine) {
-        const int kzf = (k * RPE + 15) / 16 * 16;
-        for (int ks = 0; ks < kzf; ks += 16) {
-          unsigned bf[kEmuSlices][2];
-#pragma unroll
-          for (int qq = 0; qq < kEmuSlices; qq += 2)
-            ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, gjb0, ks, bf[qq], bf[qq + 1]);
-          if (gimag) {
-#pragma unroll
-            for (int qq = 0; qq < kEmuSlices; ++qq) {
-              bf[qq][0] = im_pair(bf[qq][0]);
-              bf[qq][1] = im_pair(bf[qq][1]);
-            }
-          }
-#pragma unroll
-          for (int p = 0; p < kEmuSlices; ++p) {
-            unsigned a[4];
-            ld_afrag(Vs + (p * kr) * kEmuLd, gmt * 16, ks, a);
-#pragma unroll
-            for (int qq = 0; qq < kEmuSlices; ++qq) {
-              if (p + qq > kEmuLevels - 1) continue;
-              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
-            }
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            bf[qq][0] = im_pair(bf[qq][0]);
+            bf[qq][1] = im_pair(bf[qq][1]);
           }
         }
-        long long bhi[4] = {0, 0, 0, 0}, blo[4] = {0, 0, 0, 0};
-        emu_fold(acc, bhi, blo);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int l = gmt * 16 + g + (e >= 2 ? 8 : 0);
-          const int j = gjb0 + 2 * t4 + (e & 1);
-          if (l >= k || j >= k) continue;
-          const double v = emu_fx((long long)bhi[e], (long long)blo[e], eK[l] + eZ[j] - 2044);
-          reinterpret_cast<double*>(Ms + l + j * ldf)[gimag ? 1 : 0] = v;
+        for (int p = 0; p < kEmuSlices; ++p) {
+          unsigned a[4];
+          ld_afrag(Vs + (p * kApplyTM) * kEmuLd, mt * 16, ks, a);
+#pragma unroll
+          for (int qq = 0; qq < kEmuSlices; ++qq) {
+            if (p + qq > kEmuLevels - 1) continue;
+            mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+          }
         }
       }
-      __syncthreads();
+      long long bhi[4] = {0, 0, 0, 0}, blo[4] = {0, 0, 0, 0};
+      emu_fold(acc, bhi, blo);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int l = mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int j = jb0 + 2 * t4 + (e & 1);
+        if (l >= k || j >= k) continue;
+        const double v = emu_fx((long long)bhi[e], (long long)blo[e], eK[l] + eZ[j] - 2044);
+        reinterpret_cast<double*>(Ms + l + j * ldf)[imag ? 1 : 0] = v;
+      }
     }
-    // Second operand: F_b, or -M with the compact WY form.
-    const S* Zsrc = wy ? Ms : Fr;
-    const double zsg = wy ? -1.0 : 1.0;
+    __syncthreads();
+    // (4) Second operand -M' (Y's column scales moved in), sliced per column j.
     auto fp = [&](int q, int j) -> double {
       if (q >= kz || j >= k) return 0.0;
       const int i = q / RPE;
       double b;
       if constexpr (C) {
-        const z64 z = Zsrc[i + j * ldf];
+        const z64 z = Ms[i + j * ldf];
         b = (q & 1) ? -z.y : z.x;
       } else {
-        b = reinterpret_cast<const double*>(Zsrc)[i + j * ldf];
+        b = reinterpret_cast<const double*>(Ms)[i + j * ldf];
       }
-      return scale2(zsg * b, eV[i] - 1078);
+      return scale2(-b, eV[i] - 1078);
     };
     for (int j = warp; j < kpe; j += NW) {
       int m = 0;
@@ -1130,69 +1121,86 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_apply_emu(const Inst* insts,
       if (lane == 0) eZ[j] = m;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kpe * kzp; e += kEmuThreads) {
+    for (int e = threadIdx.x; e < kpe * kzp; e += kApplyThreads) {
       const int q = e % kzp, j = e / kzp;
       float sl[kEmuSlices];
       emu_split(fp(q, j), eZ[j], sl);
 #pragma unroll
       for (int p = 0; p < kEmuSlices; ++p) Zs[(p * kpe + j) * kEmuLd + q] = bf16_bits(sl[p]);
     }
-    for (int r0 = 0; r0 < rb; r0 += TM) {
+    // (5) Row tiles of kApplyTM rows: Qbar rows = [F_b; 0] + Y (-M).
+    for (int r0 = 0; r0 < rb; r0 += kApplyTM) {
       __syncthreads();  // Zs complete; the previous row tile's MMAs are done with Vs
-      for (int e2 = threadIdx.x; e2 < TM * kzp / 2; e2 += kEmuThreads) {
-        const int q = 2 * (e2 % (kzp / 2)), r = e2 / (kzp / 2);
+      // Consecutive threads take consecutive rows of a pair of real steps
+      // (coalesced reads of Y's columns).
+      for (int e2 = threadIdx.x; e2 < kApplyTM * kzp / 2; e2 += kApplyThreads) {
+        const int r = e2 % kApplyTM, q = 2 * (e2 / kApplyTM);
         double x0 = 0.0, x1 = 0.0;
         if (r0 + r < rb) {
-          const double* row = reinterpret_cast<const double*>(Qr + (r0 + r) * ldr);
-          if (q < kz) x0 = row[q];
-          if (q + 1 < kz) x1 = row[q + 1];
+          if constexpr (C) {
+            if (q < kz) {
+              const z64 y = Qg[(lo + r0 + r) + (int64_t)(q / 2) * ldq];
+              x0 = y.x;
+              x1 = y.y;
+            }
+          } else {
+            const double* Yr = reinterpret_cast<const double*>(Qg) + lo + r0 + r;
+            if (q < kz) x0 = Yr[(int64_t)q * ldq];
+            if (q + 1 < kz) x1 = Yr[(int64_t)(q + 1) * ldq];
+          }
         }
         unsigned w[kEmuSlices];
         emu_split2(x0, x1, q < kz ? eV[q / RPE] : 0, q + 1 < kz ? eV[(q + 1) / RPE] : 0, w);
 #pragma unroll
-        for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * TM + r) * kEmuLd + q) = w[p];
+        for (int p = 0; p < kEmuSlices; ++p)
+          *reinterpret_cast<unsigned*>(Vs + (p * kApplyTM + r) * kEmuLd + q) = w[p];
       }
       __syncthreads();
-      if (!mine) continue;
-      float acc[kEmuLevels][4];
+      for (int tile = warp; tile < (kApplyTM / 16) * NT; tile += NW) {
+        int mt, jb0;
+        bool imag;
+        tile_of(tile, mt, imag, jb0);
+        if (r0 + mt * 16 >= rb) continue;
+        float acc[kEmuLevels][4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
+        for (int e = 0; e < 4; ++e)
 #pragma unroll
-        for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
-      for (int ks = 0; ks < kzp; ks += 16) {
-        unsigned bf[kEmuSlices][2];
+          for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
+        for (int ks = 0; ks < kzp; ks += 16) {
+          unsigned bf[kEmuSlices][2];
 #pragma unroll
-        for (int qq = 0; qq < kEmuSlices; qq += 2)
-          ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, jb0, ks, bf[qq], bf[qq + 1]);
-        if (imag) {
+          for (int qq = 0; qq < kEmuSlices; qq += 2)
+            ld_bfrag2(Zs + (qq * kpe) * kEmuLd, Zs + ((qq + 1) * kpe) * kEmuLd, jb0, ks, bf[qq], bf[qq + 1]);
+          if (imag) {
 #pragma unroll
-          for (int qq = 0; qq < kEmuSlices; ++qq) {
-            bf[qq][0] = im_pair_update(bf[qq][0]);
-            bf[qq][1] = im_pair_update(bf[qq][1]);
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              bf[qq][0] = im_pair_update(bf[qq][0]);
+              bf[qq][1] = im_pair_update(bf[qq][1]);
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < kEmuSlices; ++p) {
+            unsigned a[4];
+            ld_afrag(Vs + (p * kApplyTM) * kEmuLd, mt * 16, ks, a);
+#pragma unroll
+            for (int qq = 0; qq < kEmuSlices; ++qq) {
+              if (p + qq > kEmuLevels - 1) continue;
+              mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+            }
           }
         }
+        long long hi[4] = {0, 0, 0, 0}, lo4[4] = {0, 0, 0, 0};
+        emu_fold(acc, hi, lo4);
 #pragma unroll
-        for (int p = 0; p < kEmuSlices; ++p) {
-          unsigned a[4];
-          ld_afrag(Vs + (p * TM) * kEmuLd, mt * 16, ks, a);
-#pragma unroll
-          for (int qq = 0; qq < kEmuSlices; ++qq) {
-            if (p + qq > kEmuLevels - 1) continue;
-            mma_bf16(acc[p + qq], a[0], a[1], a[2], a[3], bf[qq][0], bf[qq][1]);
+        for (int e = 0; e < 4; ++e) {
+          const int r = r0 + mt * 16 + g + (e >= 2 ? 8 : 0);
+          const int j = jb0 + 2 * t4 + (e & 1);
+          if (r < rb && j < k) {
+            const int sc = eZ[j] - 966;
+            double v = emu_fx((long long)hi[e], (long long)lo4[e], sc);
+            if (r < k) v += reinterpret_cast<const double*>(Fb + r + (int64_t)j * k)[imag ? 1 : 0];  // [F_b; 0]
+            reinterpret_cast<double*>(Qg + (lo + r) + (int64_t)j * ldq)[imag ? 1 : 0] = v;
           }
-        }
-      }
-      long long hi[4] = {0, 0, 0, 0}, lo4[4] = {0, 0, 0, 0};
-      emu_fold(acc, hi, lo4);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = r0 + mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int j = jb0 + 2 * t4 + (e & 1);
-        if (r < rb && j < k) {
-          const int sc = eZ[j] - 966;
-          double v = emu_fx((long long)hi[e], (long long)lo4[e], sc);
-          if (wy && r < k) v += reinterpret_cast<const double*>(Fr + r + j * ldf)[imag ? 1 : 0];  // [F_b; 0]
-          reinterpret_cast<double*>(Qg + (lo + r) + (int64_t)j * ldq)[imag ? 1 : 0] = v;
         }
       }
     }

@@ -41,13 +41,9 @@ void launch_gram_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, cons
 template <class S>
 void launch_apply_emu(const PlanCore& pc, const Inst* insts, const Io* d_io, const Io& io0, const WorkItem* items,
                       void* ws, cudaStream_t st) {
-  const int wy = 1 | (pc.leaf_tc ? 2 : 0);  // compact WY form; G' from the leaf kernel
-  if (pc.apply_mt == 1)
-    k_apply_emu<S, 1><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, wy);
-  else if (pc.apply_mt == 2)
-    k_apply_emu<S, 2><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, wy);
-  else
-    k_apply_emu<S, 4><<<pc.tab.apply_n, kEmuThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws, pc.P, wy);
+  // G' comes from the leaf kernel when it is k_leaf_emu.
+  k_apply_emu<S><<<pc.tab.apply_n, kApplyThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, items, ws,
+                                                                           pc.leaf_tc ? 1 : 0);
 }
 
 template <class S, class B, bool EMU>
@@ -124,24 +120,13 @@ cudaError_t configure_impl(PlanCore& pc) {
   pc.gram_pipe = EMU && pc.smem_gram_pipe <= (size_t)optin &&
                  raise((const void*)k_gram_emu_pipe<S>, pc.smem_gram_pipe) == cudaSuccess;
   if (EMU) {
-    // Emulated apply: staged Y (P x (k+1)), F_b, G, T (unused) and M, slices of
-    // -M' and of one row tile of at most 16 apply_mt rows per warp column.  MTM
-    // only bounds the row tiles, so it is lowered until the stage fits.
-    const int kpm = (pc.kmax + 7) / 8 * 8, krm = (pc.kmax + 15) / 16 * 16;
-    auto apply_smem = [&](int mt) {
-      return (((size_t)pc.P * (pc.kmax + 1) + 1) / 2 * 2 + 4 * (((size_t)pc.kmax * (pc.kmax + 1) + 1) / 2 * 2)) *
-                 sizeof(S) +
-             (size_t)kEmuSlices * 2 * kEmuLd * (kpm + std::max(16 * mt, krm)) + sizeof(int) * 2 * kMaxKP;
-    };
-    pc.apply_mt = pc.upd_mt;
-    while (pc.apply_mt > 1 && apply_smem(pc.apply_mt) + 1024 > (size_t)optin) pc.apply_mt /= 2;
-    pc.smem_apply_emu = apply_smem(pc.apply_mt);
+    // Emulated apply: G', M, scales and two slice buffers (Y and F_b are read
+    // from global memory), two CTAs per SM.
+    pc.smem_apply_emu = apply_emu_smem(pc.kmax, sizeof(S));
     const void* f = pc.upd_mt == 1 ? (const void*)k_update_emu<S, 1>
                     : pc.upd_mt == 2 ? (const void*)k_update_emu<S, 2> : (const void*)k_update_emu<S, 4>;
     if ((e = raise(f, pc.smem_upd_emu)) != cudaSuccess) return e;
-    const void* fa = pc.apply_mt == 1 ? (const void*)k_apply_emu<S, 1>
-                     : pc.apply_mt == 2 ? (const void*)k_apply_emu<S, 2> : (const void*)k_apply_emu<S, 4>;
-    if ((e = raise(fa, pc.smem_apply_emu)) != cudaSuccess) return e;
+    if ((e = raise((const void*)k_apply_emu<S>, pc.smem_apply_emu)) != cudaSuccess) return e;
   }
   if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;

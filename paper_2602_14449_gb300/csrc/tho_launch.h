@@ -49,7 +49,6 @@ struct PlanCore {
   int* d_status = nullptr;
   size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
   int upd_mt = 4;    // emulated update: 16-row tiles per warp column (max over problems)
-  int apply_mt = 4;  // emulated apply: the same bound, lowered until its stage fits
   int sms = 0;       // SMs of the plan's device
   bool leaf_tc = false;  // emulated complex plan with k >= 24: k_leaf_emu (writes G' for the apply)
   size_t smem_apply_emu = 0;

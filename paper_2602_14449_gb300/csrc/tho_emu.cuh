@@ -1260,6 +1260,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
   unsigned short* Us = reinterpret_cast<unsigned short*>(
       (reinterpret_cast<uintptr_t>(eZ + kMaxKP) + 15) & ~(uintptr_t)15);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+  __shared__ S xd[2];       // the pair's partial dot products
+  __shared__ double xn[2];  // the pair's partial norms
 
   const S* Asrc = from_q ? reinterpret_cast<const S*>(io.Q) : reinterpret_cast<const S*>(io.A);
   const int64_t ldsrc = from_q ? io.ldq : io.lda;
@@ -1283,42 +1285,72 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
   for (int J = 0; J < k; J += kNB) {
     const int jb = min(kNB, k - J);
     // Panel factorization (FP64), column by column, one barrier per column:
-    // in step j warp 0 applies reflector j to column j + 1 and at once forms
-    // reflector j + 1 from it, while the other warps apply reflector j to
-    // columns j + 2.. of the panel (a one-column look-ahead).
-    auto reflector = [&](int j) {  // warp-wide; column j is final below row j - 1
-      double sn = 0.0;
-      for (int i = j + lane; i < rb; i += 32) sn += abs2d(Lb[i + j * P]);
-      sn = warp_sum(sn);
-      if (lane == 0) {
-        double b;
+    // in step j warps 0 and 1 (the pair) apply reflector j to column j + 1 and
+    // at once form reflector j + 1 from it, while warps 2..7 apply reflector j
+    // to columns j + 2.. of the panel (a one-column look-ahead).  A warp issues
+    // one FP64 instruction per 64 cycles at most (the FP64 pipe is shared by
+    // the SM and needs several warps to fill), so the serial chain of the
+    // pair's column is split over the pair's 64 lanes: lane pl takes rows
+    // j + pl, j + pl + 64, .. and the two warps' partial sums meet through
+    // shared memory at a named barrier of the two warps.  The norm of the next
+    // reflector's column is accumulated by the lanes that update its rows.
+    static_assert(kThreads == 256 && kNB <= 8, "the column slots assume 8 warps and panels of <= 8 columns");
+    const bool pair = warp < 2;
+    const int pl = (warp & 1) * 32 + lane;
+    // Sums over the pair's 64 lanes, bitwise the same in both warps.
+    auto pair_sum = [&](S v) -> S {
+      v = warp_sum(v);
+      if (lane == 0) xd[warp] = v;
+      asm volatile("bar.sync 1, 64;" ::: "memory");
+      return add(xd[0], xd[1]);
+    };
+    auto pair_sum_d = [&](double v) -> double {
+      v = warp_sum(v);
+      if (lane == 0) xn[warp] = v;
+      asm volatile("bar.sync 1, 64;" ::: "memory");
+      return xn[0] + xn[1];
+    };
+    auto form = [&](int c, double sn) {  // the pair: reflector c from ||column c below row c - 1||^2
+      if (warp == 0 && lane == 0) {
+        double bb;
         S vj, rjj;
-        make_reflector<S>(sn, Lb[j + j * P], b, vj, rjj);
-        beta_s[j] = b;
-        vdiag[j] = vj;
-        rdiag[j] = rjj;
+        make_reflector<S>(sn, Lb[c + c * P], bb, vj, rjj);
+        beta_s[c] = bb;
+        vdiag[c] = vj;
+        rdiag[c] = rjj;
       }
     };
-    if (warp == 0) reflector(J);
+    if (pair) {
+      double sn = 0.0;
+      for (int i = J + pl; i < rb; i += 64) sn += abs2d(Lb[i + J * P]);
+      form(J, pair_sum_d(sn));
+    }
     __syncthreads();
-    // Column slots: warp 0 takes column j + 1 (the serial chain); warp 4, which
-    // shares warp 0's SM sub-partition and so its FP64 pipe, takes none; the
-    // other six warps take columns j + 2.. (at most six: kNB = 8).
-    static_assert(kThreads == 256 && kNB <= 8, "the column slots assume 8 warps and panels of <= 8 columns");
-    const int slot = warp == 0 ? 0 : (warp < 4 ? warp : (warp > 4 ? warp - 1 : -1));
+    const int slot = pair ? 0 : warp - 1;  // column j + 1 + slot
     for (int j = J; j < J + jb; ++j) {
       const double b = beta_s[j];
       const int c = j + 1 + slot;
-      if (slot >= 0 && c < J + jb) {
-        if (b != 0.0) {
+      if (c < J + jb) {
+        if (pair) {
+          double sn = 0.0;
+          if (b != 0.0) {
+            S d = zero<S>();
+            for (int i = j + pl; i < rb; i += 64) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
+            d = scale(pair_sum(d), b);
+            for (int i = j + pl; i < rb; i += 64) {
+              const S y = msub(Lb[i + c * P], Yv(i, j), d);
+              Lb[i + c * P] = y;
+              if (i > j) sn += abs2d(y);
+            }
+          } else {
+            for (int i = j + 1 + pl; i < rb; i += 64) sn += abs2d(Lb[i + c * P]);
+          }
+          form(c, pair_sum_d(sn));
+        } else if (b != 0.0) {
           S d = zero<S>();
           for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
           d = scale(warp_sum(d), b);
           for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
-        }
-        if (slot == 0) {
-          __syncwarp();
-          reflector(c);
         }
       }
       __syncthreads();

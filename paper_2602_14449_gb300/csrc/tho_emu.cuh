@@ -995,6 +995,8 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
           for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
         int chunk = 0;
         for (int q0 = q_begin; q0 < nq; q0 += kEmuKT, ++chunk) {
+          // A single chunk (a node's U) is sliced once and serves every pass.
+          if (nq - q_begin > kEmuKT || pass == 0) {
           __syncthreads();  // the previous chunk's MMAs are done with Vs
           for (int e2 = threadIdx.x; e2 < kr * (kEmuKT / 2); e2 += kApplyThreads) {
             const int l = e2 / (kEmuKT / 2), q = 2 * (e2 % (kEmuKT / 2)), qa = q0 + q;
@@ -1010,6 +1012,7 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
             for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * kApplyTM + l) * kEmuLd + q) = w[p];
           }
           __syncthreads();
+          }
           if (gup) {
             for (int ks = 0; ks < kEmuKT; ks += 16) {
               unsigned bf[kEmuSlices][2];

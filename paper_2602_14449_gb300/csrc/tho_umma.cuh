@@ -277,7 +277,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
         if (ok && (t % kUmmaGroup) == 0 && t > 0) ok = mbar_wait(b_free, ((t / kUmmaGroup) - 1) & 1);
         if (ok) {
           tc_fence_after();
-          const uint32_t id = umma_idesc_bf16(kUmmaM, N);
           const uint32_t sb = smem_u32(stages + s * stage_bytes);
           const bool first = (t % kUmmaGroup) == 0;
           if (!which) {
@@ -287,11 +286,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
             }
             bulk_store(gvs + (int64_t)t * kVsTileBytes, sb, (uint32_t)kVsTileBytes);
           }
-          // The B slices q and q + 1 are contiguous and so are the level
-          // accumulators p + q and p + q + 1: one N = 2N MMA covers both pairs
-          // (20 MMAs per K step instead of 36; p = 0 touches every level first).
-          // Descriptors advance by (byte offset >> 4) in their address field.
-          const uint32_t id2 = umma_idesc_bf16(kUmmaM, 2 * N);
+          // The B slices q .. q + G - 1 are contiguous and so are the level
+          // accumulators p + q .. p + q + G - 1: one MMA of N = G N covers G
+          // pairs.  The second sweep (slices loaded, not split) takes G = 4
+          // (N <= 256): each A slice is read from shared memory about twice per
+          // K step instead of four or five times, 12 MMAs per K step instead of
+          // 36.  The first sweep, bound by its producers' splitting, keeps G = 2
+          // (20 MMAs), which releases each stage sooner.  p = 0 touches every
+          // level first.  Descriptors advance by (byte offset >> 4) in their
+          // address field.
+          const int G = which ? 4 : 2;
           const uint64_t d0 = umma_sdesc(sb, 128, (kUmmaKT / 8) * 128);
           const uint64_t db = d0 + (uint64_t)((kEmuSlices * abytes) >> 4);
 #pragma unroll
@@ -301,9 +305,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gram_umma(const Inst* insts
               const uint64_t ad = d0 + (uint64_t)((p * abytes + (kk / 8) * 128) >> 4);
               const uint32_t acc = (first && kk == 0 && p == 0) ? 0u : 1u;
 #pragma unroll 1
-              for (int q = 0; p + q < kEmuLevels; q += 2) {
+              for (int q = 0; p + q < kEmuLevels; q += G) {
+                const int nq = min(G, kEmuLevels - p - q);
                 const uint64_t bd = db + (uint64_t)((q * bbytes + (kk / 8) * 128) >> 4);
-                umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd, p + q + 1 < kEmuLevels ? id2 : id, acc);
+                umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd, umma_idesc_bf16(kUmmaM, nq * N), acc);
               }
             }
           }
@@ -565,8 +570,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
   if (warp == 16) {
     if (lane == 0) {
       // A MN-major: LBO = 2048 (i-groups, along K), SBO = 128 (step groups, along M).
-      const uint32_t id = umma_idesc_bf16(128, N) | (1u << 15);
-      const uint32_t id2 = umma_idesc_bf16(128, 2 * N) | (1u << 15);
+
       const uint64_t da = umma_sdesc(smem_u32(stages), 2048, 128);
       const uint64_t db = umma_sdesc(smem_u32(Bz), 128, 16 * 128);
       int sidx = 0;
@@ -580,16 +584,17 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update_umma(const Inst* inst
             break;
           }
           tc_fence_after();
-          // Pairs (p, q), (p, q + 1) as one N = 2N MMA (B slices and level
+          // Pairs (p, q) .. (p, q + 3) as one MMA of N = 4N (B slices and level
           // accumulators are contiguous), as in the Gram.
 #pragma unroll 1
           for (int p = 0; p < kEmuSlices; ++p) {
             const uint64_t ad = da + (uint64_t)((s * kUpdStageBytes + p * (kUpdStageBytes / kEmuSlices)) >> 4);
             const uint32_t acc = (ks == 0 && p == 0) ? 0u : 1u;
 #pragma unroll 1
-            for (int q = 0; p + q < kEmuLevels; q += 2) {
+            for (int q = 0; p + q < kEmuLevels; q += 4) {
+              const int nq = min(4, kEmuLevels - p - q);
               const uint64_t bd = db + (uint64_t)((q * bz + 2 * ks * 128) >> 4);
-              umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd, p + q + 1 < kEmuLevels ? id2 : id, acc);
+              umma_bf16(tmem + (uint32_t)((p + q) * N), ad, bd, umma_idesc_bf16(128, nq * N) | (1u << 15), acc);
             }
           }
           umma_commit(b_empty + 8 * s);

@@ -832,16 +832,6 @@ __global__ void __launch_bounds__(kEmuThreads, 1) k_update_emu(const Inst* insts
 // tensor-core and memory work of the other.
 // Shared: Gs, Ms [k][k+1] S | betas | eK, eV, eZ | Zs [8][kpe][kEmuLd] |
 // Vs [8][kApplyTM][kEmuLd] bf16 (a row tile of Y, or K, or a chunk of Y^T).
-//
-// NODE = true: the same product for the downward pass of the tree (a7): the
-// children of node i of level `lev` get [F_{2i}; F_{2i+1}] = H_0 ... H_{k-1}
-// [F_i; 0], and the node's reflectors (k_tree_up: the bottom parts U, k x k
-// upper triangular, the top entries v_j at row j, the betas) form the 2k x k
-// compact WY block Y = [diag(v); U] with Y_1 = diag(v).  So the children are
-// [F_i; 0] - Y (K F_i), K = T diag(conj v), with G' from the Gram of U on
-// tensor cores (the top block adds nothing off the diagonal).  Each CTA takes
-// npc consecutive nodes of the level's work items; a node with one child
-// passes F_i down.  All problems of the plan share k in this mode.
 constexpr int kApplyThreads = 256;  // 8 warps; two CTAs share an SM
 constexpr int kApplyTM = 32;        // rows per row tile (two 16-row MMA tiles; also k rounded up to 16)
 
@@ -852,18 +842,17 @@ __host__ __device__ inline size_t apply_emu_smem(int k, size_t elem) {
          (size_t)kEmuSlices * kEmuLd * 2 * (kpe + kApplyTM);
 }
 
-template <class S, bool NODE = false>
+template <class S>
 __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* insts, const Io* iot, Io io0,
-                                                                const WorkItem* items, void* ws, int gpre,
-                                                                int lev = 0, int nitems = 0, int npc = 0) {
+                                                                const WorkItem* items, void* ws, int gpre) {
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
   constexpr int NW = kApplyThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const WorkItem it = items[NODE ? min(blockIdx.x * npc, nitems - 1) : blockIdx.x];
-  const Inst& I0 = insts[it.inst];
+  const WorkItem it = items[blockIdx.x];
+  const Inst& I = insts[it.inst];
   const Io io = get_io(iot, io0, it.inst);
-  const int k = (int)I0.k, kk = k * k;
+  const int k = (int)I.k, kk = k * k;
   const int kpe = (k + 7) / 8 * 8;
   const int NT = (C ? 2 * kpe : kpe) / 8;  // 8-column output tiles (complex: Re outputs, then Im)
   const int kz = RPE * k, kzp = (kz + 15) / 16 * 16;
@@ -880,9 +869,10 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
   unsigned short* Vs = Zs + kEmuSlices * kpe * kEmuLd;
   S* Qg = reinterpret_cast<S*>(io.Q);
   const int64_t ldq = io.ldq;
+  const S* Fg = wsp<S>(ws, I.oF);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
-  const int b_begin = NODE ? blockIdx.x * npc : it.idx * I0.leaves3;
-  const int b_end = NODE ? min(nitems, b_begin + npc) : min(I0.nb, b_begin + I0.leaves3);
+  const int b_begin = it.idx * I.leaves3;
+  const int b_end = min(I.nb, b_begin + I.leaves3);
   // Output tile `tile` of an MMA stage: 16-row tile mt, 8-column tile nt
   // (complex: nt >= kpe / 8 are the Im outputs of columns nt * 8 - kpe..).
   auto tile_of = [&](int tile, int& mt, bool& imag, int& jb0) {
@@ -892,60 +882,11 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
     jb0 = imag ? nt * 8 - kpe : nt * 8;
   };
   for (int lb = b_begin; lb < b_end; ++lb) {
-    const Inst& I = NODE ? insts[items[lb].inst] : I0;
-    S* Fg = wsp<S>(ws, I.oF);
-    // Leaf: Y in Q's rows lo.., F_b, output in place.  Node: Y = [diag(v); U]
-    // from the reflectors, F_i, output into the children's F blocks.
-    int64_t lo = 0;
-    int rb;
-    const S* Fb;
-    const S* Ur = nullptr;  // node: U (k x k, ld k), then v (k), then the betas (k)
-    S* Fa = nullptr;        // node: F_{2i}, followed by F_{2i+1}
-    if constexpr (NODE) {
-      const int i = items[lb].idx;
-      const int64_t node = I.lev_off[lev] + i;
-      const int64_t c0 = I.lev_off[lev - 1] + 2 * (int64_t)i;
-      Fb = Fg + node * kk;
-      Fa = Fg + c0 * kk;
-      rb = 2 * k;
-      Ur = wsp<S>(ws, I.oRef) + (node - I.lev_off[1]) * (int64_t)(kk + 2 * k);
-      if (2 * i + 1 >= I.lev_cnt[lev - 1]) {  // one child: F passes down
-        for (int e = threadIdx.x; e < kk; e += kApplyThreads) Fa[e] = Fb[e];
-        continue;
-      }
-    } else {
-      lo = leaf_lo(I, lb);
-      rb = (int)(leaf_lo(I, lb + 1) - lo);
-      Fb = Fg + (I.lev_off[0] + lb) * (int64_t)kk;  // column-major, ld k
-    }
-    // Y(r, c) and real step q of column c of Y.
-    auto yv = [&](int r, int c) -> S {
-      if constexpr (NODE) return r < k ? (r == c ? Ur[kk + c] : zero<S>()) : Ur[(r - k) + c * k];
-      else return Qg[(lo + r) + (int64_t)c * ldq];
-    };
-    auto ypart = [&](int q, int c) -> double {
-      if constexpr (NODE) {
-        const S v = yv(q / RPE, c);
-        if constexpr (C) return (q & 1) ? v.y : v.x;
-        else return v;
-      } else {
-        return reinterpret_cast<const double*>(Qg + lo + (int64_t)c * ldq)[q];
-      }
-    };
-    if (NODE && lb + 1 < b_end) {
-      // The next node's reflectors and F_i are requested into L2.
-      const Inst& I1 = insts[items[lb + 1].inst];
-      const int i1 = items[lb + 1].idx;
-      const int64_t node1 = I1.lev_off[lev] + i1;
-      const S* ref1 = wsp<S>(ws, I1.oRef) + (node1 - I1.lev_off[1]) * (int64_t)(kk + 2 * k);
-      const S* F1 = wsp<S>(ws, I1.oF) + node1 * kk;
-      constexpr int EPL = 128 / sizeof(S);
-      for (int t = threadIdx.x; t * EPL < kk + 2 * k; t += kApplyThreads)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ref1 + t * EPL));
-      for (int t = threadIdx.x; t * EPL < kk; t += kApplyThreads)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(F1 + t * EPL));
-    }
-    if (!NODE && lb + 1 < b_end) {
+    const int64_t lo = leaf_lo(I, lb);
+    const int rb = (int)(leaf_lo(I, lb + 1) - lo);
+    const S* Fb = Fg + (I.lev_off[0] + lb) * (int64_t)kk;  // column-major, ld k
+    const double* Yd = reinterpret_cast<const double*>(Qg + lo);  // column i at Yd + RPE i ldq
+    if (lb + 1 < b_end) {
       // The next leaf's rows of Q (its Y) and its F_b are requested into L2
       // now, one 128-byte line per thread, so that its reads find them there.
       const int64_t lo1 = leaf_lo(I, lb + 1);
@@ -958,18 +899,19 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
         asm volatile("prefetch.global.L2 [%0];" ::"l"(Fb + kk + t * EPL));
     }
     __syncthreads();  // the previous leaf is done with every buffer
-    // Column scales of Y over its rows; the betas.
+    // Column scales of Y over the leaf's rows; the betas.
     for (int i = warp; i < k; i += NW) {
       int m = 0;
-      for (int q = lane; q < rb * RPE; q += 32) m = max(m, dexp(ypart(q, i)));
+      const double* col = Yd + (int64_t)RPE * i * ldq;
+      for (int q = lane; q < rb * RPE; q += 32) m = max(m, dexp(col[q]));
       m = __reduce_max_sync(0xffffffffu, m);
       if (lane == 0) eV[i] = m;
     }
-    const S* btg = NODE ? Ur + kk + k : wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
+    const S* btg = wsp<S>(ws, I.oBeta) + (int64_t)lb * k;
     for (int i = threadIdx.x; i < k; i += kApplyThreads) bs[i] = real_(btg[i]);
     __syncthreads();
     // (1) G' = (Y^* Y) diag(beta), strictly upper part.
-    if (!NODE && gpre) {
+    if (gpre) {
       const S* gw = wsp<S>(ws, I.oGw) + (int64_t)lb * kk;
       for (int e = threadIdx.x; e < kk; e += kApplyThreads)
         if (e % k < e / k) Gs[(e % k) + (e / k) * ldf] = gw[e];
@@ -979,8 +921,7 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
       // operands.  One pass per 16-row tile of G and block of eight 8-column
       // tiles (the chunk is sliced again), so that each warp keeps one
       // accumulator set; tiles wholly below the diagonal are skipped.
-      // (Node: only U's rows, the bottom block, add to the strictly upper part.)
-      const int nq = rb * RPE, q_begin = NODE ? k * RPE : 0;
+      const int nq = rb * RPE;
       const int nblk = (NT + NW - 1) / NW;  // warps' passes over the 8-column tiles
       for (int pass = 0; pass < (kr / 16) * nblk; ++pass) {
         const int mt = pass / nblk, nt = (pass % nblk) * NW + warp;
@@ -994,16 +935,15 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
 #pragma unroll
           for (int L = 0; L < kEmuLevels; ++L) acc[L][e] = 0.0f;
         int chunk = 0;
-        for (int q0 = q_begin; q0 < nq; q0 += kEmuKT, ++chunk) {
-          // A single chunk (a node's U) is sliced once and serves every pass.
-          if (nq - q_begin > kEmuKT || pass == 0) {
+        for (int q0 = 0; q0 < nq; q0 += kEmuKT, ++chunk) {
           __syncthreads();  // the previous chunk's MMAs are done with Vs
           for (int e2 = threadIdx.x; e2 < kr * (kEmuKT / 2); e2 += kApplyThreads) {
             const int l = e2 / (kEmuKT / 2), q = 2 * (e2 % (kEmuKT / 2)), qa = q0 + q;
             double x0 = 0.0, x1 = 0.0;
             if (l < k) {
-              if (qa < nq) x0 = ypart(qa, l);
-              if (qa + 1 < nq) x1 = ypart(qa + 1, l);
+              const double* col = Yd + (int64_t)RPE * l * ldq;
+              if (qa < nq) x0 = col[qa];
+              if (qa + 1 < nq) x1 = col[qa + 1];
             }
             const int em = l < k ? eV[l] : 0;
             unsigned w[kEmuSlices];
@@ -1012,7 +952,6 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
             for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Vs + (p * kApplyTM + l) * kEmuLd + q) = w[p];
           }
           __syncthreads();
-          }
           if (gup) {
             for (int ks = 0; ks < kEmuKT; ks += 16) {
               unsigned bf[kEmuSlices][2];
@@ -1062,7 +1001,7 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
     // from the rows above, in the columns j >= i where it is nonzero.
     for (int e = threadIdx.x; e < kk; e += kApplyThreads) {
       const int j = e % k, l = e / k;  // consecutive threads: consecutive rows j of Y's column l
-      Ms[l + j * ldf] = j >= l ? conj_(yv(j, l)) : zero<S>();  // Y_1^*(l, j) = conj(Y(j, l))
+      Ms[l + j * ldf] = j >= l ? conj_(Qg[(lo + j) + (int64_t)l * ldq]) : zero<S>();  // Y_1^*(l, j) = conj(Y(j, l))
     }
     for (int j = warp; j < k; j += NW) {  // column scales of F_b
       int m = 0;
@@ -1200,13 +1139,14 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
         if (r0 + r < rb) {
           if constexpr (C) {
             if (q < kz) {
-              const S y = yv(r0 + r, q / 2);
+              const z64 y = Qg[(lo + r0 + r) + (int64_t)(q / 2) * ldq];
               x0 = y.x;
               x1 = y.y;
             }
           } else {
-            if (q < kz) x0 = yv(r0 + r, q);
-            if (q + 1 < kz) x1 = yv(r0 + r, q + 1);
+            const double* Yr = reinterpret_cast<const double*>(Qg) + lo + r0 + r;
+            if (q < kz) x0 = Yr[(int64_t)q * ldq];
+            if (q + 1 < kz) x1 = Yr[(int64_t)(q + 1) * ldq];
           }
         }
         unsigned w[kEmuSlices];
@@ -1259,8 +1199,7 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
             const int sc = eZ[j] - 966;
             double v = emu_fx((long long)hi[e], (long long)lo4[e], sc);
             if (r < k) v += reinterpret_cast<const double*>(Fb + r + (int64_t)j * k)[imag ? 1 : 0];  // [F_b; 0]
-            S* dst = NODE ? Fa + (r < k ? r : kk + (r - k)) + (int64_t)j * k : Qg + (lo + r) + (int64_t)j * ldq;
-            reinterpret_cast<double*>(dst)[imag ? 1 : 0] = v;
+            reinterpret_cast<double*>(Qg + (lo + r) + (int64_t)j * ldq)[imag ? 1 : 0] = v;
           }
         }
       }

@@ -127,9 +127,6 @@ cudaError_t configure_impl(PlanCore& pc) {
                     : pc.upd_mt == 2 ? (const void*)k_update_emu<S, 2> : (const void*)k_update_emu<S, 4>;
     if ((e = raise(f, pc.smem_upd_emu)) != cudaSuccess) return e;
     if ((e = raise((const void*)k_apply_emu<S>, pc.smem_apply_emu)) != cudaSuccess) return e;
-    if ((e = raise((const void*)k_apply_emu<S, true>, pc.smem_apply_emu)) != cudaSuccess) return e;
-    pc.tree_emu = true;
-    for (const Inst& I : pc.h_insts) pc.tree_emu = pc.tree_emu && I.k == pc.kmax;
   }
   if ((e = raise((const void*)k_apply_gram<S, B>, pc.smem_apply)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
@@ -238,18 +235,10 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
     const int nl = pc.tab.lev_n[l];
     const WorkItem* li = items + pc.tab.lev_off[l];
     if (nl <= 0) continue;
-    // Emulated plans: every level as compact WY products on tensor cores (the
-    // apply kernel's node mode), two CTAs per SM, consecutive nodes per CTA.
-    // Otherwise the widest levels take a warp per node and the others four row
-    // groups per column (more row groups cost more FP64 warp instructions per
-    // node, and the FP64 pipe, charged per warp instruction, bounds even the
-    // narrow levels).
-    if (EMU && pc.tree_emu) {
-      const int grid = std::min(nl, 2 * std::max(1, pc.sms));
-      const int npc = (nl + grid - 1) / grid;
-      k_apply_emu<S, true><<<(nl + npc - 1) / npc, kApplyThreads, pc.smem_apply_emu, st>>>(insts, d_io, io0, li, ws, 0,
-                                                                                          l, nl, npc);
-    } else if (nl >= kTreeDownWide * pc.sms)
+    // Widest levels: a warp per node; the others four row groups per column
+    // (more row groups cost more FP64 warp instructions per node, and the FP64
+    // pipe, charged per warp instruction, bounds even the narrow levels).
+    if (nl >= kTreeDownWide * pc.sms)
       k_tree_down_w<S><<<nl, 32, pc.smem_tree, st>>>(insts, li, ws, l);
     else
       k_tree_down<S><<<nl, kTreeThreads, pc.smem_tree, st>>>(insts, li, ws, l);

@@ -50,7 +50,6 @@ struct PlanCore {
   size_t smem_gram = 0, smem_leaf = 0, smem_apply = 0, smem_upd = 0, smem_tree = 0;
   int upd_mt = 4;    // emulated update: 16-row tiles per warp column (max over problems)
   int sms = 0;       // SMs of the plan's device
-  bool tree_emu = false;  // emulated plan whose problems share k: the tree's downward levels on tensor cores
   bool leaf_tc = false;  // emulated complex plan with k >= 24: k_leaf_emu (writes G' for the apply)
   size_t smem_apply_emu = 0;
   size_t smem_gram_pipe = 0, smem_gram_umma = 0;

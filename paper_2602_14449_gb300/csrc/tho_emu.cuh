@@ -1222,6 +1222,24 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
 // rows, the betas into the workspace.
 // Shared: Lb [kp][P] S | vdiag, rdiag, beta, T (kNB x kNB), W (kNB x kp) | scales |
 // slices: step W: A [8][16][40], B [8][kpc + 8 + J][40]; step C: A [8][64][24], B [8][kpc][24].
+// Warp sums of the leaf panel.  Complex: five FP64 additions instead of ten
+// (the FP64 pipe, shared by the SM, bounds the panel): at the first level the
+// lower half of the warp keeps real parts and the upper half imaginary parts,
+// each lane adding the component its partner sends; four levels sum within
+// each half; one exchange gives every lane both parts.  Every lane ends with
+// bitwise the same value (each level adds the same two operands in both lanes
+// of a pair).
+__device__ __forceinline__ double panel_sum(double v) { return warp_sum(v); }
+__device__ __forceinline__ z64 panel_sum(z64 v) {
+  const bool up = (threadIdx.x & 16u) != 0;
+  double keep = up ? v.y : v.x;
+  keep += __shfl_xor_sync(0xffffffffu, up ? v.x : v.y, 16);
+#pragma unroll
+  for (int m = 8; m >= 1; m >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, m);
+  const double other = __shfl_xor_sync(0xffffffffu, keep, 16);
+  return up ? z64{other, keep} : z64{keep, other};
+}
+
 constexpr int kLeKT = 32;   // real contraction steps per chunk of the W product
 constexpr int kLeLdW = 40;  // row stride of the W-product slices (conflict-free ldmatrix)
 constexpr int kLeLdC = 24;  // row stride of the C-product slices (16 steps + pad)
@@ -1262,6 +1280,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
   __shared__ S xd[2];       // the pair's partial dot products
   __shared__ double xn[2];  // the pair's partial norms
+  __shared__ double xa;     // |x_c| of the reflector being formed
+  __shared__ S xph;         // and its phase
 
   const S* Asrc = from_q ? reinterpret_cast<const S*>(io.Q) : reinterpret_cast<const S*>(io.A);
   const int64_t ldsrc = from_q ? io.ldq : io.lda;
@@ -1299,7 +1319,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     const int pl = (warp & 1) * 32 + lane;
     // Sums over the pair's 64 lanes, bitwise the same in both warps.
     auto pair_sum = [&](S v) -> S {
-      v = warp_sum(v);
+      v = panel_sum(v);
       if (lane == 0) xd[warp] = v;
       asm volatile("bar.sync 1, 64;" ::: "memory");
       return add(xd[0], xd[1]);
@@ -1310,14 +1330,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
       asm volatile("bar.sync 1, 64;" ::: "memory");
       return xn[0] + xn[1];
     };
-    auto form = [&](int c, double sn) {  // the pair: reflector c from ||column c below row c - 1||^2
+    // The pair forms reflector c from sn = ||column c below row c - 1||^2 with
+    // make_reflector's arithmetic, its two independent parts on the two warps:
+    // warp 1 takes |x_c| and the phase of x_c, warp 0 alpha = sqrt(sn), then
+    // warp 0 combines them (the same operations, so the same bits).
+    auto form = [&](int c, double sn) {
+      double alpha = 0.0;
+      if (lane == 0) {
+        if (warp == 1) {
+          double ax;
+          S ph;
+          abs_phase(Lb[c + c * P], ax, ph);
+          xa = ax;
+          xph = ph;
+        } else {
+          alpha = sqrt(sn);
+        }
+      }
+      asm volatile("bar.sync 1, 64;" ::: "memory");
       if (warp == 0 && lane == 0) {
-        double bb;
-        S vj, rjj;
-        make_reflector<S>(sn, Lb[c + c * P], bb, vj, rjj);
-        beta_s[c] = bb;
-        vdiag[c] = vj;
-        rdiag[c] = rjj;
+        if (alpha == 0.0) {
+          beta_s[c] = 0.0;
+          vdiag[c] = zero<S>();
+          rdiag[c] = zero<S>();
+        } else {
+          const S ph = xph;
+          vdiag[c] = add(Lb[c + c * P], scale(ph, alpha));
+          rdiag[c] = scale(ph, -alpha);
+          beta_s[c] = 1.0 / (alpha * (alpha + xa));  // 2 / (2 alpha (alpha + |x_c|))
+        }
       }
     };
     if (pair) {
@@ -1349,7 +1390,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
         } else if (b != 0.0) {
           S d = zero<S>();
           for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
-          d = scale(warp_sum(d), b);
+          d = scale(panel_sum(d), b);
           for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
         }
       }

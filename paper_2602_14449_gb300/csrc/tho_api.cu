@@ -374,7 +374,10 @@ tho_status_t plan_impl(const tho_desc_t* descs, int32_t count, const tho_tuning_
     }
     I.oRn = take(nodes * kk);
     I.oRef = take((nodes - I.nb) * (kk + 2 * k));
-    I.oF = take(nodes * kk);
+    // A node's F (downward pass) takes the slot of its R: every R but the
+    // root's is dead once the upward pass has combined it, and the root's is
+    // read out by k_root before F_root overwrites it.
+    I.oF = I.oRn;
     I.oPs = take((pc.flags & THO_FLAG_P_POLAR) ? 2 + tho::kPolarMaxIt : 1);
     I.oBeta = take(pc.prec == THO_PREC_FP64_EMU ? (int64_t)I.nb * k : 1);
     I.oGw = take(pc.leaf_tc ? (int64_t)I.nb * kk : 1);

@@ -175,7 +175,10 @@ extern "C" tho_status_t tho_orth_noalloc(const tho_desc_t* d, const void* V, int
   I.oG3 = take((int64_t)std::max(I.g3, I.g1) * k0 * k);
   I.oRn = take(nodes * kk);
   I.oRef = take((nodes - I.nb) * (kk + 2 * k));
-  I.oF = take(nodes * kk);
+  // A node's F (downward pass) takes the slot of its R: every R but the
+  // root's is dead once the upward pass has combined it, and the root's is
+  // read out by k_root before F_root overwrites it.
+  I.oF = I.oRn;
   // Work-item table: gram, leaf, apply, update, then one block per tree level.
   int nit = 0;
   pc.tab.gram_off = nit;

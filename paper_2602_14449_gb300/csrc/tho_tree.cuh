@@ -379,9 +379,14 @@ __global__ void __launch_bounds__(kTreeUpG * kMaxKP, 3) k_tree_up_p(const Inst* 
 }
 
 // Root of the tree: D = diag(phase(R_jj)); R_out = D^* R (diag real >= 0);
-// F_root = D so that the leaf factors carry the normalization.
+// F_root = D so that the leaf factors carry the normalization.  F_root shares
+// R_root's storage: every read of R comes before the barrier, every write
+// after it.
+constexpr int kRootPer = (kMaxKP * kMaxKP + kThreads - 1) / kThreads;  // entries per thread
 template <class S>
-__global__ void k_root(const Inst* insts, const Io* iot, Io io0, void* ws, int* status, uint32_t flags) {
+__global__ void __launch_bounds__(kThreads) k_root(const Inst* insts, const Io* iot, Io io0, void* ws, int* status,
+                                                   uint32_t flags) {
+  __shared__ S dg[kMaxKP];  // phase(R_jj)
   const int inst = blockIdx.x;
   const Inst& I = insts[inst];
   const Io io = get_io(iot, io0, inst);
@@ -390,17 +395,28 @@ __global__ void k_root(const Inst* insts, const Io* iot, Io io0, void* ws, int* 
   const S* R = wsp<S>(ws, I.oRn) + node * kk;
   S* F = wsp<S>(ws, I.oF) + node * kk;
   S* Ro = reinterpret_cast<S*>(io.R);
-  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-    int r = e % k, c = e / k;
-    S dr = phase(R[r + r * k]);
+  S rv[kRootPer];
+#pragma unroll
+  for (int u = 0; u < kRootPer; ++u) {
+    const int e = threadIdx.x + u * kThreads;
+    rv[u] = e < kk ? R[e] : zero<S>();
+  }
+  for (int r = threadIdx.x; r < k; r += kThreads) dg[r] = phase(R[r + r * k]);
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kRootPer; ++u) {
+    const int e = threadIdx.x + u * kThreads;
+    if (e >= kk) continue;
+    const int r = e % k, c = e / k;
+    const S dr = dg[r];
     F[e] = (r == c) ? dr : zero<S>();
     if (Ro) {
       S v = zero<S>();
-      if (r < c) v = mul(conj_(dr), R[e]);
-      else if (r == c) v = from_real<S>(absd(R[e]));
+      if (r < c) v = mul(conj_(dr), rv[u]);
+      else if (r == c) v = from_real<S>(absd(rv[u]));
       Ro[e] = v;
     }
-    if ((flags & 0x2u) && r == c && !finite_(R[e])) atomicExch(status, 7);
+    if ((flags & 0x2u) && r == c && !finite_(rv[u])) atomicExch(status, 7);
   }
 }
 

@@ -78,27 +78,18 @@ __device__ __forceinline__ double scale2i(double x, int e) {
 
 // The 56-bit fixed-point magnitude X of x relative to emax (the integer
 // emu_split slices), as its top and bottom 28 bits, and the sign.  With M the
-// 53-bit mantissa and sh = e - emax + 3 <= 3: top = M >> (28 - sh); bottom =
-// (M << sh) mod 2^28 for sh >= 0, (M >> -sh) mod 2^28 otherwise; computed on
-// the two 32-bit words of M with funnel shifts.
+// 53-bit mantissa and sh = e - emax + 3 <= 3: X = M 2^sh (M >> -sh when sh < 0;
+// zero for x = 0 or subnormal), top = X >> 28, bottom = X mod 2^28.
 __device__ __forceinline__ void emu_fixed56(double x, int emax, unsigned& h, unsigned& l, bool& neg) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const unsigned hw = (unsigned)(bits >> 32), lw = (unsigned)bits;
-  const int e = (int)((hw >> 20) & 0x7ff);
-  const unsigned mh = (hw & 0xfffffu) | 0x100000u;
+  const int e = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long M = (bits & 0xfffffffffffffULL) | 0x10000000000000ULL;
   const int sh = e - emax + 3;
-  const int t = 28 - sh;  // >= 25
-  unsigned hh = t < 32 ? __funnelshift_r(lw, mh, t) : (t < 64 ? mh >> (t - 32) : 0u);
-  unsigned ll;
-  if (sh >= 0) {
-    ll = (lw << sh) & 0xfffffffu;
-  } else {
-    const int r = -sh;
-    ll = (r < 32 ? __funnelshift_r(lw, mh, r) : (r < 64 ? mh >> (r - 32) : 0u)) & 0xfffffffu;
-  }
-  h = e != 0 ? hh : 0u;
-  l = e != 0 ? ll : 0u;
-  neg = (hw >> 31) != 0;
+  unsigned long long X = sh >= 0 ? (M << sh) : (M >> (-sh < 63 ? -sh : 63));
+  X = e != 0 ? X : 0ULL;
+  h = (unsigned)(X >> 28);
+  l = (unsigned)X & 0xfffffffu;
+  neg = (long long)bits < 0;
 }
 
 // xor shuffle of a scalar (double or complex double) within the lanes of mask.

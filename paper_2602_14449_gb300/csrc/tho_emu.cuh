@@ -1112,12 +1112,12 @@ __global__ void __launch_bounds__(kApplyThreads, 2) k_apply_emu(const Inst* inst
       if (lane == 0) eZ[j] = m;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kpe * kzp; e += kApplyThreads) {
-      const int q = e % kzp, j = e / kzp;
-      float sl[kEmuSlices];
-      emu_split(fp(q, j), eZ[j], sl);
+    for (int e2 = threadIdx.x; e2 < kpe * kzp / 2; e2 += kApplyThreads) {
+      const int q = 2 * (e2 % (kzp / 2)), j = e2 / (kzp / 2);
+      unsigned w[kEmuSlices];
+      emu_split2(fp(q, j), fp(q + 1, j), eZ[j], eZ[j], w);
 #pragma unroll
-      for (int p = 0; p < kEmuSlices; ++p) Zs[(p * kpe + j) * kEmuLd + q] = bf16_bits(sl[p]);
+      for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Zs + (p * kpe + j) * kEmuLd + q) = w[p];
     }
     // (5) Row tiles of kApplyTM rows: Qbar rows = [F_b; 0] + Y (-M).
     for (int r0 = 0; r0 < rb; r0 += kApplyTM) {

@@ -108,23 +108,22 @@ __device__ __forceinline__ unsigned bf16x2_sub(unsigned a, unsigned b) {
 // The eight slices of two values (x0 with scale emax0, x1 with emax1) as packed
 // bf16 pairs: w[p] holds slice p of x0 in its low half and of x1 in its high
 // half.  With the 7-bit slice magnitudes a0, a1 placed under the bf16 pattern
-// of 128 (0x4300: exponent 2^7, the magnitude as the 7-bit mantissa), one
-// packed subtraction of (128, 128) gives (a0, a1) exactly; the signs are
-// XOR-ed in.
+// of +-128 (0x4300 or 0xC300: exponent 2^7, the magnitude as the 7-bit
+// mantissa, the value's sign), one packed subtraction of that same pattern
+// gives (+-a0, +-a1) exactly (a zero slice of a negative value comes out +0).
 __device__ __forceinline__ void emu_split2(double x0, double x1, int emax0, int emax1,
                                            unsigned (&w)[kEmuSlices]) {
   unsigned h0, l0, h1, l1;
   bool n0, n1;
   emu_fixed56(x0, emax0, h0, l0, n0);
   emu_fixed56(x1, emax1, h1, l1, n1);
-  const unsigned sg = (n0 ? 0x8000u : 0u) | (n1 ? 0x80000000u : 0u);
+  const unsigned base = 0x43004300u | (n0 ? 0x8000u : 0u) | (n1 ? 0x80000000u : 0u);
 #pragma unroll
   for (int p = 0; p < kEmuSlices; ++p) {
     const int sh = 21 - 7 * (p & 3);
     const unsigned a = p < 4 ? h0 : l0, b = p < 4 ? h1 : l1;
-    const unsigned lo = ((a >> sh) & 0x7fu) | 0x43004300u;
     const unsigned hi = (sh <= 16 ? (b << (16 - sh)) : (b >> (sh - 16))) & 0x7f0000u;
-    w[p] = bf16x2_sub(lo | hi, 0x43004300u) ^ sg;
+    w[p] = bf16x2_sub(((a >> sh) & 0x7fu) | hi | base, base);
   }
 }
 

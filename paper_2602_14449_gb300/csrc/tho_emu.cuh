@@ -1233,22 +1233,33 @@ __device__ __forceinline__ z64 panel_sum(z64 v) {
 constexpr int kLeKT = 32;   // real contraction steps per chunk of the W product
 constexpr int kLeLdW = 40;  // row stride of the W-product slices (conflict-free ldmatrix)
 constexpr int kLeLdC = 24;  // row stride of the C-product slices (16 steps + pad)
-constexpr int kLeRC = 64;   // rows per chunk of the C product (4 m-tiles: 2-3 output tiles per warp)
+// Threads of a leaf CTA: 8 warps for leaves of <= 128 rows (two CTAs share an
+// SM), 16 for 256-row leaves (one CTA per SM, the same warps per SM).
+__host__ __device__ constexpr int leaf_emu_threads(int P) { return P > 128 ? 512 : 256; }
+// Rows per chunk of the C product: 4 m-tiles per 8 warps (2-3 output tiles per warp).
+__host__ __device__ constexpr int leaf_emu_rc(int threads) { return threads / 4; }
 __host__ __device__ inline size_t leaf_emu_smem(int P, int kp, size_t elem) {
   const size_t sw = (size_t)kEmuSlices * 2 * kLeLdW * (16 + kMaxKP);
-  const size_t sc = (size_t)kEmuSlices * 2 * kLeLdC * (kLeRC + 24);
+  const size_t sc = (size_t)kEmuSlices * 2 * kLeLdC * (leaf_emu_rc(leaf_emu_threads(P)) + 24);
   return (size_t)P * kp * elem + (size_t)kMaxKP * (2 * elem + 8) + (size_t)kNB * kNB * elem +
          (size_t)kNB * kMaxKP * elem + sizeof(int) * (kNB + 2 * kMaxKP) + (sw > sc ? sw : sc) + 64;
 }
 
-template <class S>
-__global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, const Io* iot, Io io0,
+template <class S, int TH>
+__global__ void __launch_bounds__(TH, TH == 256 ? 2 : 1) k_leaf_emu(const Inst* insts, const Io* iot, Io io0,
                                                          const WorkItem* items, void* ws, int P, int from_q) {
   // Besides R, Y and the betas, the leaf writes G' = (Y^* Y) diag(beta) (its
   // strictly upper part) for the apply, from the same tensor-core products.
   constexpr bool C = Tr<S>::C;
   constexpr int RPE = C ? 2 : 1;
-  constexpr int NW = kThreads / 32;
+  constexpr int NW = TH / 32;
+  // The panel's serial chain runs on CW warps (CL lanes); the look-ahead
+  // columns on CAW warps each; the W product splits its contraction steps
+  // over KG groups of 8 warps.
+  constexpr int CW = NW / 4, CL = CW * 32, CAW = (NW - CW) / 6, KG = NW / 8;
+  constexpr int kRC = leaf_emu_rc(TH);
+  static_assert((TH == 256 || TH == 512) && kNB <= 8 && (NW - CW) % 6 == 0,
+                "the column slots assume 8 or 16 warps and panels of <= 8 columns");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const WorkItem it = items[blockIdx.x];
   const Inst& I = insts[it.inst];
@@ -1268,24 +1279,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
   unsigned short* Us = reinterpret_cast<unsigned short*>(
       (reinterpret_cast<uintptr_t>(eZ + kMaxKP) + 15) & ~(uintptr_t)15);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
-  __shared__ S xd[2];       // the pair's partial dot products
-  __shared__ double xn[2];  // the pair's partial norms
+  __shared__ S xd[CW];       // the chain warps' partial dot products
+  __shared__ double xn[CW];  // the chain warps' partial norms
+  __shared__ S xc[6][CAW];   // the look-ahead warps' partial dot products, per column slot
   __shared__ double xa;     // |x_c| of the reflector being formed
   __shared__ S xph;         // and its phase
 
   const S* Asrc = from_q ? reinterpret_cast<const S*>(io.Q) : reinterpret_cast<const S*>(io.A);
   const int64_t ldsrc = from_q ? io.ldq : io.lda;
   // Loads in groups of 8 per thread ahead of their stores (one round trip per group).
-  for (int e0 = threadIdx.x; e0 < P * kp; e0 += 8 * kThreads) {
+  for (int e0 = threadIdx.x; e0 < P * kp; e0 += 8 * TH) {
     S v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * kThreads, r = e % P, c = e / P;
+      const int e = e0 + u * TH, r = e % P, c = e / P;
       v[u] = (e < P * kp && r < rb && c < k) ? Asrc[(lo + r) + (int64_t)c * ldsrc] : zero<S>();
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * kThreads;
+      const int e = e0 + u * TH;
       if (e < P * kp) Lb[e] = v[u];
     }
   }
@@ -1304,21 +1316,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     // j + pl, j + pl + 64, .. and the two warps' partial sums meet through
     // shared memory at a named barrier of the two warps.  The norm of the next
     // reflector's column is accumulated by the lanes that update its rows.
-    static_assert(kThreads == 256 && kNB <= 8, "the column slots assume 8 warps and panels of <= 8 columns");
-    const bool pair = warp < 2;
-    const int pl = (warp & 1) * 32 + lane;
-    // Sums over the pair's 64 lanes, bitwise the same in both warps.
+    // With 16 warps the chain runs on four warps (two rows per lane of a
+    // 256-row leaf, as two warps for 128 rows) and each look-ahead column on
+    // two, whose partial sums meet at a named barrier of their own.
+    const bool pair = warp < CW;
+    const int pl = warp * 32 + lane;  // chain lane (pair only)
+    // Sums over the chain's CL lanes, bitwise the same in all its warps.
     auto pair_sum = [&](S v) -> S {
       v = panel_sum(v);
       if (lane == 0) xd[warp] = v;
-      asm volatile("bar.sync 1, 64;" ::: "memory");
-      return add(xd[0], xd[1]);
+      asm volatile("bar.sync 1, %0;" ::"r"(CL) : "memory");
+      S r = xd[0];
+#pragma unroll
+      for (int u = 1; u < CW; ++u) r = add(r, xd[u]);
+      return r;
     };
     auto pair_sum_d = [&](double v) -> double {
       v = warp_sum(v);
       if (lane == 0) xn[warp] = v;
-      asm volatile("bar.sync 1, 64;" ::: "memory");
-      return xn[0] + xn[1];
+      asm volatile("bar.sync 1, %0;" ::"r"(CL) : "memory");
+      double r = xn[0];
+#pragma unroll
+      for (int u = 1; u < CW; ++u) r += xn[u];
+      return r;
     };
     // The pair forms reflector c from sn = ||column c below row c - 1||^2 with
     // make_reflector's arithmetic, its two independent parts on the two warps:
@@ -1337,7 +1357,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
           alpha = sqrt(sn);
         }
       }
-      asm volatile("bar.sync 1, 64;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(CL) : "memory");
       if (warp == 0 && lane == 0) {
         if (alpha == 0.0) {
           beta_s[c] = 0.0;
@@ -1353,11 +1373,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     };
     if (pair) {
       double sn = 0.0;
-      for (int i = J + pl; i < rb; i += 64) sn += abs2d(Lb[i + J * P]);
+      for (int i = J + pl; i < rb; i += CL) sn += abs2d(Lb[i + J * P]);
       form(J, pair_sum_d(sn));
     }
     __syncthreads();
-    const int slot = pair ? 0 : warp - 1;  // column j + 1 + slot
+    const int slot = pair ? 0 : (warp - CW) / CAW + 1;  // column j + 1 + slot
+    const int sub = pair ? 0 : (warp - CW) % CAW;       // the warp's share of the slot's rows
     for (int j = J; j < J + jb; ++j) {
       const double b = beta_s[j];
       const int c = j + 1 + slot;
@@ -1366,22 +1387,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
           double sn = 0.0;
           if (b != 0.0) {
             S d = zero<S>();
-            for (int i = j + pl; i < rb; i += 64) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
+            for (int i = j + pl; i < rb; i += CL) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
             d = scale(pair_sum(d), b);
-            for (int i = j + pl; i < rb; i += 64) {
+            for (int i = j + pl; i < rb; i += CL) {
               const S y = msub(Lb[i + c * P], Yv(i, j), d);
               Lb[i + c * P] = y;
               if (i > j) sn += abs2d(y);
             }
           } else {
-            for (int i = j + 1 + pl; i < rb; i += 64) sn += abs2d(Lb[i + c * P]);
+            for (int i = j + 1 + pl; i < rb; i += CL) sn += abs2d(Lb[i + c * P]);
           }
           form(c, pair_sum_d(sn));
         } else if (b != 0.0) {
+          constexpr int RS = 32 * CAW;  // row stride of the slot's warps
           S d = zero<S>();
-          for (int i = j + lane; i < rb; i += 32) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
-          d = scale(panel_sum(d), b);
-          for (int i = j + lane; i < rb; i += 32) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
+          for (int i = j + sub * 32 + lane; i < rb; i += RS) d = cmadd(d, Yv(i, j), Lb[i + c * P]);
+          d = panel_sum(d);
+          if constexpr (CAW > 1) {
+            if (lane == 0) xc[slot - 1][sub] = d;
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(32 * CAW) : "memory");
+            d = xc[slot - 1][0];
+#pragma unroll
+            for (int u = 1; u < CAW; ++u) d = add(d, xc[slot - 1][u]);
+          }
+          d = scale(d, b);
+          for (int i = j + sub * 32 + lane; i < rb; i += RS) Lb[i + c * P] = msub(Lb[i + c * P], Yv(i, j), d);
         }
       }
       __syncthreads();
@@ -1416,9 +1446,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
       const int kpb = kpc + kNB + J, NTB = (C ? 2 : 1) * kpb / 8;
       unsigned short* Aw = Us;                           // [8][16][kLeLdW]
       unsigned short* Bw = Us + kEmuSlices * 16 * kLeLdW;  // [8][kpb][kLeLdW]
-      const bool mine = warp < NTB;
-      const bool imag = C && warp * 8 >= kpb;
-      const int jb0 = imag ? warp * 8 - kpb : warp * 8;
+      // Warp w takes output tile w mod 8 over the steps of group w / 8 (KG
+      // groups split each chunk's steps; their exact sums add at the end).
+      const int wt = warp % 8, kg = warp / 8;
+      const bool mine = wt < NTB;
+      const bool imag = C && wt * 8 >= kpb;
+      const int jb0 = imag ? wt * 8 - kpb : wt * 8;
       float acc[kEmuLevels][4];
       long long hi[4] = {0, 0, 0, 0}, lo4[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -1431,7 +1464,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
         // pairs: A rows l < 16 (l < jb real), B rows j < kpb (C column j < nc,
         // panel column j - kpc < jb, or earlier column j - kpc - 8 < J); q pair in 0..30
         const int npa = 16 * (kLeKT / 2), npb = kpb * (kLeKT / 2);
-        for (int e2 = threadIdx.x; e2 < npa + npb; e2 += kThreads) {
+        for (int e2 = threadIdx.x; e2 < npa + npb; e2 += TH) {
           const bool isA = e2 < npa;
           const int f = isA ? e2 : e2 - npa;
           const int row = f / (kLeKT / 2), q = 2 * (f % (kLeKT / 2)), qa = q0 + q;
@@ -1463,7 +1496,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
         __syncthreads();
         if (mine) {
 #pragma unroll
-          for (int ks = 0; ks < kLeKT; ks += 16) {
+          for (int u = 0; u < kLeKT / (16 * KG); ++u) {
+            const int ks = (u * KG + kg) * 16;
             unsigned bf[kEmuSlices][2];
 #pragma unroll
             for (int qq = 0; qq < kEmuSlices; qq += 2)
@@ -1490,8 +1524,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
         }
         __syncthreads();
       }
-      if (mine) {
-        emu_fold(acc, hi, lo4);
+      if (mine) emu_fold(acc, hi, lo4);
+      if constexpr (KG > 1) {  // the slice buffers are free: they carry group 1's sums
+        long long* xs = reinterpret_cast<long long*>(Us);  // [8 tiles][hi 4, lo 4][32 lanes]
+        if (mine && kg == 1) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xs[(wt * 8 + e) * 32 + lane] = hi[e];
+            xs[(wt * 8 + 4 + e) * 32 + lane] = lo4[e];
+          }
+        }
+        __syncthreads();
+        if (mine && kg == 0) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            hi[e] += xs[(wt * 8 + e) * 32 + lane];
+            lo4[e] += xs[(wt * 8 + 4 + e) * 32 + lane];
+          }
+        }
+      }
+      if (mine && kg == 0) {
         double* gw = reinterpret_cast<double*>(wsp<S>(ws, I.oGw) + (int64_t)it.idx * k * k);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {  // rows g (< 8) of the 16-row tile
@@ -1519,7 +1571,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     //   (T^* W)(i) = beta_i (W(i) - sum_{l < i} conj(G(l, i)) (T^* W)(l)),
     // which also holds for beta_i = 0.  Right-looking: row l is final once
     // scaled, then removed from the rows below.  One thread per column of W.
-    for (int c = threadIdx.x; c < nc; c += kThreads) {
+    for (int c = threadIdx.x; c < nc; c += TH) {
       S x[kNB];
 #pragma unroll
       for (int l = 0; l < kNB; ++l) x[l] = l < jb ? Wb[l + c * kNB] : zero<S>();
@@ -1539,8 +1591,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
     // ---- C <- C - Y_J W on tensor cores.  W'(l, j) = 2^(eY_l - 1078) W(l, j), real-embedded
     // along the contraction (complex: (Re W', -Im W') pairs; Im outputs swap).
     {
-      unsigned short* Ac = Us;                                // [8][kLeRC][kLeLdC]
-      unsigned short* Bc = Us + kEmuSlices * kLeRC * kLeLdC;  // [8][kpc][kLeLdC]
+      unsigned short* Ac = Us;                              // [8][kRC][kLeLdC]
+      unsigned short* Bc = Us + kEmuSlices * kRC * kLeLdC;  // [8][kpc][kLeLdC]
       auto wp = [&](int q, int j) -> double {  // W' entry at real contraction step q, column j
         const int l = q / RPE;
         if (l >= jb || j >= nc) return 0.0;
@@ -1560,16 +1612,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
         if (lane == 0) eZ[j] = m;
       }
       __syncthreads();
-      for (int e2 = threadIdx.x; e2 < kpc * 8; e2 += kThreads) {
+      for (int e2 = threadIdx.x; e2 < kpc * 8; e2 += TH) {
         const int j = e2 / 8, q = 2 * (e2 % 8);
         unsigned w[kEmuSlices];
         emu_split2(wp(q, j), wp(q + 1, j), eZ[j], eZ[j], w);
 #pragma unroll
         for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Bc + (p * kpc + j) * kLeLdC + q) = w[p];
       }
-      for (int rc = J; rc < rb; rc += kLeRC) {
+      for (int rc = J; rc < rb; rc += kRC) {
         __syncthreads();  // Bc written; the previous chunk's MMAs are done with Ac
-        for (int e2 = threadIdx.x; e2 < kLeRC * 8; e2 += kThreads) {
+        for (int e2 = threadIdx.x; e2 < kRC * 8; e2 += TH) {
           const int r = e2 / 8, q = 2 * (e2 % 8), ra = rc + r;
           double x0 = 0.0, x1 = 0.0;
           if (ra < rb) {
@@ -1587,10 +1639,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
           unsigned w[kEmuSlices];
           emu_split2(x0, x1, l0 < jb ? eY[l0] : 0, l1 < jb ? eY[l1] : 0, w);
 #pragma unroll
-          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Ac + (p * kLeRC + r) * kLeLdC + q) = w[p];
+          for (int p = 0; p < kEmuSlices; ++p) *reinterpret_cast<unsigned*>(Ac + (p * kRC + r) * kLeLdC + q) = w[p];
         }
         __syncthreads();
-        for (int tile = warp; tile < (kLeRC / 16) * NT; tile += NW) {
+        for (int tile = warp; tile < (kRC / 16) * NT; tile += NW) {
           const int mt = tile / NT, nt = tile % NT;
           const bool imag = C && nt * 8 >= kpc;
           const int jb0 = imag ? nt * 8 - kpc : nt * 8;
@@ -1613,7 +1665,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
 #pragma unroll
           for (int p = 0; p < kEmuSlices; ++p) {
             unsigned a[4];
-            ld_afrag<kLeLdC>(Ac + (p * kLeRC) * kLeLdC, mt * 16, 0, a);
+            ld_afrag<kLeLdC>(Ac + (p * kRC) * kLeLdC, mt * 16, 0, a);
 #pragma unroll
             for (int qq = 0; qq < kEmuSlices; ++qq) {
               if (p + qq > kEmuLevels - 1) continue;
@@ -1639,17 +1691,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_leaf_emu(const Inst* insts, con
   }
   // R into the tree's leaf node, Y into Q's rows, the betas into the workspace.
   S* Rn = wsp<S>(ws, I.oRn) + (I.lev_off[0] + it.idx) * (int64_t)(k * k);
-  for (int e = threadIdx.x; e < k * k; e += kThreads) {
+  for (int e = threadIdx.x; e < k * k; e += TH) {
     const int i = e % k, c = e / k;
     Rn[e] = i < c ? Lb[i + c * P] : (i == c ? rdiag[c] : zero<S>());
   }
   S* Q = reinterpret_cast<S*>(io.Q);
-  for (int e = threadIdx.x; e < rb * k; e += kThreads) {
+  for (int e = threadIdx.x; e < rb * k; e += TH) {
     const int r = e % rb, c = e / rb;
     Q[(lo + r) + (int64_t)c * io.ldq] = Yv(r, c);
   }
   S* bt = wsp<S>(ws, I.oBeta) + (int64_t)it.idx * k;
-  for (int c = threadIdx.x; c < k; c += kThreads) bt[c] = from_real<S>(beta_s[c]);
+  for (int c = threadIdx.x; c < k; c += TH) bt[c] = from_real<S>(beta_s[c]);
 }
 
 }  // namespace tho

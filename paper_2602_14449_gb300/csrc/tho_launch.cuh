@@ -132,7 +132,11 @@ cudaError_t configure_impl(PlanCore& pc) {
   if ((e = raise((const void*)k_update_q<S, B>, pc.smem_upd)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_leaf<S, B>, pc.smem_leaf)) != cudaSuccess) return e;
   pc.smem_leaf_emu = leaf_emu_smem(pc.P, pc.kpmax, sizeof(S));
-  if (EMU && (e = raise((const void*)k_leaf_emu<S>, pc.smem_leaf_emu)) != cudaSuccess) return e;
+  if constexpr (EMU && Tr<S>::C) {  // k_leaf_emu serves complex plans only (leaf_tc)
+    if ((e = raise(pc.P > 128 ? (const void*)k_leaf_emu<S, 512> : (const void*)k_leaf_emu<S, 256>,
+                   pc.smem_leaf_emu)) != cudaSuccess)
+      return e;
+  }
   if ((e = raise((const void*)k_tree_down<S>, pc.smem_tree)) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_up_p<S>, tree_up_p_smem(kTreeUpG, pc.kmax, sizeof(S)))) != cudaSuccess) return e;
   if ((e = raise((const void*)k_tree_down_w<S>, pc.smem_tree)) != cudaSuccess) return e;
@@ -203,10 +207,17 @@ cudaError_t run_impl(const PlanCore& pc, const Io* d_io, const Io& io0, cudaStre
   // Emulated mode: the leaf QR ends with the compact WY output.  Its trailing
   // updates go to tensor cores when they are wide enough to pay for the
   // slicing (complex, k >= 24: two CTAs per SM instead of three); else FP64.
-  if (EMU && pc.leaf_tc)
-    k_leaf_emu<S><<<pc.tab.leaf_n, blk, pc.smem_leaf_emu, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
-                                                               pc.any_k0 ? 1 : 0);
-  else
+  bool leaf_done = false;
+  if constexpr (EMU && Tr<S>::C) {
+    if (pc.leaf_tc && pc.P > 128)  // 256-row leaves: 16 warps, one CTA per SM
+      k_leaf_emu<S, 512><<<pc.tab.leaf_n, leaf_emu_threads(pc.P), pc.smem_leaf_emu, st>>>(
+          insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P, pc.any_k0 ? 1 : 0);
+    else if (pc.leaf_tc)
+      k_leaf_emu<S, 256><<<pc.tab.leaf_n, blk, pc.smem_leaf_emu, st>>>(insts, d_io, io0, items + pc.tab.leaf_off,
+                                                                      ws, pc.P, pc.any_k0 ? 1 : 0);
+    leaf_done = pc.leaf_tc;
+  }
+  if (!leaf_done)
     k_leaf<S, B><<<pc.tab.leaf_n, blk, pc.smem_leaf, st>>>(insts, d_io, io0, items + pc.tab.leaf_off, ws, pc.P,
                                                          EMU ? ((pc.any_k0 ? 1 : 0) | 2) : 0);
   hk(kPhLeaf, 1, st);

@@ -77,19 +77,17 @@ __device__ __forceinline__ double scale2i(double x, int e) {
 }
 
 // The 56-bit fixed-point magnitude X of x relative to emax (the integer
-// emu_split slices), as its top and bottom 28 bits, and the sign.  With M the
-// 53-bit mantissa and sh = e - emax + 3 <= 3: X = M 2^sh (M >> -sh when sh < 0;
-// zero for x = 0 or subnormal), top = X >> 28, bottom = X mod 2^28.
-__device__ __forceinline__ void emu_fixed56(double x, int emax, unsigned& h, unsigned& l, bool& neg) {
+// emu_split slices) and the sign.  With M the 53-bit mantissa and
+// sh = e - emax + 3 <= 3: X = M 2^sh (M >> -sh when sh < 0; zero for x = 0 or
+// subnormal).
+__device__ __forceinline__ unsigned long long emu_fixed56(double x, int emax, bool& neg) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7ff);
   const unsigned long long M = (bits & 0xfffffffffffffULL) | 0x10000000000000ULL;
   const int sh = e - emax + 3;
-  unsigned long long X = sh >= 0 ? (M << sh) : (M >> (-sh < 63 ? -sh : 63));
-  X = e != 0 ? X : 0ULL;
-  h = (unsigned)(X >> 28);
-  l = (unsigned)X & 0xfffffffu;
+  const unsigned long long X = sh >= 0 ? (M << sh) : (M >> (-sh < 63 ? -sh : 63));
   neg = (long long)bits < 0;
+  return e != 0 ? X : 0ULL;
 }
 
 // xor shuffle of a scalar (double or complex double) within the lanes of mask.
@@ -107,23 +105,29 @@ __device__ __forceinline__ unsigned bf16x2_sub(unsigned a, unsigned b) {
 
 // The eight slices of two values (x0 with scale emax0, x1 with emax1) as packed
 // bf16 pairs: w[p] holds slice p of x0 in its low half and of x1 in its high
-// half.  With the 7-bit slice magnitudes a0, a1 placed under the bf16 pattern
-// of +-128 (0x4300 or 0xC300: exponent 2^7, the magnitude as the 7-bit
-// mantissa, the value's sign), one packed subtraction of that same pattern
-// gives (+-a0, +-a1) exactly (a zero slice of a negative value comes out +0).
+// half (slice p = bits 49 - 7p .. 55 - 7p of X).  The 14-bit groups of X0 and
+// X1 (bits 42-55, 28-41, 14-27, 0-13) are first paired in one word, group g of
+// X0 in bits 0-13 and of X1 in bits 16-29, so that one shift and one mask give
+// slices 2g and 2g + 1 of both values.  With the 7-bit magnitudes a0, a1 placed
+// under the bf16 pattern of +-128 (0x4300 or 0xC300: exponent 2^7, the
+// magnitude as the 7-bit mantissa, the value's sign), one packed subtraction of
+// that same pattern gives (+-a0, +-a1) exactly (a zero slice of a negative
+// value comes out +0).
 __device__ __forceinline__ void emu_split2(double x0, double x1, int emax0, int emax1,
                                            unsigned (&w)[kEmuSlices]) {
-  unsigned h0, l0, h1, l1;
   bool n0, n1;
-  emu_fixed56(x0, emax0, h0, l0, n0);
-  emu_fixed56(x1, emax1, h1, l1, n1);
+  const unsigned long long X0 = emu_fixed56(x0, emax0, n0), X1 = emu_fixed56(x1, emax1, n1);
+  const unsigned l0 = (unsigned)X0, h0 = (unsigned)(X0 >> 32), l1 = (unsigned)X1, h1 = (unsigned)(X1 >> 32);
+  unsigned g[4];
+  g[0] = ((h0 >> 10) & 0x3fffu) | ((h1 << 6) & 0x3fff0000u);
+  g[1] = (__funnelshift_r(l0, h0, 28) & 0x3fffu) | ((__funnelshift_r(l1, h1, 28) << 16) & 0x3fff0000u);
+  g[2] = ((l0 >> 14) & 0x3fffu) | ((l1 << 2) & 0x3fff0000u);
+  g[3] = (l0 & 0x3fffu) | ((l1 << 16) & 0x3fff0000u);
   const unsigned base = 0x43004300u | (n0 ? 0x8000u : 0u) | (n1 ? 0x80000000u : 0u);
 #pragma unroll
-  for (int p = 0; p < kEmuSlices; ++p) {
-    const int sh = 21 - 7 * (p & 3);
-    const unsigned a = p < 4 ? h0 : l0, b = p < 4 ? h1 : l1;
-    const unsigned hi = (sh <= 16 ? (b << (16 - sh)) : (b >> (sh - 16))) & 0x7f0000u;
-    w[p] = bf16x2_sub(((a >> sh) & 0x7fu) | hi | base, base);
+  for (int q = 0; q < 4; ++q) {
+    w[2 * q] = bf16x2_sub(((g[q] >> 7) & 0x007f007fu) | base, base);
+    w[2 * q + 1] = bf16x2_sub((g[q] & 0x007f007fu) | base, base);
   }
 }
 

@@ -77,17 +77,17 @@ __device__ __forceinline__ double scale2i(double x, int e) {
 }
 
 // The 56-bit fixed-point magnitude X of x relative to emax (the integer
-// emu_split slices) and the sign.  With M the 53-bit mantissa and
-// sh = e - emax + 3 <= 3: X = M 2^sh (M >> -sh when sh < 0; zero for x = 0 or
-// subnormal).
+// emu_split slices) and the sign.  With M the 53-bit mantissa and e <= emax
+// (emax is the largest exponent of x's group): X = (M 2^3) >> (emax - e), i.e.
+// M 2^(e - emax + 3); zero for x = 0 or subnormal, and for e > emax (never
+// passed).
 __device__ __forceinline__ unsigned long long emu_fixed56(double x, int emax, bool& neg) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7ff);
   const unsigned long long M = (bits & 0xfffffffffffffULL) | 0x10000000000000ULL;
-  const int sh = e - emax + 3;
-  const unsigned long long X = sh >= 0 ? (M << sh) : (M >> (-sh < 63 ? -sh : 63));
+  const unsigned r = min((unsigned)(emax - e), 63u);
   neg = (long long)bits < 0;
-  return e != 0 ? X : 0ULL;
+  return e != 0 ? (M << 3) >> r : 0ULL;
 }
 
 // xor shuffle of a scalar (double or complex double) within the lanes of mask.

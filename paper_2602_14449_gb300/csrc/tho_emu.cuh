@@ -1486,8 +1486,17 @@ __global__ void __launch_bounds__(TH, TH == 256 ? 2 : 1) k_leaf_emu(const Inst* 
               if constexpr (C) return (qq & 1) ? v.y : v.x;
               else return v;
             };
-            x0 = part(qa);
-            x1 = part(qa + 1);
+            if constexpr (C) {  // qa is even and nq even: steps qa, qa + 1 are one entry's (Re, Im)
+              if (qa < nq) {
+                const int r = J + qa / 2;
+                const S v = isY ? Yv(r, col) : Lb[r + col * P];
+                x0 = v.x;
+                x1 = v.y;
+              }
+            } else {
+              x0 = part(qa);
+              x1 = part(qa + 1);
+            }
             em = pl >= 0 ? eP[pl] : (isY ? eY[yl] : eC[row]);
           }
           unsigned w[kEmuSlices];
@@ -1636,8 +1645,16 @@ __global__ void __launch_bounds__(TH, TH == 256 ? 2 : 1) k_leaf_emu(const Inst* 
               if constexpr (C) return (qq & 1) ? v.y : v.x;
               else return v;
             };
-            x0 = part(q);
-            x1 = part(q + 1);
+            if constexpr (C) {  // q is even: steps q, q + 1 are one entry's (Re, Im)
+              if (q / 2 < jb) {
+                const S v = Yv(ra, J + q / 2);
+                x0 = v.x;
+                x1 = v.y;
+              }
+            } else {
+              x0 = part(q);
+              x1 = part(q + 1);
+            }
           }
           const int l0 = q / RPE, l1 = (q + 1) / RPE;
           unsigned w[kEmuSlices];

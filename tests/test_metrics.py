@@ -1,7 +1,7 @@
 """The accuracy measures themselves, on the CPU.
 
-tests/gpu_metrics.py judges the full-size GPU runs (chunked, pairwise-summed
-Gram products in torch); tests/metrics.py judges the small ones (numpy/LAPACK).
+tests/gpu_metrics.py checks the full-size GPU runs (chunked, pairwise-summed
+Gram products in torch); tests/metrics.py checks the small ones (numpy/LAPACK).
 Both must agree with each other and with values known in closed form."""
 import numpy as np
 import pytest
